@@ -1,0 +1,217 @@
+/*
+ * apm.h -- C ABI of the all-principal-minor library (libapm.so) for GB300.
+ *
+ * What the library computes (Simkovic & Ferrero, "Fast Principal Minor
+ * Algorithms for Quantum Many Body Systems", arXiv:2104.07638):
+ *   - all 2^n principal minors of n x n matrices by the Schur-complement tree
+ *     with pivot correction (Section II, Eq. minor, Alg. 1);
+ *   - the connected sums of the CDet recursion over all subsets (Section V.A,
+ *     Eq. recursion), fused with the minors;
+ *   - the real-time Keldysh sum over 2^n index assignments as the sum of XOR
+ *     principal minors of the 2n x 2n block matrix (Sections III.D and V.D);
+ *   - all 2^n permanent principal minors in O(3^n) (Section IV).
+ *
+ * Conventions shared by every call
+ *   Subsets are bit masks: element k (0-based) <-> bit k, so an array indexed by
+ *   mask S in [0, 2^n) holds the value for the subset S (Section II labels the
+ *   subset S_i by the binary digits of i). minors[0] = det(empty) = 1,
+ *   perms[0] = 1, c[0] = 0.
+ *   Matrices are row-major and stored back to back ("batch-major"): matrix b of a
+ *   fixed-order batch starts at element b*n*n.
+ *   All data pointers are DEVICE pointers owned by the caller, 16-byte aligned.
+ *   The library allocates no device memory in any call: where scratch is needed
+ *   the caller passes it (apm_workspace_size tells how much).
+ *   Calls are asynchronous on `stream` (NULL = the legacy default stream).
+ *   Argument errors are detected on the host, before any launch, and return
+ *   APM_ERR_ARG / APM_ERR_UNSUPPORTED_N / APM_ERR_WORKSPACE with nothing written.
+ *   A launch failure returns APM_ERR_CUDA (apm_last_cuda_error gives the code).
+ *   Numerical trouble never aborts a launch: it sets bits in the optional
+ *   per-matrix `status` array (device memory, one uint32 per matrix, written by
+ *   every call that takes it) and, where the result cannot be trusted, fills that
+ *   matrix's outputs with NaN. apm_status_reduce() collects the bits on the host.
+ */
+#ifndef APM_H
+#define APM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A cudaStream_t. */
+typedef struct CUstream_st *apm_stream_t;
+
+typedef enum {
+    APM_OK = 0,
+    APM_ERR_ARG = 1,            /* null/misaligned pointer, negative batch, bad flags */
+    APM_ERR_UNSUPPORTED_N = 2,  /* order outside the supported range of the call */
+    APM_ERR_CUDA = 3,           /* a CUDA runtime call or launch failed */
+    APM_ERR_NUMERIC = 4,        /* apm_status_reduce: some matrix has an error bit */
+    APM_ERR_TIMEOUT = 5,        /* a bounded device-side wait gave up */
+    APM_ERR_WORKSPACE = 6       /* scratch missing or smaller than apm_workspace_size */
+} apm_status_t;
+
+/* Per-matrix status bits. */
+#define APM_ST_PIVOT_CORRECTED     0x01u /* a pivot correction was applied and back-propagated */
+#define APM_ST_NONFINITE_INPUT     0x02u /* the input held a NaN or an infinity */
+#define APM_ST_ZERO_PIVOT          0x04u /* Keldysh: a zero or non-finite pivot; sum set to NaN */
+#define APM_ST_CORRECTION_OVERFLOW 0x08u /* more pivot corrections than the per-matrix log holds
+                                            (256); outputs set to NaN */
+#define APM_ST_ERROR_MASK          (APM_ST_NONFINITE_INPUT | APM_ST_ZERO_PIVOT | APM_ST_CORRECTION_OVERFLOW)
+
+/* Largest supported orders. */
+#define APM_MAX_N_MINORS   16
+#define APM_MAX_N_KELDYSH  16
+#define APM_MAX_N_PERM     16
+
+/*
+ * Pivot correction (Section II, the paragraph after Eq. minor and Alg. 1): when
+ * a pivot p of the Schur-complement tree satisfies |p| <= piv_threshold*||A||max
+ * it is replaced by p + C with C = sign(p)*piv_shift*||A||max (sign(0) = +1),
+ * the node's minor is stored with the shifted pivot, and after the tree the
+ * shift is removed exactly by det(A[S]) = det(A~[S]) - C det(A[S \ {l}]),
+ * applied to the node and its whole right subtree, deepest level first.
+ * Any choice gives the same exact result; the threshold trades stability.
+ * NULL selects the defaults below (||A||max = 0 is treated as 1).
+ */
+typedef struct {
+    double piv_threshold; /* default 1e-6 */
+    double piv_shift;     /* default 1.0 */
+} apm_pivot_opts;
+
+#define APM_DEFAULT_PIV_THRESHOLD 1e-6
+#define APM_DEFAULT_PIV_SHIFT 1.0
+
+/*
+ * apm_all_minors -- all 2^n principal minors of each matrix.
+ * Section II (Eq. dets_schur, Eq. lemma1/lemma2, Eq. minor, Alg. 1): the minor of
+ * subset S_i is the minor of S_i \ {l} times the (1,1) entry of the Schur
+ * complement reached along the tree path of S_i.
+ *   A       [batch][n][n] float64, input.
+ *   n       1..APM_MAX_N_MINORS.
+ *   batch   >= 0 (0 launches nothing).
+ *   minors  [batch][2^n] float64, output, minors[b][S] = det(A_b[S]).
+ *   opt     pivot-correction options or NULL.
+ *   status  [batch] uint32 or NULL.
+ *   workspace / workspace_bytes: scratch for n > 12 (see apm_workspace_size);
+ *           may be NULL/0 for n <= 12.
+ */
+apm_status_t apm_all_minors(const double *A, int n, int64_t batch, double *minors,
+                            const apm_pivot_opts *opt, uint32_t *status, void *workspace,
+                            size_t workspace_bytes, apm_stream_t stream);
+
+/* flags for apm_cdet_connected */
+#define APM_CDET_SINGLE_DET 0x1 /* a[S] = det(A_up[S]) instead of det(A_up[S]) det(A_dn[S]) */
+
+/*
+ * apm_cdet_connected -- connected sums c[S] for all subsets S, fused with the
+ * minors that define the weights.
+ * Section V.A: a[S] = det(M_up[S]) det(M_dn[S]); Eq. recursion:
+ *     c[S] = a[S] - sum_{T proper subset of S, j in T} c[T] a[S \ T],
+ * with j = the lowest element of S (the paper lets j be any element of S).
+ *   A_up       [batch][n][n] float64.
+ *   A_dn       [batch][n][n] float64 or NULL; NULL means the spin-symmetric case
+ *              M_dn = M_up, so a[S] = det(A_up[S])^2.
+ *   flags      0 or APM_CDET_SINGLE_DET (then A_dn must be NULL).
+ *   c          [batch][2^n] float64 output.
+ *   minors_out [batch][2^n] float64 (minors of A_up) or NULL; when A_dn is given,
+ *              [batch][2][2^n] (minors of A_up, then of A_dn).
+ *   opt, status, workspace: as for apm_all_minors.
+ */
+apm_status_t apm_cdet_connected(const double *A_up, const double *A_dn, int n, int64_t batch,
+                                int flags, double *c, double *minors_out,
+                                const apm_pivot_opts *opt, uint32_t *status, void *workspace,
+                                size_t workspace_bytes, apm_stream_t stream);
+
+/*
+ * apm_cdet_from_weights -- the CDet recursion (Eq. recursion) applied to given
+ * weights a[S] (e.g. permanent minors for the bosonic connected sum of
+ * Section V.F, or products of two minor arrays).
+ *   a  [batch][2^n] float64 input (a[0] is ignored).   c  [batch][2^n] output.
+ */
+apm_status_t apm_cdet_from_weights(const double *a, int n, int64_t batch, double *c,
+                                   void *workspace, size_t workspace_bytes, apm_stream_t stream);
+
+/* flags for apm_keldysh_sum */
+#define APM_KELDYSH_SIGNED 0x1 /* weight each assignment by (-1)^{number of - indices} */
+
+/*
+ * apm_keldysh_sum -- sum over all 2^n Keldysh index assignments alpha of
+ * det[G^{alpha_i alpha_j}(X_i - X_j)] (Section V.D), computed as the sum of the
+ * XOR principal minors of the 2n x 2n block matrix (Section III.D) by a binary
+ * tree of Schur complements in O(2^n); no pivot correction is possible there.
+ *   Mt       [batch][2n][2n] complex128, interleaved (re, im); the 2x2 block of
+ *            vertices (i, j) is at rows 2i (index +), 2i+1 (index -) and columns
+ *            2j, 2j+1.
+ *   n        1..APM_MAX_N_KELDYSH.
+ *   flags    0 or APM_KELDYSH_SIGNED.
+ *   sum      [batch][2] float64 output (re, im).
+ *   partial  [batch][n+1][2] float64 or NULL: partial[b][d] = the same sum over
+ *            the first d vertices only (the lower orders obtained on the way,
+ *            Section V.D); partial[b][0] = 1, partial[b][n] = sum[b].
+ *   status   [batch] or NULL; APM_ST_ZERO_PIVOT marks a zero or non-finite pivot,
+ *            and then sum (and partial) of that matrix are NaN.
+ */
+apm_status_t apm_keldysh_sum(const double *Mt, int n, int64_t batch, int flags, double *sum,
+                             double *partial, uint32_t *status, apm_stream_t stream);
+
+/*
+ * apm_perm_minors -- all 2^n permanent principal minors perm(A[S]) in O(3^n)
+ * (Section IV): for every column subset T the row sums r_i(T) = sum_{j in T} A_ij,
+ * the products over supersets S of T built one element at a time, and
+ *     perm(A[S]) = (-1)^|S| sum_{T subset of S} (-1)^|T| prod_{i in S} r_i(T).
+ *   A      [batch][n][n] float64.    perms  [batch][2^n] float64 output.
+ *   n      1..APM_MAX_N_PERM.
+ */
+apm_status_t apm_perm_minors(const double *A, int n, int64_t batch, double *perms,
+                             void *workspace, size_t workspace_bytes, apm_stream_t stream);
+
+/* operation codes for apm_workspace_size */
+#define APM_OP_ALL_MINORS 1
+#define APM_OP_CDET 2
+#define APM_OP_CDET_FROM_WEIGHTS 3
+#define APM_OP_PERM_MINORS 4
+#define APM_OP_CDET_VARLEN 5
+
+/*
+ * apm_workspace_size -- bytes of device scratch the call `op` needs for orders up
+ * to n_max and `batch` matrices on the current device (0 when none is needed).
+ * two_mats != 0 sizes APM_OP_CDET for a separate A_dn.
+ */
+apm_status_t apm_workspace_size(int op, int n_max, int64_t batch, int two_mats, size_t *bytes);
+
+/*
+ * apm_status_reduce -- OR of the per-matrix status words; synchronises `stream`.
+ *   status_dev [batch] device array written by an earlier call on `stream`.
+ *   or_bits    host output.
+ * Returns APM_ERR_NUMERIC when any APM_ST_ERROR_MASK bit is set, else APM_OK.
+ */
+apm_status_t apm_status_reduce(const uint32_t *status_dev, int64_t batch, uint32_t *or_bits,
+                               apm_stream_t stream);
+
+/* Human-readable name of a status code (static storage). */
+const char *apm_status_string(apm_status_t s);
+
+/* The cudaError_t of the last APM_ERR_CUDA on this thread (0 if none). */
+int apm_last_cuda_error(void);
+
+/* Library version, e.g. 100 for 0.1.0. */
+int apm_version(void);
+
+/*
+ * apm_fp64_fma_probe -- FP64 throughput microbenchmark (no counterpart in the
+ * paper; it measures the roofline denominator of the FP64-bound kernels).
+ * Launches `blocks` x `threads` threads, each running `iters` rounds of 8
+ * independent dependent-chain FP64 fused multiply-adds; writes one double per
+ * thread to `sink` (device, blocks*threads doubles) so nothing is optimised away.
+ * FLOPs = 16 * blocks * threads * iters.
+ */
+apm_status_t apm_fp64_fma_probe(double *sink, int blocks, int threads, int iters,
+                                apm_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* APM_H */

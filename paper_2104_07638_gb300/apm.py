@@ -1,0 +1,242 @@
+"""Thin Python binding of libapm.so (ctypes). Argument marshalling only.
+
+Every function takes CUDA tensors (torch is used for device memory and the
+current stream), checks shapes and dtypes, allocates the outputs with torch and
+calls the C ABI declared in include/apm.h with raw device pointers. All
+computation happens in the CUDA kernels of the library; there is no CPU or
+PyTorch fallback: if the library cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+APM_OK, APM_ERR_ARG, APM_ERR_UNSUPPORTED_N, APM_ERR_CUDA, APM_ERR_NUMERIC, APM_ERR_TIMEOUT, \
+    APM_ERR_WORKSPACE = range(7)
+ST_PIVOT_CORRECTED, ST_NONFINITE_INPUT, ST_ZERO_PIVOT, ST_CORRECTION_OVERFLOW = 1, 2, 4, 8
+CDET_SINGLE_DET = 1
+KELDYSH_SIGNED = 1
+OP_ALL_MINORS, OP_CDET, OP_CDET_FROM_WEIGHTS, OP_PERM_MINORS, OP_CDET_VARLEN = 1, 2, 3, 4, 5
+
+
+class ApmError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        lib = _lib
+        msg = lib.apm_status_string(code).decode() if lib is not None else str(code)
+        if code == APM_ERR_CUDA and lib is not None:
+            msg += f" (cudaError {lib.apm_last_cuda_error()})"
+        super().__init__(f"{where}: {msg}")
+        self.code = code
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Loads libapm.so (building it first if the sources are newer)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if _build.needs_build():
+                _build.build()
+            if not os.path.exists(path):
+                raise RuntimeError(f"libapm.so missing at {path}: the CUDA library was not built")
+            L = ctypes.CDLL(path)
+            P, i32, i64, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_size_t
+            OPT = ctypes.POINTER(PivotOpts)
+            sig = {
+                "apm_all_minors": [P, i32, i64, P, OPT, P, P, sz, P],
+                "apm_cdet_connected": [P, P, i32, i64, i32, P, P, OPT, P, P, sz, P],
+                "apm_cdet_from_weights": [P, i32, i64, P, P, sz, P],
+                "apm_keldysh_sum": [P, i32, i64, i32, P, P, P, P],
+                "apm_perm_minors": [P, i32, i64, P, P, sz, P],
+                "apm_workspace_size": [i32, i32, i64, i32, ctypes.POINTER(sz)],
+                "apm_status_reduce": [P, i64, ctypes.POINTER(ctypes.c_uint32), P],
+                "apm_fp64_fma_probe": [P, i32, i32, i32, P],
+            }
+            for name, args in sig.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = ctypes.c_int
+            L.apm_status_string.argtypes = [ctypes.c_int]
+            L.apm_status_string.restype = ctypes.c_char_p
+            L.apm_last_cuda_error.restype = ctypes.c_int
+            L.apm_version.restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+class PivotOpts(ctypes.Structure):
+    _fields_ = [("piv_threshold", ctypes.c_double), ("piv_shift", ctypes.c_double)]
+
+
+def _check(code: int, where: str):
+    if code != APM_OK:
+        raise ApmError(code, where)
+
+
+def _stream(t: torch.Tensor) -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream(t.device).cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _mat_batch(A: torch.Tensor, dtype=torch.float64, name="A"):
+    if not isinstance(A, torch.Tensor) or not A.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if A.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}")
+    if A.dim() == 2:
+        A = A.unsqueeze(0)
+    if A.dim() != 3 or A.shape[1] != A.shape[2]:
+        raise ValueError(f"{name} must be (batch, n, n)")
+    return A.contiguous()
+
+
+def _opts(piv_threshold, piv_shift):
+    if piv_threshold is None and piv_shift is None:
+        return None
+    return ctypes.pointer(PivotOpts(1e-6 if piv_threshold is None else piv_threshold,
+                                    1.0 if piv_shift is None else piv_shift))
+
+
+def workspace_size(op: int, n: int, batch: int, two_mats: bool = False) -> int:
+    out = ctypes.c_size_t(0)
+    _check(lib().apm_workspace_size(op, n, batch, int(two_mats), ctypes.byref(out)),
+           "apm_workspace_size")
+    return int(out.value)
+
+
+def _workspace(op, n, batch, device, two_mats=False):
+    nb = workspace_size(op, n, batch, two_mats)
+    if nb == 0:
+        return None, 0
+    return torch.empty(nb, dtype=torch.uint8, device=device), nb
+
+
+def all_minors(A: torch.Tensor, piv_threshold=None, piv_shift=None, return_status=False):
+    """All 2^n principal minors of each matrix of A (batch, n, n) float64."""
+    A = _mat_batch(A)
+    b, n, _ = A.shape
+    out = torch.empty((b, 1 << n), dtype=torch.float64, device=A.device)
+    st = torch.zeros(b, dtype=torch.int32, device=A.device) if return_status else None
+    ws, nb = _workspace(OP_ALL_MINORS, n, b, A.device)
+    _check(lib().apm_all_minors(_ptr(A), n, b, _ptr(out), _opts(piv_threshold, piv_shift),
+                                _ptr(st), _ptr(ws), nb, _stream(A)), "apm_all_minors")
+    return (out, st) if return_status else out
+
+
+def cdet_connected(A_up: torch.Tensor, A_dn: torch.Tensor | None = None, single_det=False,
+                   return_minors=False, return_status=False, piv_threshold=None, piv_shift=None,
+                   out_c=None, out_minors=None, workspace=None):
+    """Connected sums c[S] (Eq. recursion) of a[S] = det(A_up[S]) det(A_dn[S])
+    (A_dn None: det(A_up[S])^2; single_det: det(A_up[S])). out_c / out_minors /
+    workspace may pass preallocated tensors."""
+    A_up = _mat_batch(A_up, name="A_up")
+    b, n, _ = A_up.shape
+    if A_dn is not None:
+        A_dn = _mat_batch(A_dn, name="A_dn")
+        if A_dn.shape != A_up.shape:
+            raise ValueError("A_dn must match A_up")
+    dev = A_up.device
+    c = out_c if out_c is not None else torch.empty((b, 1 << n), dtype=torch.float64, device=dev)
+    mo = None
+    if return_minors or out_minors is not None:
+        shape = (b, 2, 1 << n) if A_dn is not None else (b, 1 << n)
+        mo = out_minors if out_minors is not None else torch.empty(shape, dtype=torch.float64,
+                                                                   device=dev)
+        if tuple(mo.shape) != shape or not mo.is_contiguous() or mo.dtype != torch.float64:
+            raise ValueError("out_minors has the wrong shape/dtype")
+    if tuple(c.shape) != (b, 1 << n) or not c.is_contiguous() or c.dtype != torch.float64:
+        raise ValueError("out_c has the wrong shape/dtype")
+    st = torch.zeros(b, dtype=torch.int32, device=dev) if return_status else None
+    if workspace is not None:
+        ws, nb = workspace, workspace.numel()
+    else:
+        ws, nb = _workspace(OP_CDET, n, b, dev, A_dn is not None)
+    flags = CDET_SINGLE_DET if single_det else 0
+    _check(lib().apm_cdet_connected(_ptr(A_up), _ptr(A_dn), n, b, flags, _ptr(c), _ptr(mo),
+                                    _opts(piv_threshold, piv_shift), _ptr(st), _ptr(ws), nb,
+                                    _stream(A_up)), "apm_cdet_connected")
+    res = [c]
+    if return_minors:
+        res.append(mo)
+    if return_status:
+        res.append(st)
+    return res[0] if len(res) == 1 else tuple(res)
+
+
+def cdet_from_weights(a: torch.Tensor):
+    """Eq. recursion applied to given weights a (batch, 2^n)."""
+    if not a.is_cuda or a.dtype != torch.float64:
+        raise TypeError("a must be a CUDA float64 tensor")
+    if a.dim() == 1:
+        a = a.unsqueeze(0)
+    a = a.contiguous()
+    b, N = a.shape
+    n = N.bit_length() - 1
+    if 1 << n != N:
+        raise ValueError("last dimension must be 2^n")
+    c = torch.empty_like(a)
+    ws, nb = _workspace(OP_CDET_FROM_WEIGHTS, n, b, a.device)
+    _check(lib().apm_cdet_from_weights(_ptr(a), n, b, _ptr(c), _ptr(ws), nb, _stream(a)),
+           "apm_cdet_from_weights")
+    return c
+
+
+def keldysh_sum(Mt: torch.Tensor, signed=False, partial=False, return_status=False):
+    """Sum over the 2^n Keldysh assignments; Mt (batch, 2n, 2n) complex128."""
+    Mt = _mat_batch(Mt, torch.complex128, "Mt")
+    b, n2, _ = Mt.shape
+    if n2 % 2:
+        raise ValueError("Mt must be 2n x 2n")
+    n = n2 // 2
+    dev = Mt.device
+    s = torch.empty((b, 2), dtype=torch.float64, device=dev)
+    p = torch.empty((b, n + 1, 2), dtype=torch.float64, device=dev) if partial else None
+    st = torch.zeros(b, dtype=torch.int32, device=dev) if return_status else None
+    _check(lib().apm_keldysh_sum(_ptr(Mt), n, b, KELDYSH_SIGNED if signed else 0, _ptr(s), _ptr(p),
+                                 _ptr(st), _stream(Mt)), "apm_keldysh_sum")
+    res = [torch.view_as_complex(s)]
+    if partial:
+        res.append(torch.view_as_complex(p))
+    if return_status:
+        res.append(st)
+    return res[0] if len(res) == 1 else tuple(res)
+
+
+def perm_minors(A: torch.Tensor):
+    """All 2^n permanent principal minors of A (batch, n, n) float64."""
+    A = _mat_batch(A)
+    b, n, _ = A.shape
+    out = torch.empty((b, 1 << n), dtype=torch.float64, device=A.device)
+    ws, nb = _workspace(OP_PERM_MINORS, n, b, A.device)
+    _check(lib().apm_perm_minors(_ptr(A), n, b, _ptr(out), _ptr(ws), nb, _stream(A)),
+           "apm_perm_minors")
+    return out
+
+
+def status_reduce(status: torch.Tensor) -> tuple[int, int]:
+    """(return code, OR of bits) of a per-matrix status tensor; synchronises."""
+    bits = ctypes.c_uint32(0)
+    code = lib().apm_status_reduce(_ptr(status), status.numel(), ctypes.byref(bits), _stream(status))
+    return code, int(bits.value)
+
+
+def fp64_probe(blocks: int, threads: int, iters: int, device="cuda") -> torch.Tensor:
+    sink = torch.empty(blocks * threads, dtype=torch.float64, device=device)
+    _check(lib().apm_fp64_fma_probe(_ptr(sink), blocks, threads, iters, _stream(sink)),
+           "apm_fp64_fma_probe")
+    return sink

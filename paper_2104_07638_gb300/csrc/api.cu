@@ -1,0 +1,182 @@
+// C-ABI entry points of libapm.so: argument validation on the host, then one
+// asynchronous launch on the caller's stream. See include/apm.h.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdlib.h>
+
+#include <vector>
+
+#include "apm_internal.cuh"
+
+namespace {
+
+thread_local int t_last_cuda = 0;
+
+apm_status_t cuda_fail(int e) {
+    t_last_cuda = e;
+    return APM_ERR_CUDA;
+}
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+apm_status_t check_ptr(const void *p, int64_t batch) {
+    if (batch == 0) return APM_OK;
+    if (!p || !aligned16(p)) return APM_ERR_ARG;
+    return APM_OK;
+}
+
+apm_status_t check_opt_ptr(const void *p) {
+    if (p && !aligned16(p)) return APM_ERR_ARG;
+    return APM_OK;
+}
+
+void pivot_values(const apm_pivot_opts *opt, double *thr, double *shift) {
+    *thr = opt ? opt->piv_threshold : APM_DEFAULT_PIV_THRESHOLD;
+    *shift = opt ? opt->piv_shift : APM_DEFAULT_PIV_SHIFT;
+}
+
+apm_status_t cdet_common(apm::CdetArgs &a, void *workspace, size_t workspace_bytes,
+                         cudaStream_t s) {
+    if (a.batch == 0) return APM_OK;
+    const bool two = a.two_mats != 0;
+    const bool smem_arrays = a.n <= apm::cdet_smem_max_n(two);
+    if (!smem_arrays) {
+        int err = 0;
+        const int grid = apm::cdet_grid(a.n, a.batch, two, false, &err);
+        if (err) return cuda_fail(err);
+        const size_t need = static_cast<size_t>(grid) * apm::cdet_slot_doubles(a.n) * sizeof(double);
+        if (!workspace || workspace_bytes < need || !aligned16(workspace)) return APM_ERR_WORKSPACE;
+        a.gscratch = static_cast<double *>(workspace);
+    }
+    const int e = apm::launch_fpm_cdet(a, s);
+    return e ? cuda_fail(e) : APM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+apm_status_t apm_all_minors(const double *A, int n, int64_t batch, double *minors,
+                            const apm_pivot_opts *opt, uint32_t *status, void *workspace,
+                            size_t workspace_bytes, apm_stream_t stream) {
+    if (n < 1 || n > APM_MAX_N_MINORS) return APM_ERR_UNSUPPORTED_N;
+    if (batch < 0) return APM_ERR_ARG;
+    apm_status_t st;
+    if ((st = check_ptr(A, batch)) || (st = check_ptr(minors, batch)) || (st = check_opt_ptr(status)))
+        return st;
+    apm::CdetArgs a = {};
+    a.A_up = A;
+    a.minors_out = minors;
+    a.status = status;
+    a.batch = batch;
+    a.n = n;
+    a.mode = apm::kModeMinors;
+    pivot_values(opt, &a.piv_thr, &a.piv_shift);
+    return cdet_common(a, workspace, workspace_bytes, reinterpret_cast<cudaStream_t>(stream));
+}
+
+apm_status_t apm_cdet_connected(const double *A_up, const double *A_dn, int n, int64_t batch,
+                                int flags, double *c, double *minors_out,
+                                const apm_pivot_opts *opt, uint32_t *status, void *workspace,
+                                size_t workspace_bytes, apm_stream_t stream) {
+    if (n < 1 || n > APM_MAX_N_MINORS) return APM_ERR_UNSUPPORTED_N;
+    if (batch < 0 || (flags & ~APM_CDET_SINGLE_DET)) return APM_ERR_ARG;
+    if ((flags & APM_CDET_SINGLE_DET) && A_dn) return APM_ERR_ARG;
+    apm_status_t st;
+    if ((st = check_ptr(A_up, batch)) || (st = check_opt_ptr(A_dn)) || (st = check_ptr(c, batch)) ||
+        (st = check_opt_ptr(minors_out)) || (st = check_opt_ptr(status)))
+        return st;
+    apm::CdetArgs a = {};
+    a.A_up = A_up;
+    a.A_dn = A_dn;
+    a.minors_out = minors_out;
+    a.c_out = c;
+    a.status = status;
+    a.batch = batch;
+    a.n = n;
+    a.mode = apm::kModeCdet;
+    a.single_det = (flags & APM_CDET_SINGLE_DET) ? 1 : 0;
+    a.two_mats = A_dn ? 1 : 0;
+    pivot_values(opt, &a.piv_thr, &a.piv_shift);
+    return cdet_common(a, workspace, workspace_bytes, reinterpret_cast<cudaStream_t>(stream));
+}
+
+apm_status_t apm_cdet_from_weights(const double *a_in, int n, int64_t batch, double *c,
+                                   void *workspace, size_t workspace_bytes, apm_stream_t stream) {
+    if (n < 1 || n > APM_MAX_N_MINORS) return APM_ERR_UNSUPPORTED_N;
+    if (batch < 0) return APM_ERR_ARG;
+    apm_status_t st;
+    if ((st = check_ptr(a_in, batch)) || (st = check_ptr(c, batch))) return st;
+    apm::CdetArgs a = {};
+    a.a_in = a_in;
+    a.c_out = c;
+    a.batch = batch;
+    a.n = n;
+    a.mode = apm::kModeWeights;
+    return cdet_common(a, workspace, workspace_bytes, reinterpret_cast<cudaStream_t>(stream));
+}
+
+apm_status_t apm_workspace_size(int op, int n_max, int64_t batch, int two_mats, size_t *bytes) {
+    if (!bytes || batch < 0) return APM_ERR_ARG;
+    *bytes = 0;
+    switch (op) {
+        case APM_OP_ALL_MINORS:
+        case APM_OP_CDET:
+        case APM_OP_CDET_FROM_WEIGHTS: {
+            if (n_max < 1 || n_max > APM_MAX_N_MINORS) return APM_ERR_UNSUPPORTED_N;
+            const bool two = op == APM_OP_CDET && two_mats;
+            if (n_max <= apm::cdet_smem_max_n(two) || batch == 0) return APM_OK;
+            int err = 0;
+            const int grid = apm::cdet_grid(n_max, batch, two, false, &err);
+            if (err) return cuda_fail(err);
+            *bytes = static_cast<size_t>(grid) * apm::cdet_slot_doubles(n_max) * sizeof(double);
+            return APM_OK;
+        }
+        default:
+            return APM_ERR_ARG;
+    }
+}
+
+apm_status_t apm_status_reduce(const uint32_t *status_dev, int64_t batch, uint32_t *or_bits,
+                               apm_stream_t stream) {
+    if (!or_bits || batch < 0 || (batch > 0 && !status_dev)) return APM_ERR_ARG;
+    *or_bits = 0;
+    if (batch == 0) return APM_OK;
+    std::vector<uint32_t> host(static_cast<size_t>(batch));
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(host.data(), status_dev, host.size() * sizeof(uint32_t),
+                                    cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    uint32_t acc = 0;
+    for (uint32_t v : host) acc |= v;
+    *or_bits = acc;
+    return (acc & APM_ST_ERROR_MASK) ? APM_ERR_NUMERIC : APM_OK;
+}
+
+const char *apm_status_string(apm_status_t s) {
+    switch (s) {
+        case APM_OK: return "APM_OK";
+        case APM_ERR_ARG: return "APM_ERR_ARG: invalid argument (null, misaligned, negative or bad flags)";
+        case APM_ERR_UNSUPPORTED_N: return "APM_ERR_UNSUPPORTED_N: order outside the supported range";
+        case APM_ERR_CUDA: return "APM_ERR_CUDA: a CUDA call failed";
+        case APM_ERR_NUMERIC: return "APM_ERR_NUMERIC: a matrix has an error status bit";
+        case APM_ERR_TIMEOUT: return "APM_ERR_TIMEOUT: a bounded device wait gave up";
+        case APM_ERR_WORKSPACE: return "APM_ERR_WORKSPACE: workspace missing or too small";
+    }
+    return "APM_UNKNOWN";
+}
+
+int apm_last_cuda_error(void) { return t_last_cuda; }
+
+int apm_version(void) { return 100; }
+
+apm_status_t apm_fp64_fma_probe(double *sink, int blocks, int threads, int iters,
+                                apm_stream_t stream) {
+    if (!sink || blocks < 1 || threads < 32 || threads > 1024 || iters < 1) return APM_ERR_ARG;
+    const int e = apm::launch_fp64_probe(sink, blocks, threads, iters,
+                                         reinterpret_cast<cudaStream_t>(stream));
+    return e ? cuda_fail(e) : APM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,58 @@
+// Internal declarations shared by the translation units of libapm.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/apm.h"
+
+namespace apm {
+
+// Threads per CTA of the minor / connected-sum kernels.
+constexpr int kCdetThreads = 256;
+// Capacity of the per-matrix pivot-correction log.
+constexpr int kCorrCap = 256;
+
+// Largest order whose a[] and c[] arrays stay in shared memory.
+int cdet_smem_max_n(bool two_mats);
+
+// Bytes of dynamic shared memory of the minor / connected-sum kernel.
+size_t cdet_smem_bytes(int n, bool two_mats, bool smem_arrays);
+
+// Grid size used for a fixed-order launch (also sizes the workspace).
+int cdet_grid(int n, int64_t batch, bool two_mats, bool smem_arrays, int *err);
+
+// Doubles of global scratch one CTA uses when the arrays do not fit on chip.
+size_t cdet_slot_doubles(int n);
+
+enum CdetMode : int { kModeMinors = 0, kModeCdet = 1, kModeWeights = 2 };
+
+struct CdetArgs {
+    const double *A_up;
+    const double *A_dn;
+    const double *a_in;
+    double *minors_out;
+    double *c_out;
+    uint32_t *status;
+    double *gscratch;
+    int64_t batch;
+    int n;
+    int mode;
+    int single_det;
+    int two_mats;
+    double piv_thr;
+    double piv_shift;
+};
+
+// Launches the fused minors / connected-sum kernel. Returns a cudaError_t.
+int launch_fpm_cdet(const CdetArgs &a, cudaStream_t s);
+
+// Uploads the popcount-ordered mask table on the current device (idempotent).
+int ensure_tables();
+
+// Per-layer lane-group sizes (log2) chosen by the cost model for order n.
+void cdet_group_table(int n, int threads, uint8_t *gsel /*[17]*/);
+
+int launch_fp64_probe(double *sink, int blocks, int threads, int iters, cudaStream_t s);
+
+}  // namespace apm

@@ -1,0 +1,541 @@
+// Fused all-principal-minors (Schur-complement tree with pivot correction) and
+// CDet connected-sum recursion, FP64, one CTA per matrix, persistent over the
+// batch.
+//
+// Paper: Section II (Eq. dets_schur, lemma1, lemma2, Eq. minor, Alg. 1, the
+// pivot-correction paragraph and the depth-first remark), Section V.A
+// (a[S] = det M_up[S] det M_dn[S], Eq. recursion).
+//
+// Layout on chip (doubles, for n <= 12 in shared memory, else in per-CTA global
+// scratch):  MA[2^n]  minors, then a[]      MC[max(2^n,16)]  tree scratch, then c[]
+//            MU[2^n]  (only with a separate A_dn) minors of A_dn
+//
+// Minors (per matrix):
+//   The tree node of mask m over the elements < l holds the Schur complement of
+//   A with respect to A[m], restricted to the elements l..n-1 (size (n-l)^2).
+//   Its (1,1) entry p gives det A[m | {l}] = det A[m] * p (Eq. minor). The left
+//   child (element l excluded) is the same matrix without its first row and
+//   column; the right child (l included) is its Schur complement with respect
+//   to p. Levels 0..L-1 (L = n-4) are expanded breadth first across the CTA,
+//   one child entry per thread step; the 2^L nodes of level L (4x4 each) are
+//   finished by one thread each with closed-form 1x1..4x4 determinants, which
+//   needs no pivot at all. Level buffers alternate between MC and the not yet
+//   written upper part of MA, so the tree needs no memory beyond MA and MC.
+//   Pivot correction: a pivot with |p| <= thr is shifted by C; the node's minor
+//   is stored with p + C and the right subtree is built from the shifted
+//   matrix. The shift equals adding C to A_ll for every mask of that subtree, so
+//   by linearity in row l the exact minors follow from
+//       det[m] = det~[m] - C det[m \ {l}]
+//   for the node itself and every mask of its right subtree, applied deepest
+//   level first (a shallower correction must see deeper ones already removed).
+//
+// Connected sums: popcount layers k = 2..n in order (every proper subset of a
+// k-set lies in an earlier layer). For S with lowest element j and
+// S' = S \ {j}, c[S] = a[S] - sum_{U proper subset of S'} c[{j} u U] a[S' \ U].
+// A group of g lanes (g = 2^r chosen per layer by a cost model) shares one S:
+// lane t fixes the lowest r elements of S' to the bits of t and walks the
+// submasks of the rest; the group sum is reduced with warp shuffles.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "apm_internal.cuh"
+
+namespace apm {
+
+__device__ uint16_t g_popmasks[1 << 16];  // masks < 2^16 ordered by (popcount, value)
+__device__ int g_popoff[18];              // first index of each popcount class
+__constant__ int c_binom[17][17];
+
+struct __align__(16) CdetSmemHdr {
+    double log_c[kCorrCap];
+    int log_x[kCorrCap];
+    int log_l[kCorrCap];
+    double red[kCdetThreads / 32];
+    unsigned long long red_u[kCdetThreads / 32];
+    int ncorr;
+    int flags;
+    double anorm;
+};
+
+// doubles of global scratch per CTA slot: MA, MC, MU
+__host__ __device__ inline size_t slot_doubles(int n) {
+    const size_t N = size_t(1) << n;
+    return 2 * N + (N > 16 ? N : 16);
+}
+
+struct CdetKernelParams {
+    CdetArgs a;
+    unsigned long long gsel;  // 3 bits per popcount layer k: log2 of the lane-group size
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Bulk (TMA engine) copy of `bytes` from shared to global memory; issued by one
+// thread after a CTA barrier that ordered the shared-memory writes.
+__device__ __forceinline__ void bulk_store(double *gdst, const double *ssrc, uint32_t bytes) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst),
+                 "r"(smem_u32(ssrc)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_read() {
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() {
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+
+// max |A_ij| and finiteness of one n x n matrix, on integer bit patterns (the
+// magnitude order of finite doubles is the order of their bits without sign).
+__device__ __forceinline__ void matrix_norm(const double *__restrict__ Ag, int n, CdetSmemHdr &h) {
+    const int tid = threadIdx.x;
+    unsigned long long mx = 0ull;
+    int bad = 0;
+    for (int i = tid; i < n * n; i += blockDim.x) {
+        unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(__ldg(Ag + i)));
+        u &= 0x7fffffffffffffffull;
+        if (u >= 0x7ff0000000000000ull) bad = 1;
+        else if (u > mx) mx = u;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long v = __shfl_xor_sync(0xffffffffu, mx, o);
+        mx = v > mx ? v : mx;
+    }
+    bad = __any_sync(0xffffffffu, bad);
+    if ((tid & 31) == 0) {
+        h.red_u[tid >> 5] = mx;
+        if (bad) atomicOr(&h.flags, APM_ST_NONFINITE_INPUT);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        unsigned long long m = 0ull;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = h.red_u[w] > m ? h.red_u[w] : m;
+        double an = __longlong_as_double(static_cast<long long>(m));
+        h.anorm = an > 0.0 ? an : 1.0;
+    }
+    __syncthreads();
+}
+
+// Node bookkeeping when a BFS-level matrix's (1,1) entry v is final: store the
+// node's minor det[x | {lev}] = det[x] * p (Eq. minor), correct p if it is
+// tiny, and replace v by 1/p for the Schur step of the next level.
+__device__ __forceinline__ void node_pivot(int x, int lev, double &v, double *MA, double thr,
+                                           double shift, CdetSmemHdr &h) {
+    double piv = v;
+    if (fabs(piv) <= thr) {
+        const double cs = piv >= 0.0 ? shift : -shift;
+        piv += cs;
+        const int slot = atomicAdd(&h.ncorr, 1);
+        if (slot < kCorrCap) {
+            h.log_x[slot] = x;
+            h.log_l[slot] = lev;
+            h.log_c[slot] = cs;
+        }
+    }
+    MA[x | (1 << lev)] = MA[x] * piv;
+    v = 1.0 / piv;
+}
+
+// All 15 principal minors of a 4x4 matrix w (row-major) times `pre`, written to
+// MA[m | X << L] for X = 1 .. 2^s - 1 (s = min(n,4)); closed-form cofactor and
+// Laplace expansions, no division.
+__device__ __forceinline__ void bottom4(const double *__restrict__ w, double pre, double *MA, int m,
+                                        int L, int s) {
+    const double a = w[0], b = w[1], c = w[2], d = w[3];
+    const double e = w[4], f = w[5], g = w[6], hh = w[7];
+    const double i = w[8], j = w[9], k = w[10], l = w[11];
+    const double mm = w[12], nn = w[13], o = w[14], p = w[15];
+    // 2x2 principal
+    const double d01 = fma(a, f, -b * e);
+    const double d02 = fma(a, k, -c * i);
+    const double d03 = fma(a, p, -d * mm);
+    const double d12 = fma(f, k, -g * j);
+    const double d13 = fma(f, p, -hh * nn);
+    const double d23 = fma(k, p, -l * o);
+    // off-principal 2x2 minors used by the 3x3 and 4x4 expansions
+    const double ek_gi = fma(e, k, -g * i);
+    const double ej_fi = fma(e, j, -f * i);
+    const double ep_hm = fma(e, p, -hh * mm);
+    const double en_fm = fma(e, nn, -f * mm);
+    const double ip_lm = fma(i, p, -l * mm);
+    const double io_km = fma(i, o, -k * mm);
+    const double jp_ln = fma(j, p, -l * nn);
+    const double jo_kn = fma(j, o, -k * nn);
+    // 3x3 principal (cofactor expansion along the first row of each subset)
+    const double d012 = fma(a, d12, fma(-b, ek_gi, c * ej_fi));
+    const double d013 = fma(a, d13, fma(-b, ep_hm, d * en_fm));
+    const double d023 = fma(a, d23, fma(-c, ip_lm, d * io_km));
+    const double d123 = fma(f, d23, fma(-g, jp_ln, hh * jo_kn));
+    // 4x4 by Laplace expansion along rows 0,1
+    const double s02 = fma(a, g, -c * e);
+    const double s03 = fma(a, hh, -d * e);
+    const double s12 = fma(b, g, -c * f);
+    const double s13 = fma(b, hh, -d * f);
+    const double s23 = fma(c, hh, -d * g);
+    const double c01 = fma(i, nn, -j * mm);
+    double d0123 = d01 * d23;
+    d0123 = fma(-s02, jp_ln, d0123);
+    d0123 = fma(s03, jo_kn, d0123);
+    d0123 = fma(s12, ip_lm, d0123);
+    d0123 = fma(-s13, io_km, d0123);
+    d0123 = fma(s23, c01, d0123);
+    MA[m | (1 << L)] = pre * a;
+    if (s < 2) return;
+    MA[m | (2 << L)] = pre * f;
+    MA[m | (3 << L)] = pre * d01;
+    if (s < 3) return;
+    MA[m | (4 << L)] = pre * k;
+    MA[m | (5 << L)] = pre * d02;
+    MA[m | (6 << L)] = pre * d12;
+    MA[m | (7 << L)] = pre * d012;
+    if (s < 4) return;
+    MA[m | (8 << L)] = pre * p;
+    MA[m | (9 << L)] = pre * d03;
+    MA[m | (10 << L)] = pre * d13;
+    MA[m | (11 << L)] = pre * d013;
+    MA[m | (12 << L)] = pre * d23;
+    MA[m | (13 << L)] = pre * d023;
+    MA[m | (14 << L)] = pre * d123;
+    MA[m | (15 << L)] = pre * d0123;
+}
+
+// All principal minors of the n x n matrix Ag into MA[0 .. 2^n), MC as scratch.
+__device__ __forceinline__ void fpm_tree(const double *__restrict__ Ag, int n, double *MA, double *MC, double thr,
+                         double shift, CdetSmemHdr &h) {
+    const int tid = threadIdx.x, T = blockDim.x;
+    const int L = n > 4 ? n - 4 : 0;
+    double *const bufA = MA + (1 << L);
+    // level-l buffer: MC when L-l is even, else the upper part of MA
+#define APM_BUF(lv) ((((L) - (lv)) & 1) ? bufA : MC)
+    double *W0 = APM_BUF(0);
+    if (n >= 4) {
+        for (int t = tid; t < n * n; t += T) W0[t] = __ldg(Ag + t);
+    } else {
+        for (int t = tid; t < 16; t += T) {
+            const int r = t >> 2, q = t & 3;
+            W0[t] = (r < n && q < n) ? __ldg(Ag + r * n + q) : (r == q ? 1.0 : 0.0);
+        }
+    }
+    if (tid == 0) MA[0] = 1.0;
+    __syncthreads();
+    if (L > 0 && tid == 0) {
+        double v = W0[0];
+        node_pivot(0, 0, v, MA, thr, shift, h);
+        W0[0] = v;
+    }
+    __syncthreads();
+    for (int l = 0; l < L; ++l) {
+        const int s = n - l, s1 = s - 1, ss = s * s, ss1 = s1 * s1, P = 1 << l;
+        const double *Wl = APM_BUF(l);
+        double *Wn = APM_BUF(l + 1);
+        const int E = 2 * P * ss1;
+        const bool pivot_next = (l + 1) < L;
+        for (int e = tid; e < E; e += T) {
+            const int x = e / ss1;
+            const int rem = e - x * ss1;
+            const int p = rem / s1;
+            const int q = rem - p * s1;
+            const double *Wp = Wl + (x & (P - 1)) * ss;
+            double v = Wp[(p + 1) * s + q + 1];
+            if (x >> l) {  // right child: Schur complement w.r.t. the pivot (Wp[0] holds 1/p)
+                const double t = Wp[(p + 1) * s] * Wp[0];
+                v = fma(-t, Wp[q + 1], v);
+            }
+            if (rem == 0 && pivot_next) node_pivot(x, l + 1, v, MA, thr, shift, h);
+            Wn[x * ss1 + rem] = v;
+        }
+        __syncthreads();
+    }
+    const double *WL = APM_BUF(L);
+#undef APM_BUF
+    const int s = n < 4 ? n : 4;
+    for (int m = tid; m < (1 << L); m += T) bottom4(WL + m * 16, MA[m], MA, m, L, s);
+    __syncthreads();
+    // back-propagation of pivot corrections, deepest level first (the log is in
+    // non-decreasing level order because each level's pivots are logged in the
+    // tree step that precedes it)
+    const int nc = h.ncorr;
+    if (nc > kCorrCap) {
+        for (int t = tid; t < (1 << n); t += T) MA[t] = __longlong_as_double(0x7ff8000000000000ll);
+        if (tid == 0) h.flags |= APM_ST_CORRECTION_OVERFLOW;
+        __syncthreads();
+        return;
+    }
+    for (int ci = nc - 1; ci >= 0; --ci) {
+        const int x = h.log_x[ci], lv = h.log_l[ci];
+        const double cs = h.log_c[ci];
+        const int cnt = 1 << (n - lv - 1);
+        for (int t = tid; t < cnt; t += T) {
+            const int src = x | (t << (lv + 1));
+            const int tgt = src | (1 << lv);
+            MA[tgt] = fma(-cs, MA[src], MA[tgt]);
+        }
+        __syncthreads();
+    }
+    if (nc > 0 && tid == 0) h.flags |= APM_ST_PIVOT_CORRECTED;
+}
+
+// Connected sums from a[] (MA) into c[] (MC).
+__device__ __forceinline__ void cdet_layers(const double *a, double *c, int n, unsigned long long gsel) {
+    const int tid = threadIdx.x, T = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nw = T >> 5;
+    for (int x = tid; x < n; x += T) c[1 << x] = a[1 << x];
+    if (tid == 0) c[0] = 0.0;
+    __syncthreads();
+    for (int k = 2; k <= n; ++k) {
+        const int cnt = c_binom[n][k];
+        const uint16_t *masks = g_popmasks + g_popoff[k];
+        const int r = static_cast<int>((gsel >> (3 * k)) & 7ull);
+        const int spw = 32 >> r;  // sets per warp step
+        const int gl = lane & ((1 << r) - 1);
+        for (int base = warp * spw; base < cnt; base += nw * spw) {
+            const int G = base + (lane >> r);
+            const bool act = G < cnt;
+            const int S = masks[act ? G : cnt - 1];
+            const int j = S & (-S);
+            const int Sp = S ^ j;
+            int UL = 0, low = 0, tmp = Sp;
+            for (int i = 0; i < r; ++i) {
+                const int bt = tmp & (-tmp);
+                tmp ^= bt;
+                low |= bt;
+                if ((gl >> i) & 1) UL |= bt;
+            }
+            const int H = Sp ^ low;
+            double acc0 = 0.0, acc1 = 0.0;
+            int UH = H;
+            while (true) {
+                int U = UL | UH;
+                if (U != Sp) acc0 = fma(c[j | U], a[Sp ^ U], acc0);
+                if (UH == 0) break;
+                UH = (UH - 1) & H;
+                U = UL | UH;
+                acc1 = fma(c[j | U], a[Sp ^ U], acc1);
+                if (UH == 0) break;
+                UH = (UH - 1) & H;
+            }
+            double acc = acc0 + acc1;
+            for (int o = (1 << r) >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (act && gl == 0) c[S] = a[S] - acc;
+        }
+        __syncthreads();
+    }
+}
+
+template <bool kSmemArrays>
+__global__ void __launch_bounds__(kCdetThreads) fpm_cdet_kernel(const CdetKernelParams P) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    CdetSmemHdr &h = *reinterpret_cast<CdetSmemHdr *>(smem_raw);
+    const CdetArgs &p = P.a;
+    const int n = p.n;
+    const int N = 1 << n;
+    const int NC = N > 16 ? N : 16;
+    const int tid = threadIdx.x;
+    double *base;
+    if (kSmemArrays)
+        base = reinterpret_cast<double *>(smem_raw + ((sizeof(CdetSmemHdr) + 127) & ~size_t(127)));
+    else
+        base = p.gscratch + static_cast<size_t>(blockIdx.x) * slot_doubles(n);
+    double *MA = base;
+    double *MC = base + N;
+    double *MU = MC + NC;
+
+    for (int64_t b = blockIdx.x; b < p.batch; b += gridDim.x) {
+        if (kSmemArrays && tid == 0) bulk_wait_read();  // previous matrix's stores
+        if (tid == 0) {
+            h.ncorr = 0;
+            h.flags = 0;
+        }
+        __syncthreads();
+        const int64_t mat = static_cast<int64_t>(n) * n;
+        if (p.mode == kModeWeights) {
+            const double *ag = p.a_in + b * N;
+            for (int t = tid; t < N; t += blockDim.x) MA[t] = __ldg(ag + t);
+            __syncthreads();
+        } else {
+            if (p.two_mats) {
+                const double *Ad = p.A_dn + b * mat;
+                matrix_norm(Ad, n, h);
+                fpm_tree(Ad, n, MA, MC, p.piv_thr * h.anorm, p.piv_shift * h.anorm, h);
+                for (int t = tid; t < N; t += blockDim.x) MU[t] = MA[t];
+                if (tid == 0) h.ncorr = 0;
+                __syncthreads();
+            }
+            const double *Au = p.A_up + b * mat;
+            matrix_norm(Au, n, h);
+            fpm_tree(Au, n, MA, MC, p.piv_thr * h.anorm, p.piv_shift * h.anorm, h);
+            // minors out
+            if (p.minors_out) {
+                double *mo = p.minors_out + b * (p.two_mats ? 2 * N : N);
+                if (kSmemArrays) {
+                    if (tid == 0) {
+                        bulk_store(mo, MA, N * 8u);
+                        if (p.two_mats) bulk_store(mo + N, MU, N * 8u);
+                        bulk_wait_read();
+                    }
+                } else {
+                    for (int t = tid; t < N; t += blockDim.x) {
+                        mo[t] = MA[t];
+                        if (p.two_mats) mo[N + t] = MU[t];
+                    }
+                }
+            }
+            if (tid == 0 && p.status) p.status[b] = static_cast<uint32_t>(h.flags);
+            __syncthreads();
+            if (p.mode == kModeMinors) continue;
+            // weights a[S]
+            if (!p.single_det) {
+                if (p.two_mats)
+                    for (int t = tid; t < N; t += blockDim.x) MA[t] *= MU[t];
+                else
+                    for (int t = tid; t < N; t += blockDim.x) MA[t] *= MA[t];
+            }
+            __syncthreads();
+        }
+        cdet_layers(MA, MC, n, P.gsel);
+        double *co = p.c_out + b * N;
+        if (kSmemArrays) {
+            if (tid == 0) bulk_store(co, MC, N * 8u);
+        } else {
+            for (int t = tid; t < N; t += blockDim.x) co[t] = MC[t];
+        }
+        // the next matrix's first barrier orders these reads before any overwrite
+    }
+    if (kSmemArrays && tid == 0) bulk_wait_all();
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+static inline size_t hdr_bytes() { return (sizeof(CdetSmemHdr) + 127) & ~size_t(127); }
+
+size_t cdet_slot_doubles(int n) { return slot_doubles(n); }
+
+size_t cdet_smem_bytes(int n, bool two_mats, bool smem_arrays) {
+    if (!smem_arrays) return hdr_bytes();
+    const size_t N = size_t(1) << n;
+    return hdr_bytes() + 8 * ((two_mats ? 2 : 1) * N + (N > 16 ? N : 16));
+}
+
+int cdet_smem_max_n(bool two_mats) {
+    int best = 0;
+    for (int n = 1; n <= 16; ++n)
+        if (cdet_smem_bytes(n, two_mats, true) <= 227 * 1024) best = n;
+    return best;
+}
+
+void cdet_group_table(int n, int threads, uint8_t *gsel) {
+    // Per popcount layer k: choose the group size g = 2^r lanes per set that
+    // minimises the FP64 warp-instructions of the layer,
+    //   ceil(C(n,k) g / 32) * (2^{k-1-r} + r + 1),
+    // breaking near-ties (within 3%) toward larger groups, whose lanes read
+    // neighbouring subsets (fewer shared-memory bank conflicts).
+    (void)threads;
+    for (int k = 0; k <= 16; ++k) gsel[k] = 0;
+    double binom[17][17] = {};
+    for (int a = 0; a <= 16; ++a) {
+        binom[a][0] = 1;
+        for (int b = 1; b <= a; ++b) binom[a][b] = binom[a - 1][b - 1] + (b <= a - 1 ? binom[a - 1][b] : 0);
+    }
+    for (int k = 2; k <= n; ++k) {
+        const double cnt = binom[n][k];
+        double best = 1e300;
+        int rb = 0;
+        double cost[6];
+        const int rmax = (k - 1) < 5 ? (k - 1) : 5;
+        for (int r = 0; r <= rmax; ++r) {
+            const double tasks = ceil(cnt * double(1 << r) / 32.0);
+            cost[r] = tasks * (double(1 << (k - 1 - r)) + r + 1);
+            if (cost[r] < best) { best = cost[r]; rb = r; }
+        }
+        for (int r = rmax; r > rb; --r)
+            if (cost[r] <= best * 1.03) { rb = r; break; }
+        gsel[k] = static_cast<uint8_t>(rb);
+    }
+}
+
+int cdet_grid(int n, int64_t batch, bool two_mats, bool smem_arrays, int *err) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t smem = cdet_smem_bytes(n, two_mats, smem_arrays);
+    if (e == cudaSuccess) {
+        if (smem_arrays) {
+            e = cudaFuncSetAttribute(fpm_cdet_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     static_cast<int>(smem));
+            if (e == cudaSuccess)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fpm_cdet_kernel<true>,
+                                                                  kCdetThreads, smem);
+        } else {
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fpm_cdet_kernel<false>,
+                                                              kCdetThreads, smem);
+            if (per_sm > 2) per_sm = 2;  // bounds the scratch and keeps it L2-resident
+        }
+    }
+    if (e != cudaSuccess || per_sm < 1) {
+        if (err) *err = e != cudaSuccess ? static_cast<int>(e) : static_cast<int>(cudaErrorInvalidConfiguration);
+        return 0;
+    }
+    if (err) *err = 0;
+    int64_t g = static_cast<int64_t>(sms) * per_sm;
+    if (batch < g) g = batch;
+    return static_cast<int>(g < 1 ? 1 : g);
+}
+
+int ensure_tables() {
+    static int done_mask = 0;  // bit per device id < 32
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 32 && (done_mask >> dev) & 1) return 0;
+    static uint16_t masks[1 << 16];
+    int off[18];
+    int pos = 0;
+    for (int k = 0; k <= 16; ++k) {
+        off[k] = pos;
+        for (int S = 0; S < (1 << 16); ++S)
+            if (__builtin_popcount(static_cast<unsigned>(S)) == k) masks[pos++] = static_cast<uint16_t>(S);
+    }
+    off[17] = pos;
+    int binom[17][17] = {};
+    for (int a = 0; a <= 16; ++a) {
+        binom[a][0] = 1;
+        for (int b = 1; b <= a; ++b) binom[a][b] = binom[a - 1][b - 1] + (b <= a - 1 ? binom[a - 1][b] : 0);
+    }
+    e = cudaMemcpyToSymbol(g_popmasks, masks, sizeof(masks));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_popoff, off, sizeof(off));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_binom, binom, sizeof(binom));
+    if (e != cudaSuccess) return e;
+    if (dev < 32) done_mask |= 1 << dev;
+    return 0;
+}
+
+int launch_fpm_cdet(const CdetArgs &a, cudaStream_t s) {
+    int err = ensure_tables();
+    if (err) return err;
+    CdetKernelParams P;
+    P.a = a;
+    uint8_t gsel[17];
+    cdet_group_table(a.n, kCdetThreads, gsel);
+    P.gsel = 0ull;
+    for (int k = 0; k <= 16; ++k) P.gsel |= static_cast<unsigned long long>(gsel[k] & 7) << (3 * k);
+    const bool smem_arrays = a.n <= cdet_smem_max_n(a.two_mats != 0);
+    const int grid = cdet_grid(a.n, a.batch, a.two_mats != 0, smem_arrays, &err);
+    if (err) return err;
+    const size_t smem = cdet_smem_bytes(a.n, a.two_mats != 0, smem_arrays);
+    if (smem_arrays)
+        fpm_cdet_kernel<true><<<grid, kCdetThreads, smem, s>>>(P);
+    else
+        fpm_cdet_kernel<false><<<grid, kCdetThreads, smem, s>>>(P);
+    return static_cast<int>(cudaGetLastError());
+}
+
+}  // namespace apm

@@ -1,0 +1,57 @@
+"""Host-only checks of the C ABI: the library builds, loads without a GPU and
+exports every entry point that include/apm.h declares; argument errors are
+rejected on the host before any launch."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "apm.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(apm_[a-z0-9_]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2104_07638_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_four_paper_calls():
+    syms = declared_symbols()
+    for s in ("apm_all_minors", "apm_cdet_connected", "apm_keldysh_sum", "apm_perm_minors"):
+        assert s in syms
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [s for s in declared_symbols() if not hasattr(lib, s)]
+    assert not missing, missing
+
+
+def test_host_side_argument_errors(lib):
+    P, i32, i64, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_size_t
+    f = lib.apm_all_minors
+    f.argtypes = [P, i32, i64, P, P, P, P, sz, P]
+    f.restype = ctypes.c_int
+    fake = ctypes.c_void_p(1 << 20)           # never dereferenced: the call must fail first
+    assert f(fake, 0, 1, fake, None, None, None, 0, None) == 2      # n out of range
+    assert f(fake, 17, 1, fake, None, None, None, 0, None) == 2
+    assert f(fake, 8, -1, fake, None, None, None, 0, None) == 1     # negative batch
+    assert f(None, 8, 1, fake, None, None, None, 0, None) == 1      # null input
+    assert f(ctypes.c_void_p((1 << 20) + 8), 8, 1, fake, None, None, None, 0, None) == 1  # misaligned
+    assert f(None, 8, 0, None, None, None, None, 0, None) == 0      # empty batch: no launch
+    g = lib.apm_cdet_connected
+    g.argtypes = [P, P, i32, i64, i32, P, P, P, P, P, sz, P]
+    g.restype = ctypes.c_int
+    assert g(fake, fake, 8, 1, 1, fake, None, None, None, None, 0, None) == 1  # single-det with A_dn
+    assert g(fake, None, 8, 1, 4, fake, None, None, None, None, 0, None) == 1  # unknown flag
+    lib.apm_status_string.restype = ctypes.c_char_p
+    assert b"WORKSPACE" in lib.apm_status_string(6)
+    lib.apm_version.restype = ctypes.c_int
+    assert lib.apm_version() >= 100
