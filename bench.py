@@ -206,7 +206,7 @@ def main():
         apm.cdet_connected(A, out_c=c, out_minors=mo)
 
     # FP64 throughput probe (roofline context)
-    blocks, threads, iters = SMS * 8, 256, 4096
+    blocks, threads, iters = SMS * 4, 512, 2048
     apm.fp64_probe(blocks, threads, 64, dev)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -214,7 +214,7 @@ def main():
     apm.fp64_probe(blocks, threads, iters, dev)
     e1.record(stream)
     torch.cuda.synchronize()
-    probe_tflops = 16.0 * blocks * threads * iters / (e0.elapsed_time(e1) * 1e-3) / 1e12
+    probe_tflops = 32.0 * blocks * threads * iters / (e0.elapsed_time(e1) * 1e-3) / 1e12
 
     for _ in range(args.warmup):
         step()

@@ -203,10 +203,10 @@ int apm_version(void);
 /*
  * apm_fp64_fma_probe -- FP64 throughput microbenchmark (no counterpart in the
  * paper; it measures the roofline denominator of the FP64-bound kernels).
- * Launches `blocks` x `threads` threads, each running `iters` rounds of 8
+ * Launches `blocks` x `threads` threads, each running `iters` rounds of 16
  * independent dependent-chain FP64 fused multiply-adds; writes one double per
  * thread to `sink` (device, blocks*threads doubles) so nothing is optimised away.
- * FLOPs = 16 * blocks * threads * iters.
+ * FLOPs = 32 * blocks * threads * iters.
  */
 apm_status_t apm_fp64_fma_probe(double *sink, int blocks, int threads, int iters,
                                 apm_stream_t stream);

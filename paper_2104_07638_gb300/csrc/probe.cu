@@ -1,4 +1,4 @@
-// FP64 throughput microbenchmark: 8 independent fused-multiply-add chains per
+// FP64 throughput microbenchmark: 16 independent fused-multiply-add chains per
 // thread. It measures the denominator of the FP64 roofline of the minor and
 // connected-sum kernels (the chip's published FP64 rate is a nominal figure).
 #include <cuda_runtime.h>
@@ -9,20 +9,18 @@ namespace apm {
 
 __global__ void fp64_probe_kernel(double *sink, int iters) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    double x0 = 1e-9 * t, x1 = x0 + 1e-3, x2 = x0 + 2e-3, x3 = x0 + 3e-3;
-    double x4 = x0 + 4e-3, x5 = x0 + 5e-3, x6 = x0 + 6e-3, x7 = x0 + 7e-3;
+    double x[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) x[k] = 1e-9 * t + 1e-3 * k;
     const double a = 0.9999999, b = 1e-7;
     for (int i = 0; i < iters; ++i) {
-        x0 = fma(x0, a, b);
-        x1 = fma(x1, a, b);
-        x2 = fma(x2, a, b);
-        x3 = fma(x3, a, b);
-        x4 = fma(x4, a, b);
-        x5 = fma(x5, a, b);
-        x6 = fma(x6, a, b);
-        x7 = fma(x7, a, b);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) x[k] = fma(x[k], a, b);
     }
-    sink[t] = ((x0 + x1) + (x2 + x3)) + ((x4 + x5) + (x6 + x7));
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) s += x[k];
+    sink[t] = s;
 }
 
 int launch_fp64_probe(double *sink, int blocks, int threads, int iters, cudaStream_t s) {
