@@ -36,6 +36,11 @@ SMS = 152
 SM_MAX_MHZ = 2070.0
 FP64_FLOP_PER_CLK_SM = 4.0   # 1.25 TFLOP/s nominal FP64 / (152 SMs x 2.07 GHz), 2 DFMA/clk/SM
 METRIC = "minor-sets/sec at n=12 FP64 (% of roofline)"
+# DRAM bytes (read + write) per matrix of the fused kernel from one ncu capture
+# (profiles/fpm_cdet_n12_hubbard.md: 213.7 MB per 4096 matrices), valid only for
+# the kernel source it was taken on (sha256 prefix below).
+TRAFFIC_PER_SET = 213.7e6 / 4096
+TRAFFIC_SRC_SHA = "a7ca5ba3fddba388"
 UNIT = "minor-sets/s"
 
 
@@ -283,6 +288,10 @@ def main():
     # spot check of the end-to-end result against the device-timed one
     assert torch.equal(c_host[:4].to(dev), c[:4]) if rank == 0 else True
 
+    import hashlib
+    src = os.path.join(ROOT, "paper_2104_07638_gb300", "csrc", "fpm_cdet.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    traffic = TRAFFIC_PER_SET * B if sha == TRAFFIC_SRC_SHA else None
     F = flops_per_set(n)
     peak = FP64_FLOP_PER_CLK_SM * SMS * SM_MAX_MHZ * 1e6 / 1e12
     achieved = F * B / (ms_per_step * 1e-3) / 1e12
@@ -296,7 +305,8 @@ def main():
                    "l2": "256 MB buffer rewritten between timed steps (outside the events)",
                    "timing": "CUDA events around each step on the launching stream"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": traffic,
+                     "traffic_note": "DRAM bytes per launch scaled from a 4096-matrix ncu capture",
                      "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz "
                                     "(nominal 1.25 TFLOP/s FP64 at max clock)",
                      "flops_per_set": F, "fp64_probe_tflops": probe_tflops,
