@@ -153,9 +153,12 @@ apm_status_t apm_cdet_from_weights(const double *a, int n, int64_t batch, double
  *            Section V.D); partial[b][0] = 1, partial[b][n] = sum[b].
  *   status   [batch] or NULL; APM_ST_ZERO_PIVOT marks a zero or non-finite pivot,
  *            and then sum (and partial) of that matrix are NaN.
+ *   workspace / workspace_bytes: scratch for the depth-first part of the tree,
+ *            needed for n > 7 (apm_workspace_size with APM_OP_KELDYSH).
  */
 apm_status_t apm_keldysh_sum(const double *Mt, int n, int64_t batch, int flags, double *sum,
-                             double *partial, uint32_t *status, apm_stream_t stream);
+                             double *partial, uint32_t *status, void *workspace,
+                             size_t workspace_bytes, apm_stream_t stream);
 
 /*
  * apm_perm_minors -- all 2^n permanent principal minors perm(A[S]) in O(3^n)
@@ -164,6 +167,10 @@ apm_status_t apm_keldysh_sum(const double *Mt, int n, int64_t batch, int flags, 
  *     perm(A[S]) = (-1)^|S| sum_{T subset of S} (-1)^|T| prod_{i in S} r_i(T).
  *   A      [batch][n][n] float64.    perms  [batch][2^n] float64 output.
  *   n      1..APM_MAX_N_PERM.
+ *   workspace / workspace_bytes: unused (pass NULL, 0); kept for a uniform
+ *          signature with the other batched calls.
+ *   Summation order differs from run to run (products from different T are
+ *   accumulated with atomic adds), so results agree to rounding, not bitwise.
  */
 apm_status_t apm_perm_minors(const double *A, int n, int64_t batch, double *perms,
                              void *workspace, size_t workspace_bytes, apm_stream_t stream);
@@ -174,6 +181,7 @@ apm_status_t apm_perm_minors(const double *A, int n, int64_t batch, double *perm
 #define APM_OP_CDET_FROM_WEIGHTS 3
 #define APM_OP_PERM_MINORS 4
 #define APM_OP_CDET_VARLEN 5
+#define APM_OP_KELDYSH 6
 
 /*
  * apm_workspace_size -- bytes of device scratch the call `op` needs for orders up

@@ -11,6 +11,7 @@ no FMA contraction so that x86 and Arm hosts round identically) into
 Functions (numpy in, numpy out; FP64 / complex128):
   minors_lu(A)              all 2^n principal minors, one partial-pivot LU each (Section II)
   perm_ryser(A, absval)     all 2^n principal permanents by Ryser per subset (Eq. ryser)
+  perm_ryser_term_scale(A)  sum of |terms| of Ryser's formula per subset (error scale)
   cdet_recursion(a)         connected sums by Eq. recursion, plain loops
   cdet_partition(a)         connected sums by the set-partition Moebius formula
   cdet_scale(ahat)          the recursion with all terms taken positive (error scale)
@@ -106,6 +107,16 @@ def perm_ryser(A, absval: bool = False, nthreads: int = 0) -> np.ndarray:
     b, n, _ = A.shape
     out = np.empty((b, 1 << n))
     _load().oracle_perm_ryser(A.ctypes.data, n, b, out.ctypes.data, int(absval), nthreads)
+    return out[0] if single else out
+
+
+def perm_ryser_term_scale(A, nthreads: int = 0) -> np.ndarray:
+    """sum_{T subset of S} |prod_{i in S} sum_{j in T} A_ij| for every S: the sum
+    of the absolute values of the terms of Ryser's formula (its rounding scale)."""
+    A, single = _mat_batch(A)
+    b, n, _ = A.shape
+    out = np.empty((b, 1 << n))
+    _load().oracle_perm_ryser(A.ctypes.data, n, b, out.ctypes.data, 2, nthreads)
     return out[0] if single else out
 
 

@@ -133,13 +133,15 @@ void oracle_minors_lu(const double *A, int n, int64_t batch, double *minors, int
     }
 }
 
-/* All 2^n principal permanents perm(A[S]) (or perm(|A[S]|) when absval != 0).
+/* All 2^n principal permanents perm(A[S]) (mode 0), perm(|A[S]|) (mode 1), or
+ * the sum of the absolute values of the Ryser terms (mode 2, the rounding-error
+ * scale of any evaluation of Ryser's formula).
  * Ryser's formula (Eq. ryser) on the submatrix A[S] with k = |S| rows:
  *     perm(A[S]) = (-1)^k sum_{T subset of S} (-1)^{|T|} prod_{i in S} sum_{j in T} A_ij.
  * (As printed, Eq. ryser lacks the (-1)^k; with it the formula gives the
  * permanent, e.g. perm of the all-ones k x k matrix = k!.) The inner column
- * sums are rebuilt from scratch for every T; perm(A[empty]) = 1. */
-void oracle_perm_ryser(const double *A, int n, int64_t batch, double *perms, int absval,
+ * sums are rebuilt from scratch for every T; the empty subset gives 1. */
+void oracle_perm_ryser(const double *A, int n, int64_t batch, double *perms, int mode,
                        int nthreads) {
     const int64_t N = (int64_t)1 << n;
 #pragma omp parallel for schedule(dynamic, 1) num_threads(threads_for(nthreads))
@@ -159,13 +161,14 @@ void oracle_perm_ryser(const double *A, int n, int64_t batch, double *perms, int
                     for (int q = 0; q < k; ++q)
                         if ((T >> q) & 1) {
                             double v = Ab[idx[r] * n + idx[q]];
-                            rs += absval ? fabs(v) : v;
+                            rs += mode == 1 ? fabs(v) : v;
                         }
                     prod *= rs;
                 }
-                total += (popcount_u32((uint32_t)T) & 1) ? -prod : prod;
+                if (mode == 2) total += fabs(prod);
+                else total += (popcount_u32((uint32_t)T) & 1) ? -prod : prod;
             }
-            out[S] = (k & 1) ? -total : total;
+            out[S] = (mode != 2 && (k & 1)) ? -total : total;
         }
     }
 }

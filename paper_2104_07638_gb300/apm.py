@@ -24,7 +24,8 @@ APM_OK, APM_ERR_ARG, APM_ERR_UNSUPPORTED_N, APM_ERR_CUDA, APM_ERR_NUMERIC, APM_E
 ST_PIVOT_CORRECTED, ST_NONFINITE_INPUT, ST_ZERO_PIVOT, ST_CORRECTION_OVERFLOW = 1, 2, 4, 8
 CDET_SINGLE_DET = 1
 KELDYSH_SIGNED = 1
-OP_ALL_MINORS, OP_CDET, OP_CDET_FROM_WEIGHTS, OP_PERM_MINORS, OP_CDET_VARLEN = 1, 2, 3, 4, 5
+OP_ALL_MINORS, OP_CDET, OP_CDET_FROM_WEIGHTS, OP_PERM_MINORS, OP_CDET_VARLEN, OP_KELDYSH = \
+    1, 2, 3, 4, 5, 6
 
 
 class ApmError(RuntimeError):
@@ -58,7 +59,7 @@ def lib():
                 "apm_all_minors": [P, i32, i64, P, OPT, P, P, sz, P],
                 "apm_cdet_connected": [P, P, i32, i64, i32, P, P, OPT, P, P, sz, P],
                 "apm_cdet_from_weights": [P, i32, i64, P, P, sz, P],
-                "apm_keldysh_sum": [P, i32, i64, i32, P, P, P, P],
+                "apm_keldysh_sum": [P, i32, i64, i32, P, P, P, P, sz, P],
                 "apm_perm_minors": [P, i32, i64, P, P, sz, P],
                 "apm_workspace_size": [i32, i32, i64, i32, ctypes.POINTER(sz)],
                 "apm_status_reduce": [P, i64, ctypes.POINTER(ctypes.c_uint32), P],
@@ -207,8 +208,9 @@ def keldysh_sum(Mt: torch.Tensor, signed=False, partial=False, return_status=Fal
     s = torch.empty((b, 2), dtype=torch.float64, device=dev)
     p = torch.empty((b, n + 1, 2), dtype=torch.float64, device=dev) if partial else None
     st = torch.zeros(b, dtype=torch.int32, device=dev) if return_status else None
+    ws, nb = _workspace(OP_KELDYSH, n, b, dev)
     _check(lib().apm_keldysh_sum(_ptr(Mt), n, b, KELDYSH_SIGNED if signed else 0, _ptr(s), _ptr(p),
-                                 _ptr(st), _stream(Mt)), "apm_keldysh_sum")
+                                 _ptr(st), _ptr(ws), nb, _stream(Mt)), "apm_keldysh_sum")
     res = [torch.view_as_complex(s)]
     if partial:
         res.append(torch.view_as_complex(p))

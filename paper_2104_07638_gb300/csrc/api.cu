@@ -116,6 +116,38 @@ apm_status_t apm_cdet_from_weights(const double *a_in, int n, int64_t batch, dou
     return cdet_common(a, workspace, workspace_bytes, reinterpret_cast<cudaStream_t>(stream));
 }
 
+apm_status_t apm_keldysh_sum(const double *Mt, int n, int64_t batch, int flags, double *sum,
+                             double *partial, uint32_t *status, void *workspace,
+                             size_t workspace_bytes, apm_stream_t stream) {
+    if (n < 1 || n > APM_MAX_N_KELDYSH) return APM_ERR_UNSUPPORTED_N;
+    if (batch < 0 || (flags & ~APM_KELDYSH_SIGNED)) return APM_ERR_ARG;
+    apm_status_t st;
+    if ((st = check_ptr(Mt, batch)) || (st = check_ptr(sum, batch)) || (st = check_opt_ptr(partial)) ||
+        (st = check_opt_ptr(status)))
+        return st;
+    if (batch == 0) return APM_OK;
+    size_t need = 0;
+    if ((st = apm_workspace_size(APM_OP_KELDYSH, n, batch, 0, &need))) return st;
+    if (need > 0 && (!workspace || workspace_bytes < need || !aligned16(workspace)))
+        return APM_ERR_WORKSPACE;
+    const int e = apm::launch_keldysh(Mt, n, batch, (flags & APM_KELDYSH_SIGNED) ? 1 : 0, sum, partial,
+                                      status, workspace, reinterpret_cast<cudaStream_t>(stream));
+    return e ? cuda_fail(e) : APM_OK;
+}
+
+apm_status_t apm_perm_minors(const double *A, int n, int64_t batch, double *perms, void *workspace,
+                             size_t workspace_bytes, apm_stream_t stream) {
+    (void)workspace;
+    (void)workspace_bytes;
+    if (n < 1 || n > APM_MAX_N_PERM) return APM_ERR_UNSUPPORTED_N;
+    if (batch < 0) return APM_ERR_ARG;
+    apm_status_t st;
+    if ((st = check_ptr(A, batch)) || (st = check_ptr(perms, batch))) return st;
+    if (batch == 0) return APM_OK;
+    const int e = apm::launch_ppm(A, n, batch, perms, reinterpret_cast<cudaStream_t>(stream));
+    return e ? cuda_fail(e) : APM_OK;
+}
+
 apm_status_t apm_workspace_size(int op, int n_max, int64_t batch, int two_mats, size_t *bytes) {
     if (!bytes || batch < 0) return APM_ERR_ARG;
     *bytes = 0;
@@ -132,6 +164,19 @@ apm_status_t apm_workspace_size(int op, int n_max, int64_t batch, int two_mats, 
             *bytes = static_cast<size_t>(grid) * apm::cdet_slot_doubles(n_max) * sizeof(double);
             return APM_OK;
         }
+        case APM_OP_KELDYSH: {
+            if (n_max < 1 || n_max > APM_MAX_N_KELDYSH) return APM_ERR_UNSUPPORTED_N;
+            const size_t per = apm::keldysh_stack_entries(n_max);
+            if (per == 0 || batch == 0) return APM_OK;
+            int err = 0;
+            const int grid = apm::keldysh_grid(batch, &err);
+            if (err) return cuda_fail(err);
+            *bytes = static_cast<size_t>(grid) * apm::keldysh_warps_per_block() * per * 2 * sizeof(double);
+            return APM_OK;
+        }
+        case APM_OP_PERM_MINORS:
+            if (n_max < 1 || n_max > APM_MAX_N_PERM) return APM_ERR_UNSUPPORTED_N;
+            return APM_OK;
         default:
             return APM_ERR_ARG;
     }

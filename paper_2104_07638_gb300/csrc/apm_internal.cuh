@@ -53,6 +53,14 @@ int ensure_tables();
 // Per-layer lane-group sizes (log2) chosen by the cost model for order n.
 void cdet_group_table(int n, int threads, uint8_t *gsel /*[17]*/);
 
+int launch_keldysh(const double *Mt, int n, int64_t batch, int sgn, double *sum, double *partial,
+                   uint32_t *status, void *workspace, cudaStream_t s);
+int keldysh_grid(int64_t batch, int *err);
+int keldysh_warps_per_block();
+size_t keldysh_stack_entries(int n);
+
+int launch_ppm(const double *A, int n, int64_t batch, double *perms, cudaStream_t s);
+
 int launch_fp64_probe(double *sink, int blocks, int threads, int iters, cudaStream_t s);
 
 }  // namespace apm

@@ -1,0 +1,277 @@
+// Real-time Keldysh sum as the sum of XOR principal minors (complex128).
+//
+// Paper: Section III.D (XOR minors: of each pair (2l+1, 2l+2) exactly one row
+// and column is kept; only the two Schur-complement branches of the ternary
+// tree remain, a binary tree with O(2^n) nodes, no pivot correction possible)
+// and Section V.D (the sum over all 2^n Keldysh index assignments equals the
+// sum of those minors of the 2n x 2n block matrix; the per-depth sums are the
+// lower orders obtained on the way).
+//
+// Tree: the node at depth d fixes the indices alpha_0..alpha_{d-1}; it holds
+// the Schur complement of the block matrix with respect to the kept rows and
+// columns {(i, alpha_i), i < d}, restricted to the rows/columns of vertices
+// d..n-1 (size 2(n-d)). Child alpha: pivot p = entry (d,alpha),(d,alpha); the
+// partner row/column (d, 1-alpha) is dropped and the rest is Schur-complemented
+// with respect to p; det(child) = det(node) * p (times -1 for alpha = - when
+// the assignments are sign-weighted).
+//
+// Mapping: one warp per matrix. The upper vertices 0..D-1 (D = n - 6) are
+// walked depth first; each Schur step is spread over the 32 lanes and its
+// result goes to a per-warp stack in caller scratch (global memory, L1/L2
+// resident). The last min(n,6) vertices are expanded breadth first in shared
+// memory (one child entry per lane step), and the 4x4 nodes of the last level
+// are finished with closed-form 2x2 determinants, one leaf per lane.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "apm_internal.cuh"
+
+namespace apm {
+
+constexpr int kKelWarps = 4;
+constexpr int kKelTail = 6;
+constexpr int kKelBufE = 256;  // levels 0, 2, 4 of a 6-vertex tail: 144, 256, 256 entries
+constexpr int kKelBufO = 288;  // levels 1, 3: 200, 288 entries
+
+struct KelWarpSmem {
+    double2 bufE[kKelBufE];
+    double2 bufO[kKelBufO];
+    double2 fac[64];
+    double2 inv[16];
+    double2 ndet[2][16];
+    double2 part[17];
+    double2 pdet[17];
+    int bad;
+    int flags;
+};
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+// c - a*b
+__device__ __forceinline__ double2 cfms(double2 a, double2 b, double2 c) {
+    return make_double2(fma(-a.x, b.x, fma(a.y, b.y, c.x)), fma(-a.x, b.y, fma(-a.y, b.x, c.y)));
+}
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 cneg_if(double2 a, bool neg) {
+    return neg ? make_double2(-a.x, -a.y) : a;
+}
+// 1/p; flags a zero or non-finite pivot
+__device__ __forceinline__ double2 crcp(double2 p, int &bad) {
+    const double d = fma(p.x, p.x, p.y * p.y);
+    if (!(d > 0.0) || !isfinite(d)) bad = 1;
+    const double r = 1.0 / d;
+    return make_double2(p.x * r, -p.y * r);
+}
+__device__ __forceinline__ double2 warp_csum(double2 v) {
+    for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    }
+    return v;
+}
+
+// doubles2 of per-warp stack for order n: depths 1..D-1
+__host__ __device__ inline size_t kel_stack_entries(int n) {
+    const int D = n > kKelTail ? n - kKelTail : 0;
+    size_t t = 0;
+    for (int d = 1; d < D; ++d) t += static_cast<size_t>(2 * (n - d)) * (2 * (n - d));
+    return t;
+}
+
+// One Schur step of the depth-first part: src (m x m) -> dst ((m-2) x (m-2)).
+__device__ __forceinline__ void kel_schur(const double2 *src, int m, int alpha, double2 *dst,
+                                          KelWarpSmem &w, int lane, double2 &piv, int &bad) {
+    piv = src[alpha * m + alpha];
+    const double2 iv = crcp(piv, bad);
+    const int m2 = m - 2;
+    for (int r = lane; r < m2; r += 32) w.fac[r] = cmul(src[(r + 2) * m + alpha], iv);
+    __syncwarp();
+    for (int e = lane; e < m2 * m2; e += 32) {
+        const int r = e / m2, q = e - r * m2;
+        dst[e] = cfms(w.fac[r], src[alpha * m + q + 2], src[(r + 2) * m + q + 2]);
+    }
+    __syncwarp();
+}
+
+// Breadth-first tail over the last s vertices; the root (2s x 2s) is in bufE
+// with determinant det0 at depth depth0. Adds the leaf sum to part[n] and the
+// per-depth node sums to part[depth0+1 .. n-1] (partials only if want_part).
+__device__ void kel_tail(int s, int n, double2 det0, int depth0, bool want_part, bool sgn,
+                         KelWarpSmem &w, int lane, int &bad) {
+    if (s == 1) {
+        if (lane == 0) {
+            const double2 *M = w.bufE;
+            const double2 v = cadd(M[0], cneg_if(M[3], sgn));
+            w.part[n] = cadd(w.part[n], cmul(det0, v));
+        }
+        __syncwarp();
+        return;
+    }
+    double2 *cur = w.bufE, *nxt = w.bufO;
+    int nodes = 1, m = 2 * s;
+    if (lane == 0) w.ndet[0][0] = det0;
+    __syncwarp();
+    for (int j = 0; j < s - 2; ++j) {
+        const int nchild = 2 * nodes, m2 = m - 2, mm = m * m, mm2 = m2 * m2;
+        if (lane < nchild) {
+            const int alpha = lane & 1;
+            const double2 *P = cur + (lane >> 1) * mm;
+            const double2 piv = P[alpha * m + alpha];
+            w.inv[lane] = crcp(piv, bad);
+            w.ndet[(j + 1) & 1][lane] = cneg_if(cmul(w.ndet[j & 1][lane >> 1], piv), sgn && alpha);
+        }
+        __syncwarp();
+        for (int idx = lane; idx < nchild * m2; idx += 32) {
+            const int c = idx / m2, r = idx - c * m2, alpha = c & 1;
+            const double2 *P = cur + (c >> 1) * mm;
+            w.fac[idx] = cmul(P[(r + 2) * m + alpha], w.inv[c]);
+        }
+        __syncwarp();
+        for (int e = lane; e < nchild * mm2; e += 32) {
+            const int c = e / mm2, rem = e - c * mm2, r = rem / m2, q = rem - r * m2, alpha = c & 1;
+            const double2 *P = cur + (c >> 1) * mm;
+            nxt[e] = cfms(w.fac[c * m2 + r], P[alpha * m + q + 2], P[(r + 2) * m + q + 2]);
+        }
+        __syncwarp();
+        if (want_part) {
+            double2 v = lane < nchild ? w.ndet[(j + 1) & 1][lane] : make_double2(0.0, 0.0);
+            v = warp_csum(v);
+            if (lane == 0) w.part[depth0 + j + 1] = cadd(w.part[depth0 + j + 1], v);
+        }
+        double2 *t = cur;
+        cur = nxt;
+        nxt = t;
+        nodes = nchild;
+        m = m2;
+    }
+    // 4x4 nodes: leaves are 2x2 determinants of rows/cols (0|1, 2|3)
+    const double2 *nd = w.ndet[(s - 2) & 1];
+    double2 acc = make_double2(0.0, 0.0), accp = make_double2(0.0, 0.0);
+    for (int idx = lane; idx < nodes * 4; idx += 32) {
+        const int k = idx >> 2, al = idx & 1, be = (idx >> 1) & 1;
+        const double2 *M = cur + k * 16;
+        const double2 dk = nd[k];
+        const double2 d2 = cfms(M[al * 4 + 2 + be], M[(2 + be) * 4 + al],
+                                cmul(M[al * 4 + al], M[(2 + be) * 4 + 2 + be]));
+        acc = cadd(acc, cneg_if(cmul(dk, d2), sgn && (al ^ be)));
+        if (want_part && be == 0) accp = cadd(accp, cneg_if(cmul(dk, M[al * 4 + al]), sgn && al));
+    }
+    acc = warp_csum(acc);
+    if (want_part) accp = warp_csum(accp);
+    if (lane == 0) {
+        w.part[n] = cadd(w.part[n], acc);
+        if (want_part) w.part[n - 1] = cadd(w.part[n - 1], accp);
+    }
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(kKelWarps * 32) keldysh_kernel(
+    const double2 *__restrict__ Mt, int n, int64_t batch, int sgn_flag, double *sum, double *partial,
+    uint32_t *status, double2 *stack_base, size_t stack_per_warp) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    KelWarpSmem &w = reinterpret_cast<KelWarpSmem *>(smem_raw)[wid];
+    const int64_t gw = static_cast<int64_t>(blockIdx.x) * kKelWarps + wid;
+    const int64_t nw = static_cast<int64_t>(gridDim.x) * kKelWarps;
+    double2 *stack = stack_base + gw * stack_per_warp;
+    const bool sgn = sgn_flag != 0;
+    const bool want_part = partial != nullptr;
+    const int s = n < kKelTail ? n : kKelTail;
+    const int D = n - s;
+    const int m0 = 2 * n;
+    for (int64_t b = gw; b < batch; b += nw) {
+        const double2 *A = Mt + b * static_cast<int64_t>(m0) * m0;
+        int bad = 0, nonfin = 0;
+        for (int e = lane; e < m0 * m0; e += 32) {
+            const double2 v = A[e];
+            if (!isfinite(v.x) || !isfinite(v.y)) nonfin = 1;
+        }
+        nonfin = __any_sync(0xffffffffu, nonfin);
+        if (lane <= n) w.part[lane] = make_double2(lane == 0 ? 1.0 : 0.0, 0.0);
+        if (lane == 0) w.pdet[0] = make_double2(1.0, 0.0);
+        __syncwarp();
+        if (D == 0) {
+            for (int e = lane; e < m0 * m0; e += 32) w.bufE[e] = A[e];
+            __syncwarp();
+            kel_tail(s, n, make_double2(1.0, 0.0), 0, want_part, sgn, w, lane, bad);
+        } else {
+            // per-depth offsets of the stack (depth 1..D-1)
+            for (int64_t t = 0; t < (int64_t(1) << D); ++t) {
+                const int d0 = t == 0 ? 0 : D - 1 - __ffsll(t) + 1;
+                size_t off = 0;
+                for (int d = 1; d < d0; ++d) off += static_cast<size_t>(2 * (n - d)) * (2 * (n - d));
+                for (int d = d0; d < D; ++d) {
+                    const int alpha = static_cast<int>((t >> (D - 1 - d)) & 1);
+                    const int m = 2 * (n - d);
+                    const double2 *src = d == 0 ? A : stack + off;
+                    if (d > 0) off += static_cast<size_t>(m) * m;
+                    double2 *dst = (d + 1 == D) ? w.bufE : stack + off;
+                    double2 piv;
+                    kel_schur(src, m, alpha, dst, w, lane, piv, bad);
+                    if (lane == 0) {
+                        const double2 pd = cneg_if(cmul(w.pdet[d], piv), sgn && alpha);
+                        w.pdet[d + 1] = pd;
+                        if (want_part) w.part[d + 1] = cadd(w.part[d + 1], pd);
+                    }
+                    __syncwarp();
+                }
+                kel_tail(s, n, w.pdet[D], D, want_part, sgn, w, lane, bad);
+            }
+        }
+        bad = __any_sync(0xffffffffu, bad);
+        const double nanv = __longlong_as_double(0x7ff8000000000000ll);
+        if (lane == 0) {
+            const double2 r = (bad || nonfin) ? make_double2(nanv, nanv) : w.part[n];
+            sum[2 * b] = r.x;
+            sum[2 * b + 1] = r.y;
+            if (status) status[b] = (bad ? APM_ST_ZERO_PIVOT : 0u) | (nonfin ? APM_ST_NONFINITE_INPUT : 0u);
+        }
+        if (want_part && lane <= n) {
+            const double2 r = (bad || nonfin) ? make_double2(nanv, nanv) : w.part[lane];
+            partial[(b * (n + 1) + lane) * 2] = r.x;
+            partial[(b * (n + 1) + lane) * 2 + 1] = r.y;
+        }
+        __syncwarp();
+    }
+}
+
+size_t keldysh_stack_entries(int n) { return kel_stack_entries(n); }
+
+int keldysh_grid(int64_t batch, int *err) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t smem = kKelWarps * sizeof(KelWarpSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(keldysh_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(smem));
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, keldysh_kernel, kKelWarps * 32, smem);
+    if (e != cudaSuccess || per_sm < 1) {
+        *err = e != cudaSuccess ? static_cast<int>(e) : static_cast<int>(cudaErrorInvalidConfiguration);
+        return 0;
+    }
+    *err = 0;
+    const int64_t need = (batch + kKelWarps - 1) / kKelWarps;
+    int64_t g = static_cast<int64_t>(sms) * per_sm;
+    if (need < g) g = need;
+    return static_cast<int>(g < 1 ? 1 : g);
+}
+
+int keldysh_warps_per_block() { return kKelWarps; }
+
+int launch_keldysh(const double *Mt, int n, int64_t batch, int sgn, double *sum, double *partial,
+                   uint32_t *status, void *workspace, cudaStream_t s) {
+    int err = 0;
+    const int grid = keldysh_grid(batch, &err);
+    if (err) return err;
+    const size_t smem = kKelWarps * sizeof(KelWarpSmem);
+    keldysh_kernel<<<grid, kKelWarps * 32, smem, s>>>(reinterpret_cast<const double2 *>(Mt), n, batch,
+                                                      sgn, sum, partial, status,
+                                                      static_cast<double2 *>(workspace),
+                                                      kel_stack_entries(n));
+    return static_cast<int>(cudaGetLastError());
+}
+
+}  // namespace apm

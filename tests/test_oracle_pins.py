@@ -184,6 +184,19 @@ def test_perm_rank_one_and_diagonal():
     np.testing.assert_allclose(oracle.perm_ryser(np.diag(d)), ref, rtol=1e-12, atol=1e-15)
 
 
+def test_perm_ryser_term_scale_closed_forms():
+    # all-ones k x k: the Ryser terms are C(k,t) t^k in magnitude
+    n = 7
+    sc = oracle.perm_ryser_term_scale(np.ones((n, n)))
+    for S, e in enumerate(masks_elems(n)):
+        k = len(e)
+        ref = sum(math.comb(k, t) * t ** k for t in range(k + 1)) if k else 1
+        assert abs(sc[S] - ref) <= 1e-12 * ref
+    rng = np.random.default_rng(23)
+    A = rng.standard_normal((6, 6))
+    assert np.all(oracle.perm_ryser_term_scale(A) >= np.abs(oracle.perm_ryser(A)) * (1 - 1e-12))
+
+
 def test_perm_zero_one_counts_perfect_matchings():
     rng = np.random.default_rng(22)
     n = 7
