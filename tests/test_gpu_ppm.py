@@ -59,9 +59,9 @@ def test_order_15_global_accumulator(apm):
 def test_all_ones_factorials_n16(apm):
     n = 16
     p = apm.perm_minors(dev(np.ones((1, n, n)))).cpu().numpy()[0]
-    size = np.array([bin(S).count("1") for S in range(1 << n)])
-    ref = np.array([math.factorial(k) for k in size], dtype=float)
-    scale = np.array([sum(math.comb(k, t) * t ** k for t in range(k + 1)) for k in size], dtype=float)
+    size = [bin(S).count("1") for S in range(1 << n)]        # python ints: no overflow
+    ref = np.array([float(math.factorial(k)) for k in size])
+    scale = np.array([float(sum(math.comb(k, t) * t ** k for t in range(k + 1))) for k in size])
     assert np.all(np.abs(p - ref) <= TOL * scale)
 
 
