@@ -268,6 +268,15 @@ def test_cdet_block_diagonal_vanishes_across_blocks(square):
             assert abs(c[S]) <= 1e-13 * scale[S]
 
 
+def test_cdet_scale_bounds_partition_route():
+    # the error scale must bound |c| computed by the independent partition route
+    rng = np.random.default_rng(35)
+    n = 8
+    a = rng.standard_normal(1 << n)
+    a[0] = 1.0
+    assert np.all(oracle.cdet_scale(np.abs(a)) >= np.abs(oracle.cdet_partition(a)) * (1 - 1e-12))
+
+
 def test_cdet_independent_of_choice_of_j():
     # Eq. recursion with j = the highest element instead of the lowest (written
     # here independently) must give the same connected sums.
