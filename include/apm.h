@@ -134,7 +134,7 @@ apm_status_t apm_cdet_connected(const double *A_up, const double *A_dn, int n, i
 apm_status_t apm_cdet_from_weights(const double *a, int n, int64_t batch, double *c,
                                    void *workspace, size_t workspace_bytes, apm_stream_t stream);
 
-/* flags for apm_keldysh_sum */
+/* flags for apm_keldysh_sum and apm_keldysh_sum_noalloc */
 #define APM_KELDYSH_SIGNED 0x1 /* weight each assignment by (-1)^{number of - indices} */
 
 /*
@@ -159,6 +159,29 @@ apm_status_t apm_cdet_from_weights(const double *a, int n, int64_t batch, double
 apm_status_t apm_keldysh_sum(const double *Mt, int n, int64_t batch, int flags, double *sum,
                              double *partial, uint32_t *status, void *workspace,
                              size_t workspace_bytes, apm_stream_t stream);
+
+/*
+ * apm_keldysh_sum_noalloc -- the same sum as apm_keldysh_sum, for callers that
+ * cannot allocate device memory around the call: programs that hand all device
+ * memory to their own pool allocator and forbid cudaMalloc inside their
+ * Monte Carlo step (cudaMalloc can synchronise the device, and fails once the
+ * pool owns the memory), and plugin hosts that only pass device pointers in.
+ * There is no counterpart in the paper; it is a packaging of the same kernel.
+ *   Instead of a caller workspace, the depth-first stack uses a fixed array in
+ *   device memory that belongs to the library: 152 x 4 warp slots for orders up
+ *   to 14, 28.3 MB, held on every GPU that loads the library until the process
+ *   exits. Orders above 14 are rejected with APM_ERR_UNSUPPORTED_N (use
+ *   apm_keldysh_sum with a workspace). The call allocates nothing.
+ *   The first call on a device looks up the array's device address (once per
+ *   device, with that device current); make that first call before any stream
+ *   capture. Every call shares the one array: calls that overlap on the GPU (for
+ *   example on two streams) race and give wrong results; serialise them. The
+ *   array keeps whatever the last call left there; nothing in it needs to start
+ *   at zero, because every entry is written before it is read.
+ *   Arguments and results as for apm_keldysh_sum (n in 1..14).
+ */
+apm_status_t apm_keldysh_sum_noalloc(const double *Mt, int n, int64_t batch, int flags, double *sum,
+                                     double *partial, uint32_t *status, apm_stream_t stream);
 
 /*
  * apm_perm_minors -- all 2^n permanent principal minors perm(A[S]) in O(3^n)

@@ -61,6 +61,7 @@ def lib():
                 "apm_cdet_from_weights": [P, i32, i64, P, P, sz, P],
                 "apm_keldysh_sum": [P, i32, i64, i32, P, P, P, P, sz, P],
                 "apm_perm_minors": [P, i32, i64, P, P, sz, P],
+                "apm_keldysh_sum_noalloc": [P, i32, i64, i32, P, P, P, P],
                 "apm_workspace_size": [i32, i32, i64, i32, ctypes.POINTER(sz)],
                 "apm_status_reduce": [P, i64, ctypes.POINTER(ctypes.c_uint32), P],
                 "apm_fp64_fma_probe": [P, i32, i32, i32, P],
@@ -211,6 +212,29 @@ def keldysh_sum(Mt: torch.Tensor, signed=False, partial=False, return_status=Fal
     ws, nb = _workspace(OP_KELDYSH, n, b, dev)
     _check(lib().apm_keldysh_sum(_ptr(Mt), n, b, KELDYSH_SIGNED if signed else 0, _ptr(s), _ptr(p),
                                  _ptr(st), _ptr(ws), nb, _stream(Mt)), "apm_keldysh_sum")
+    res = [torch.view_as_complex(s)]
+    if partial:
+        res.append(torch.view_as_complex(p))
+    if return_status:
+        res.append(st)
+    return res[0] if len(res) == 1 else tuple(res)
+
+
+def keldysh_sum_noalloc(Mt: torch.Tensor, signed=False, partial=False, return_status=False):
+    """apm_keldysh_sum_noalloc: the Keldysh sum without a caller workspace (the
+    library's fixed device array serves as scratch; orders 1..14; calls that
+    overlap on the GPU must not share a device)."""
+    Mt = _mat_batch(Mt, torch.complex128, "Mt")
+    b, n2, _ = Mt.shape
+    if n2 % 2:
+        raise ValueError("Mt must be 2n x 2n")
+    n = n2 // 2
+    dev = Mt.device
+    s = torch.empty((b, 2), dtype=torch.float64, device=dev)
+    p = torch.empty((b, n + 1, 2), dtype=torch.float64, device=dev) if partial else None
+    st = torch.zeros(b, dtype=torch.int32, device=dev) if return_status else None
+    _check(lib().apm_keldysh_sum_noalloc(_ptr(Mt), n, b, KELDYSH_SIGNED if signed else 0, _ptr(s),
+                                         _ptr(p), _ptr(st), _stream(Mt)), "apm_keldysh_sum_noalloc")
     res = [torch.view_as_complex(s)]
     if partial:
         res.append(torch.view_as_complex(p))

@@ -71,8 +71,8 @@ __device__ __forceinline__ double2 warp_csum(double2 v) {
     return v;
 }
 
-// doubles2 of per-warp stack for order n: depths 1..D-1
-__host__ __device__ inline size_t kel_stack_entries(int n) {
+// double2 entries of the per-warp stack for order n: depths 1..D-1
+__host__ __device__ constexpr size_t kel_stack_entries(int n) {
     const int D = n > kKelTail ? n - kKelTail : 0;
     size_t t = 0;
     for (int d = 1; d < D; ++d) t += static_cast<size_t>(2 * (n - d)) * (2 * (n - d));
@@ -274,4 +274,62 @@ int launch_keldysh(const double *Mt, int n, int64_t batch, int sgn, double *sum,
     return static_cast<int>(cudaGetLastError());
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free variant: the depth-first stack lives in a fixed array in
+// device memory that belongs to the library (no caller workspace).
+// ---------------------------------------------------------------------------
+
+constexpr int kKelNoAllocMaxN = 14;
+constexpr int kKelNoAllocBlocks = 152;
+constexpr size_t kKelNoAllocStack = kel_stack_entries(kKelNoAllocMaxN);
+static_assert(kKelNoAllocStack == 2912, "stack size of order 14");
+
+// 152 CTAs x 4 warps x 2912 complex entries x 16 B = 28.3 MB per device.
+static __device__ __align__(256) double2 g_kel_noalloc_stack[kKelNoAllocBlocks * kKelWarps *
+                                                            kKelNoAllocStack];
+
 }  // namespace apm
+
+#include <mutex>
+
+namespace {
+std::mutex g_noalloc_mu;
+constexpr int kNoAllocMaxDevices = 64;
+void *g_noalloc_addr[kNoAllocMaxDevices] = {};
+}  // namespace
+
+extern "C" apm_status_t apm_keldysh_sum_noalloc(const double *Mt, int n, int64_t batch, int flags,
+                                                double *sum, double *partial, uint32_t *status,
+                                                apm_stream_t stream) {
+    using namespace apm;
+    if (n < 1 || n > kKelNoAllocMaxN) return APM_ERR_UNSUPPORTED_N;
+    if (batch < 0 || (flags & ~APM_KELDYSH_SIGNED)) return APM_ERR_ARG;
+    auto bad_ptr = [](const void *q) { return (reinterpret_cast<uintptr_t>(q) & 15u) != 0; };
+    if (batch > 0 && (!Mt || !sum || bad_ptr(Mt) || bad_ptr(sum))) return APM_ERR_ARG;
+    if ((partial && bad_ptr(partial)) || (status && bad_ptr(status))) return APM_ERR_ARG;
+    if (batch == 0) return APM_OK;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return APM_ERR_CUDA;
+    void *scratch = nullptr;
+    {
+        // first call on this device: resolve the device address of the array
+        // (a host-side name of a __device__ array is not a device address)
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {
+            void *q = nullptr;
+            if (cudaGetSymbolAddress(&q, g_kel_noalloc_stack) != cudaSuccess || !q) return APM_ERR_CUDA;
+            g_noalloc_addr[dev] = q;
+        }
+        scratch = g_noalloc_addr[dev];
+    }
+    const size_t smem = kKelWarps * sizeof(KelWarpSmem);
+    if (cudaFuncSetAttribute(keldysh_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(smem)) != cudaSuccess)
+        return APM_ERR_CUDA;
+    const int64_t need = (batch + kKelWarps - 1) / kKelWarps;
+    const int grid = static_cast<int>(need < kKelNoAllocBlocks ? need : kKelNoAllocBlocks);
+    keldysh_kernel<<<grid, kKelWarps * 32, smem, reinterpret_cast<cudaStream_t>(stream)>>>(
+        reinterpret_cast<const double2 *>(Mt), n, batch, (flags & APM_KELDYSH_SIGNED) ? 1 : 0, sum,
+        partial, status, static_cast<double2 *>(scratch), kel_stack_entries(n));
+    return cudaGetLastError() == cudaSuccess ? APM_OK : APM_ERR_CUDA;
+}
