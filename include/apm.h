@@ -59,7 +59,9 @@ typedef enum {
 #define APM_ST_ZERO_PIVOT          0x04u /* Keldysh: a zero or non-finite pivot; sum set to NaN */
 #define APM_ST_CORRECTION_OVERFLOW 0x08u /* more pivot corrections than the per-matrix log holds
                                             (256); outputs set to NaN */
-#define APM_ST_ERROR_MASK          (APM_ST_NONFINITE_INPUT | APM_ST_ZERO_PIVOT | APM_ST_CORRECTION_OVERFLOW)
+#define APM_ST_BAD_ORDER           0x10u /* uneven batch: order outside 1..n_max; matrix skipped */
+#define APM_ST_ERROR_MASK          (APM_ST_NONFINITE_INPUT | APM_ST_ZERO_PIVOT | APM_ST_CORRECTION_OVERFLOW | \
+                                    APM_ST_BAD_ORDER)
 
 /* Largest supported orders. */
 #define APM_MAX_N_MINORS   16
@@ -205,6 +207,59 @@ apm_status_t apm_perm_minors(const double *A, int n, int64_t batch, double *perm
 #define APM_OP_PERM_MINORS 4
 #define APM_OP_CDET_VARLEN 5
 #define APM_OP_KELDYSH 6
+#define APM_OP_KELDYSH_VARLEN 7
+
+/*
+ * apm_cdet_connected_varlen -- apm_cdet_connected for a batch of matrices of
+ * uneven orders in one persistent launch (no counterpart in the paper; the
+ * per-matrix arithmetic is that of apm_cdet_connected, bit for bit).
+ *   A       packed input matrices; matrix b is n[b] x n[b] row-major at A + a_off[b].
+ *   A_dn    NULL, or packed like A (same offsets) for a separate second matrix.
+ *   a_off   [batch] int64 element offsets.     n  [batch] int32 orders in 1..n_max.
+ *   n_max   largest order present (1..16); sizes the scratch.
+ *   flags   as apm_cdet_connected.
+ *   c       packed outputs: c[S] of matrix b at c + c_off[b] (2^n[b] doubles).
+ *   minors_out NULL or packed like c (with A_dn: 2 x 2^n[b] doubles at 2*c_off[b]).
+ *   c_off   [batch] int64 element offsets (multiples of 2 for 16-byte alignment).
+ *   workspace  apm_workspace_size(APM_OP_CDET_VARLEN, n_max, batch, two_mats).
+ * Scheduling: a one-block counting sort puts the matrices in decreasing order
+ * of n (longest first) into the workspace; every CTA then takes the next matrix
+ * from a global counter (an atomic increment, no waiting). Orders up to 12 keep
+ * a[] and c[] in shared memory, larger ones in the CTA's slot of the workspace.
+ * The lane-group mapping per order is the one installed by apm_cdet_tune_set.
+ * A matrix whose n[b] is outside 1..n_max is skipped with APM_ST_BAD_ORDER.
+ * The call allocates nothing and does not synchronise: it can be captured in a
+ * CUDA graph once the first (non-captured) call on the device has run.
+ */
+apm_status_t apm_cdet_connected_varlen(const double *A, const double *A_dn, const int64_t *a_off,
+                                       const int32_t *n, int64_t batch, int n_max, int flags, double *c,
+                                       double *minors_out, const int64_t *c_off,
+                                       const apm_pivot_opts *opt, uint32_t *status, void *workspace,
+                                       size_t workspace_bytes, apm_stream_t stream);
+
+/*
+ * apm_keldysh_sum_varlen -- apm_keldysh_sum for uneven orders in one launch,
+ * longest first (same scheduling as apm_cdet_connected_varlen).
+ *   Mt       packed complex128 matrices, matrix b (2n[b] x 2n[b]) at Mt + 2*m_off[b]
+ *            doubles (m_off counts complex entries).
+ *   sum      [batch][2].   partial  NULL or [batch][17][2] (entries 0..n[b] used).
+ *   workspace  apm_workspace_size(APM_OP_KELDYSH_VARLEN, n_max, batch, 0).
+ */
+apm_status_t apm_keldysh_sum_varlen(const double *Mt, const int64_t *m_off, const int32_t *n, int64_t batch,
+                                    int n_max, int flags, double *sum, double *partial, uint32_t *status,
+                                    void *workspace, size_t workspace_bytes, apm_stream_t stream);
+
+/*
+ * apm_cdet_tune_set -- install per-order lane-group tables for the connected-sum
+ * recursion (found by an autotuner; no counterpart in the paper). table[n] for
+ * n = 0..16 packs, for each popcount layer k, 3 bits at bit 3k: log2 of the number
+ * of lanes that share one set S (0..5, at most k-1). An entry 0 (or table NULL)
+ * restores the built-in cost model. Used by every later fixed-order and uneven
+ * launch in this process. Returns APM_ERR_ARG for an invalid entry.
+ * apm_cdet_tune_get -- the table in effect for order n.
+ */
+apm_status_t apm_cdet_tune_set(const uint64_t *table);
+apm_status_t apm_cdet_tune_get(int n, uint64_t *packed);
 
 /*
  * apm_workspace_size -- bytes of device scratch the call `op` needs for orders up

@@ -7,6 +7,7 @@ the O(2^n) Keldysh (XOR-minor) sum and the O(3^n) permanent principal minors.
 
 Submodules:
   apm     -- Python binding of the C ABI (include/apm.h) of libapm.so
+  batch   -- CUDA-graph capture of uneven batches, per-order autotuner
   build   -- builds libapm.so in-tree with nvcc for sm_103a
   inputs  -- seeded synthetic workloads (no method arithmetic)
 
@@ -14,7 +15,7 @@ Submodules:
 """
 import importlib
 
-__all__ = ["apm", "build", "inputs"]
+__all__ = ["apm", "batch", "build", "inputs"]
 
 
 def __getattr__(name):

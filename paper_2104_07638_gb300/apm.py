@@ -24,8 +24,9 @@ APM_OK, APM_ERR_ARG, APM_ERR_UNSUPPORTED_N, APM_ERR_CUDA, APM_ERR_NUMERIC, APM_E
 ST_PIVOT_CORRECTED, ST_NONFINITE_INPUT, ST_ZERO_PIVOT, ST_CORRECTION_OVERFLOW = 1, 2, 4, 8
 CDET_SINGLE_DET = 1
 KELDYSH_SIGNED = 1
-OP_ALL_MINORS, OP_CDET, OP_CDET_FROM_WEIGHTS, OP_PERM_MINORS, OP_CDET_VARLEN, OP_KELDYSH = \
-    1, 2, 3, 4, 5, 6
+OP_ALL_MINORS, OP_CDET, OP_CDET_FROM_WEIGHTS, OP_PERM_MINORS, OP_CDET_VARLEN, OP_KELDYSH, \
+    OP_KELDYSH_VARLEN = 1, 2, 3, 4, 5, 6, 7
+ST_BAD_ORDER = 16
 
 
 class ApmError(RuntimeError):
@@ -62,6 +63,10 @@ def lib():
                 "apm_keldysh_sum": [P, i32, i64, i32, P, P, P, P, sz, P],
                 "apm_perm_minors": [P, i32, i64, P, P, sz, P],
                 "apm_keldysh_sum_noalloc": [P, i32, i64, i32, P, P, P, P],
+                "apm_cdet_connected_varlen": [P, P, P, P, i64, i32, i32, P, P, P, OPT, P, P, sz, P],
+                "apm_keldysh_sum_varlen": [P, P, P, i64, i32, i32, P, P, P, P, sz, P],
+                "apm_cdet_tune_set": [P],
+                "apm_cdet_tune_get": [i32, ctypes.POINTER(ctypes.c_uint64)],
                 "apm_workspace_size": [i32, i32, i64, i32, ctypes.POINTER(sz)],
                 "apm_status_reduce": [P, i64, ctypes.POINTER(ctypes.c_uint32), P],
                 "apm_fp64_fma_probe": [P, i32, i32, i32, P],
@@ -241,6 +246,101 @@ def keldysh_sum_noalloc(Mt: torch.Tensor, signed=False, partial=False, return_st
     if return_status:
         res.append(st)
     return res[0] if len(res) == 1 else tuple(res)
+
+
+def varlen_out_offsets(n: torch.Tensor) -> torch.Tensor:
+    """Exclusive prefix sum of 2^n (int64): output row offsets of an uneven batch."""
+    sizes = torch.ones_like(n, dtype=torch.int64) << n.to(torch.int64)
+    return torch.cumsum(sizes, 0) - sizes
+
+
+def cdet_connected_varlen(A: torch.Tensor, a_off: torch.Tensor, n: torch.Tensor, n_max: int | None = None,
+                          A_dn: torch.Tensor | None = None, c_off: torch.Tensor | None = None,
+                          single_det=False, return_minors=False, return_status=False,
+                          out_c=None, out_minors=None, workspace=None, piv_threshold=None,
+                          piv_shift=None):
+    """apm_cdet_connected_varlen. A: packed float64 matrices (1-D), a_off: int64
+    offsets, n: int32 orders. Returns packed c (and minors/status) with row
+    offsets c_off (varlen_out_offsets(n) when not given)."""
+    for t, nm in ((A, "A"), (a_off, "a_off"), (n, "n")):
+        if not t.is_cuda or not t.is_contiguous():
+            raise TypeError(f"{nm} must be a contiguous CUDA tensor")
+    if A.dtype != torch.float64 or a_off.dtype != torch.int64 or n.dtype != torch.int32:
+        raise TypeError("A float64, a_off int64, n int32 expected")
+    b = n.numel()
+    if n_max is None:
+        n_max = int(n.max().item()) if b else 1
+    if c_off is None:
+        c_off = varlen_out_offsets(n)
+    total = int((c_off[-1] + (1 << int(n[-1].item()))).item()) if b else 0
+    dev = A.device
+    c = out_c if out_c is not None else torch.empty(total, dtype=torch.float64, device=dev)
+    mo = None
+    if return_minors or out_minors is not None:
+        mo = out_minors if out_minors is not None else torch.empty(
+            total * (2 if A_dn is not None else 1), dtype=torch.float64, device=dev)
+    st = torch.zeros(b, dtype=torch.int32, device=dev) if return_status else None
+    if workspace is None:
+        nb = workspace_size(OP_CDET_VARLEN, n_max, b, A_dn is not None)
+        workspace = torch.empty(max(nb, 16), dtype=torch.uint8, device=dev)
+    _check(lib().apm_cdet_connected_varlen(_ptr(A), _ptr(A_dn), _ptr(a_off), _ptr(n), b, n_max,
+                                           CDET_SINGLE_DET if single_det else 0, _ptr(c), _ptr(mo),
+                                           _ptr(c_off), _opts(piv_threshold, piv_shift), _ptr(st),
+                                           _ptr(workspace), workspace.numel(), _stream(A)),
+           "apm_cdet_connected_varlen")
+    res = [c]
+    if return_minors:
+        res.append(mo)
+    if return_status:
+        res.append(st)
+    return res[0] if len(res) == 1 else tuple(res)
+
+
+def keldysh_sum_varlen(Mt: torch.Tensor, m_off: torch.Tensor, n: torch.Tensor, n_max: int | None = None,
+                       signed=False, partial=False, return_status=False, out_sum=None, out_partial=None,
+                       workspace=None):
+    """apm_keldysh_sum_varlen. Mt: packed complex128 (1-D), m_off: int64 offsets
+    in complex entries, n: int32 orders."""
+    if Mt.dtype != torch.complex128 or m_off.dtype != torch.int64 or n.dtype != torch.int32:
+        raise TypeError("Mt complex128, m_off int64, n int32 expected")
+    b = n.numel()
+    if n_max is None:
+        n_max = int(n.max().item()) if b else 1
+    dev = Mt.device
+    s = out_sum if out_sum is not None else torch.empty((b, 2), dtype=torch.float64, device=dev)
+    p = None
+    if partial or out_partial is not None:
+        p = out_partial if out_partial is not None else torch.empty((b, 17, 2), dtype=torch.float64, device=dev)
+    st = torch.zeros(b, dtype=torch.int32, device=dev) if return_status else None
+    if workspace is None:
+        nb = workspace_size(OP_KELDYSH_VARLEN, n_max, b)
+        workspace = torch.empty(max(nb, 16), dtype=torch.uint8, device=dev)
+    _check(lib().apm_keldysh_sum_varlen(_ptr(Mt), _ptr(m_off), _ptr(n), b, n_max,
+                                        KELDYSH_SIGNED if signed else 0, _ptr(s), _ptr(p), _ptr(st),
+                                        _ptr(workspace), workspace.numel(), _stream(Mt)),
+           "apm_keldysh_sum_varlen")
+    res = [torch.view_as_complex(s)]
+    if partial:
+        res.append(torch.view_as_complex(p))
+    if return_status:
+        res.append(st)
+    return res[0] if len(res) == 1 else tuple(res)
+
+
+def tune_set(table):
+    """Install per-order lane-group tables (17 packed uint64; 0 = cost model);
+    None restores the cost model everywhere."""
+    if table is None:
+        _check(lib().apm_cdet_tune_set(None), "apm_cdet_tune_set")
+        return
+    arr = (ctypes.c_uint64 * 17)(*[int(x) for x in table])
+    _check(lib().apm_cdet_tune_set(ctypes.cast(arr, ctypes.c_void_p)), "apm_cdet_tune_set")
+
+
+def tune_get(n: int) -> int:
+    out = ctypes.c_uint64(0)
+    _check(lib().apm_cdet_tune_get(n, ctypes.byref(out)), "apm_cdet_tune_get")
+    return int(out.value)
 
 
 def perm_minors(A: torch.Tensor):

@@ -2,6 +2,7 @@
 // asynchronous launch on the caller's stream. See include/apm.h.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdint.h>
 #include <stdlib.h>
 
 #include <vector>
@@ -148,6 +149,88 @@ apm_status_t apm_perm_minors(const double *A, int n, int64_t batch, double *perm
     return e ? cuda_fail(e) : APM_OK;
 }
 
+apm_status_t apm_cdet_connected_varlen(const double *A, const double *A_dn, const int64_t *a_off,
+                                       const int32_t *n, int64_t batch, int n_max, int flags, double *c,
+                                       double *minors_out, const int64_t *c_off,
+                                       const apm_pivot_opts *opt, uint32_t *status, void *workspace,
+                                       size_t workspace_bytes, apm_stream_t stream) {
+    if (n_max < 1 || n_max > APM_MAX_N_MINORS) return APM_ERR_UNSUPPORTED_N;
+    if (batch < 0 || batch > INT32_MAX || (flags & ~APM_CDET_SINGLE_DET)) return APM_ERR_ARG;
+    if ((flags & APM_CDET_SINGLE_DET) && A_dn) return APM_ERR_ARG;
+    if (batch == 0) return APM_OK;
+    apm_status_t st;
+    if ((st = check_ptr(A, batch)) || (st = check_opt_ptr(A_dn)) || (st = check_ptr(a_off, batch)) ||
+        (st = check_ptr(n, batch)) || (st = check_ptr(c, batch)) || (st = check_opt_ptr(minors_out)) ||
+        (st = check_ptr(c_off, batch)) || (st = check_opt_ptr(status)))
+        return st;
+    size_t need = 0;
+    if ((st = apm_workspace_size(APM_OP_CDET_VARLEN, n_max, batch, A_dn ? 1 : 0, &need))) return st;
+    if (!workspace || workspace_bytes < need || !aligned16(workspace)) return APM_ERR_WORKSPACE;
+    apm::CdetArgs a = {};
+    a.A_up = A;
+    a.A_dn = A_dn;
+    a.minors_out = minors_out;
+    a.c_out = c;
+    a.status = status;
+    a.batch = batch;
+    a.n = n_max;
+    a.mode = apm::kModeCdet;
+    a.single_det = (flags & APM_CDET_SINGLE_DET) ? 1 : 0;
+    a.two_mats = A_dn ? 1 : 0;
+    pivot_values(opt, &a.piv_thr, &a.piv_shift);
+    const int e = apm::launch_cdet_varlen(a, a_off, n, c_off, n_max, workspace,
+                                          reinterpret_cast<cudaStream_t>(stream));
+    return e ? cuda_fail(e) : APM_OK;
+}
+
+apm_status_t apm_keldysh_sum_varlen(const double *Mt, const int64_t *m_off, const int32_t *n, int64_t batch,
+                                    int n_max, int flags, double *sum, double *partial, uint32_t *status,
+                                    void *workspace, size_t workspace_bytes, apm_stream_t stream) {
+    if (n_max < 1 || n_max > APM_MAX_N_KELDYSH) return APM_ERR_UNSUPPORTED_N;
+    if (batch < 0 || batch > INT32_MAX || (flags & ~APM_KELDYSH_SIGNED)) return APM_ERR_ARG;
+    if (batch == 0) return APM_OK;
+    apm_status_t st;
+    if ((st = check_ptr(Mt, batch)) || (st = check_ptr(m_off, batch)) || (st = check_ptr(n, batch)) ||
+        (st = check_ptr(sum, batch)) || (st = check_opt_ptr(partial)) || (st = check_opt_ptr(status)))
+        return st;
+    size_t need = 0;
+    if ((st = apm_workspace_size(APM_OP_KELDYSH_VARLEN, n_max, batch, 0, &need))) return st;
+    if (!workspace || workspace_bytes < need || !aligned16(workspace)) return APM_ERR_WORKSPACE;
+    unsigned char *ws = static_cast<unsigned char *>(workspace);
+    const size_t order_bytes = ((static_cast<size_t>(batch) * 4) + 255) & ~size_t(255);
+    unsigned *ctr = reinterpret_cast<unsigned *>(ws);
+    int *order = reinterpret_cast<int *>(ws + 256);
+    void *stack = apm::keldysh_stack_entries(n_max) ? ws + 256 + order_bytes : nullptr;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int e = apm::launch_order(n, batch, n_max, order, ctr, s);
+    if (!e)
+        e = apm::launch_keldysh_varlen(Mt, m_off, n, batch, n_max, (flags & APM_KELDYSH_SIGNED) ? 1 : 0, sum,
+                                       partial, status, stack, order, ctr, s);
+    return e ? cuda_fail(e) : APM_OK;
+}
+
+apm_status_t apm_cdet_tune_set(const uint64_t *table) {
+    if (table) {
+        for (int n = 0; n <= 16; ++n) {
+            const uint64_t t = table[n];
+            if (!t) continue;
+            for (int k = 0; k <= 16; ++k) {
+                const int r = static_cast<int>((t >> (3 * k)) & 7u);
+                if (r > 5 || (k <= n && k >= 1 && r > k - 1) || (k > n && r != 0) || (k < 2 && r != 0))
+                    return APM_ERR_ARG;
+            }
+        }
+    }
+    apm::cdet_tune_set(reinterpret_cast<const unsigned long long *>(table));
+    return APM_OK;
+}
+
+apm_status_t apm_cdet_tune_get(int n, uint64_t *packed) {
+    if (!packed || n < 0 || n > 16) return APM_ERR_ARG;
+    *packed = apm::cdet_gsel_packed(n);
+    return APM_OK;
+}
+
 apm_status_t apm_workspace_size(int op, int n_max, int64_t batch, int two_mats, size_t *bytes) {
     if (!bytes || batch < 0) return APM_ERR_ARG;
     *bytes = 0;
@@ -177,6 +260,28 @@ apm_status_t apm_workspace_size(int op, int n_max, int64_t batch, int two_mats, 
         case APM_OP_PERM_MINORS:
             if (n_max < 1 || n_max > APM_MAX_N_PERM) return APM_ERR_UNSUPPORTED_N;
             return APM_OK;
+        case APM_OP_CDET_VARLEN: {
+            if (n_max < 1 || n_max > APM_MAX_N_MINORS) return APM_ERR_UNSUPPORTED_N;
+            if (batch == 0) return APM_OK;
+            int err = 0;
+            *bytes = apm::cdet_varlen_workspace(n_max, batch, two_mats != 0, &err);
+            return err ? cuda_fail(err) : APM_OK;
+        }
+        case APM_OP_KELDYSH_VARLEN: {
+            if (n_max < 1 || n_max > APM_MAX_N_KELDYSH) return APM_ERR_UNSUPPORTED_N;
+            if (batch == 0) return APM_OK;
+            const size_t order_bytes = ((static_cast<size_t>(batch) * 4) + 255) & ~size_t(255);
+            size_t stack = 0;
+            const size_t per = apm::keldysh_stack_entries(n_max);
+            if (per) {
+                int err = 0;
+                const int grid = apm::keldysh_grid(batch, &err);
+                if (err) return cuda_fail(err);
+                stack = static_cast<size_t>(grid) * apm::keldysh_warps_per_block() * per * 2 * sizeof(double);
+            }
+            *bytes = 256 + order_bytes + stack;
+            return APM_OK;
+        }
         default:
             return APM_ERR_ARG;
     }

@@ -61,6 +61,17 @@ size_t keldysh_stack_entries(int n);
 
 int launch_ppm(const double *A, int n, int64_t batch, double *perms, cudaStream_t s);
 
+// uneven batches
+unsigned long long cdet_gsel_packed(int n);
+void cdet_tune_set(const unsigned long long *table);
+size_t cdet_varlen_workspace(int n_max, int64_t batch, bool two_mats, int *err);
+int launch_cdet_varlen(const CdetArgs &a, const int64_t *a_off, const int *n_arr, const int64_t *c_off,
+                       int n_max, void *workspace, cudaStream_t s);
+int launch_order(const int *n_arr, int64_t batch, int n_max, int *order, unsigned *ctr, cudaStream_t s);
+int launch_keldysh_varlen(const double *Mt, const int64_t *m_off, const int *n_arr, int64_t batch, int n_max,
+                          int sgn, double *sum, double *partial, uint32_t *status, void *stack,
+                          const int *order, unsigned *ctr, cudaStream_t s);
+
 int launch_fp64_probe(double *sink, int blocks, int threads, int iters, cudaStream_t s);
 
 }  // namespace apm

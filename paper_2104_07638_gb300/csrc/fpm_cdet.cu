@@ -68,6 +68,18 @@ struct CdetKernelParams {
     unsigned long long gsel;  // 3 bits per popcount layer k: log2 of the lane-group size
 };
 
+struct VarlenParams {
+    CdetArgs a;                    // batch, mode, flags, base pointers, gscratch
+    const int64_t *a_off;          // element offset of each input matrix
+    const int *n_arr;              // order of each matrix
+    const int64_t *c_off;          // element offset of each output row (2^n entries)
+    const int *order;              // processing order (longest first)
+    unsigned *ctr;                 // work counter, zeroed by varlen_order_kernel
+    int smem_max_n;
+    int n_max;
+    unsigned long long gsel[17];   // lane-group table per order
+};
+
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
@@ -329,6 +341,67 @@ __device__ __forceinline__ void cdet_layers(const double *a, double *c, int n, u
     }
 }
 
+// One matrix: minors (and optionally the connected sums) into the output rows.
+// MA/MC/MU are on chip (in_smem) or in the CTA's global scratch slot.
+__device__ __forceinline__ void cdet_item(const CdetArgs &p, int n, const double *Au, const double *Ad,
+                                          const double *ain, double *mo, double *co, uint32_t *st,
+                                          double *MA, double *MC, double *MU, bool in_smem,
+                                          unsigned long long gsel, CdetSmemHdr &h) {
+    const int tid = threadIdx.x;
+    const int N = 1 << n;
+    if (tid == 0) bulk_wait_read();  // the previous item's bulk stores have read their source
+    if (tid == 0) {
+        h.ncorr = 0;
+        h.flags = 0;
+    }
+    __syncthreads();
+    if (p.mode == kModeWeights) {
+        for (int t = tid; t < N; t += blockDim.x) MA[t] = __ldg(ain + t);
+        __syncthreads();
+    } else {
+        if (p.two_mats) {
+            matrix_norm(Ad, n, h);
+            fpm_tree(Ad, n, MA, MC, p.piv_thr * h.anorm, p.piv_shift * h.anorm, h);
+            for (int t = tid; t < N; t += blockDim.x) MU[t] = MA[t];
+            if (tid == 0) h.ncorr = 0;
+            __syncthreads();
+        }
+        matrix_norm(Au, n, h);
+        fpm_tree(Au, n, MA, MC, p.piv_thr * h.anorm, p.piv_shift * h.anorm, h);
+        if (mo) {
+            if (in_smem) {
+                if (tid == 0) {
+                    bulk_store(mo, MA, N * 8u);
+                    if (p.two_mats) bulk_store(mo + N, MU, N * 8u);
+                    bulk_wait_read();
+                }
+            } else {
+                for (int t = tid; t < N; t += blockDim.x) {
+                    mo[t] = MA[t];
+                    if (p.two_mats) mo[N + t] = MU[t];
+                }
+            }
+        }
+        if (tid == 0 && st) *st = static_cast<uint32_t>(h.flags);
+        __syncthreads();
+        if (p.mode == kModeMinors) return;
+        if (!p.single_det) {
+            if (p.two_mats)
+                for (int t = tid; t < N; t += blockDim.x) MA[t] *= MU[t];
+            else
+                for (int t = tid; t < N; t += blockDim.x) MA[t] *= MA[t];
+        }
+        __syncthreads();
+    }
+    cdet_layers(MA, MC, n, gsel);
+    if (in_smem) {
+        if (tid == 0) bulk_store(co, MC, N * 8u);
+    } else {
+        for (int t = tid; t < N; t += blockDim.x) co[t] = MC[t];
+    }
+    // the next item's first barrier orders these reads before any overwrite
+}
+
 template <bool kSmemArrays>
 __global__ void __launch_bounds__(kCdetThreads) fpm_cdet_kernel(const CdetKernelParams P) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -337,7 +410,6 @@ __global__ void __launch_bounds__(kCdetThreads) fpm_cdet_kernel(const CdetKernel
     const int n = p.n;
     const int N = 1 << n;
     const int NC = N > 16 ? N : 16;
-    const int tid = threadIdx.x;
     double *base;
     if (kSmemArrays)
         base = reinterpret_cast<double *>(smem_raw + ((sizeof(CdetSmemHdr) + 127) & ~size_t(127)));
@@ -346,69 +418,85 @@ __global__ void __launch_bounds__(kCdetThreads) fpm_cdet_kernel(const CdetKernel
     double *MA = base;
     double *MC = base + N;
     double *MU = MC + NC;
-
+    const int64_t mat = static_cast<int64_t>(n) * n;
     for (int64_t b = blockIdx.x; b < p.batch; b += gridDim.x) {
-        if (kSmemArrays && tid == 0) bulk_wait_read();  // previous matrix's stores
-        if (tid == 0) {
-            h.ncorr = 0;
-            h.flags = 0;
-        }
-        __syncthreads();
-        const int64_t mat = static_cast<int64_t>(n) * n;
-        if (p.mode == kModeWeights) {
-            const double *ag = p.a_in + b * N;
-            for (int t = tid; t < N; t += blockDim.x) MA[t] = __ldg(ag + t);
-            __syncthreads();
-        } else {
-            if (p.two_mats) {
-                const double *Ad = p.A_dn + b * mat;
-                matrix_norm(Ad, n, h);
-                fpm_tree(Ad, n, MA, MC, p.piv_thr * h.anorm, p.piv_shift * h.anorm, h);
-                for (int t = tid; t < N; t += blockDim.x) MU[t] = MA[t];
-                if (tid == 0) h.ncorr = 0;
-                __syncthreads();
-            }
-            const double *Au = p.A_up + b * mat;
-            matrix_norm(Au, n, h);
-            fpm_tree(Au, n, MA, MC, p.piv_thr * h.anorm, p.piv_shift * h.anorm, h);
-            // minors out
-            if (p.minors_out) {
-                double *mo = p.minors_out + b * (p.two_mats ? 2 * N : N);
-                if (kSmemArrays) {
-                    if (tid == 0) {
-                        bulk_store(mo, MA, N * 8u);
-                        if (p.two_mats) bulk_store(mo + N, MU, N * 8u);
-                        bulk_wait_read();
-                    }
-                } else {
-                    for (int t = tid; t < N; t += blockDim.x) {
-                        mo[t] = MA[t];
-                        if (p.two_mats) mo[N + t] = MU[t];
-                    }
-                }
-            }
-            if (tid == 0 && p.status) p.status[b] = static_cast<uint32_t>(h.flags);
-            __syncthreads();
-            if (p.mode == kModeMinors) continue;
-            // weights a[S]
-            if (!p.single_det) {
-                if (p.two_mats)
-                    for (int t = tid; t < N; t += blockDim.x) MA[t] *= MU[t];
-                else
-                    for (int t = tid; t < N; t += blockDim.x) MA[t] *= MA[t];
-            }
-            __syncthreads();
-        }
-        cdet_layers(MA, MC, n, P.gsel);
-        double *co = p.c_out + b * N;
-        if (kSmemArrays) {
-            if (tid == 0) bulk_store(co, MC, N * 8u);
-        } else {
-            for (int t = tid; t < N; t += blockDim.x) co[t] = MC[t];
-        }
-        // the next matrix's first barrier orders these reads before any overwrite
+        cdet_item(p, n, p.A_up ? p.A_up + b * mat : nullptr, p.A_dn ? p.A_dn + b * mat : nullptr,
+                  p.a_in ? p.a_in + b * N : nullptr,
+                  p.minors_out ? p.minors_out + b * (p.two_mats ? 2 * N : N) : nullptr,
+                  p.c_out ? p.c_out + b * N : nullptr, p.status ? p.status + b : nullptr, MA, MC, MU,
+                  kSmemArrays, P.gsel, h);
     }
-    if (kSmemArrays && tid == 0) bulk_wait_all();
+    if (threadIdx.x == 0) bulk_wait_all();
+}
+
+// Uneven batch: items taken longest-first from `order` through a global
+// counter; arrays on chip for n <= smem_max_n, else in the CTA's scratch slot.
+__global__ void __launch_bounds__(kCdetThreads) fpm_cdet_varlen_kernel(const VarlenParams V) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    CdetSmemHdr &h = *reinterpret_cast<CdetSmemHdr *>(smem_raw);
+    __shared__ unsigned long long gsel_s[17];
+    __shared__ int item_s;
+    const CdetArgs &p = V.a;
+    if (threadIdx.x < 17) gsel_s[threadIdx.x] = V.gsel[threadIdx.x];
+    double *const sbase = reinterpret_cast<double *>(smem_raw + ((sizeof(CdetSmemHdr) + 127) & ~size_t(127)));
+    double *const gbase = p.gscratch ? p.gscratch + static_cast<size_t>(blockIdx.x) * slot_doubles(V.n_max) : nullptr;
+    while (true) {
+        __syncthreads();  // gsel_s ready; item_s free for reuse
+        if (threadIdx.x == 0) item_s = static_cast<int>(atomicAdd(V.ctr, 1u));
+        __syncthreads();
+        const int item = item_s;
+        if (item >= p.batch) break;
+        const int b = V.order[item];
+        const int n = V.n_arr[b];
+        if (n < 1 || n > V.n_max) {
+            if (threadIdx.x == 0 && p.status) p.status[b] = APM_ST_BAD_ORDER;
+            continue;
+        }
+        const int N = 1 << n;
+        const int NC = N > 16 ? N : 16;
+        const bool in_smem = n <= V.smem_max_n;
+        double *MA = in_smem ? sbase : gbase;
+        double *MC = MA + N;
+        double *MU = MC + NC;
+        const int64_t ao = V.a_off[b], co = V.c_off[b];
+        cdet_item(p, n, p.A_up ? p.A_up + ao : nullptr, p.A_dn ? p.A_dn + ao : nullptr,
+                  p.a_in ? p.a_in + co : nullptr,
+                  p.minors_out ? p.minors_out + (p.two_mats ? 2 * co : co) : nullptr,
+                  p.c_out ? p.c_out + co : nullptr, p.status ? p.status + b : nullptr, MA, MC, MU, in_smem,
+                  gsel_s[n], h);
+    }
+    if (threadIdx.x == 0) bulk_wait_all();
+}
+
+// Longest-first order of an uneven batch: counting sort by decreasing order n
+// (one CTA), and reset of the work counter of the consumer kernel.
+__global__ void __launch_bounds__(1024) varlen_order_kernel(const int *__restrict__ n_arr, int64_t batch,
+                                                            int n_max, int *order, unsigned *ctr) {
+    __shared__ int hist[18];
+    __shared__ int start[18];
+    if (threadIdx.x < 18) hist[threadIdx.x] = 0;
+    __syncthreads();
+    for (int64_t b = threadIdx.x; b < batch; b += blockDim.x) {
+        int n = n_arr[b];
+        n = (n < 1 || n > n_max) ? 0 : n;  // invalid orders go last (bucket 0)
+        atomicAdd(&hist[n], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int pos = 0;
+        for (int n = 17; n >= 0; --n) {
+            start[n] = pos;
+            pos += hist[n];
+        }
+        *ctr = 0u;
+    }
+    __syncthreads();
+    for (int64_t b = threadIdx.x; b < batch; b += blockDim.x) {
+        int n = n_arr[b];
+        n = (n < 1 || n > n_max) ? 0 : n;
+        const int slot = atomicAdd(&start[n], 1);
+        order[slot] = static_cast<int>(b);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -460,6 +548,22 @@ void cdet_group_table(int n, int threads, uint8_t *gsel) {
             if (cost[r] <= best * 1.03) { rb = r; break; }
         gsel[k] = static_cast<uint8_t>(rb);
     }
+}
+
+// Lane-group tables installed by apm_cdet_tune_set (0 = use the cost model).
+static unsigned long long g_tuned[17] = {};
+
+unsigned long long cdet_gsel_packed(int n) {
+    if (n >= 0 && n <= 16 && g_tuned[n]) return g_tuned[n];
+    uint8_t gsel[17];
+    cdet_group_table(n, kCdetThreads, gsel);
+    unsigned long long packed = 0ull;
+    for (int k = 0; k <= 16; ++k) packed |= static_cast<unsigned long long>(gsel[k] & 7) << (3 * k);
+    return packed;
+}
+
+void cdet_tune_set(const unsigned long long *table) {
+    for (int n = 0; n <= 16; ++n) g_tuned[n] = table ? table[n] : 0ull;
 }
 
 int cdet_grid(int n, int64_t batch, bool two_mats, bool smem_arrays, int *err) {
@@ -523,10 +627,7 @@ int launch_fpm_cdet(const CdetArgs &a, cudaStream_t s) {
     if (err) return err;
     CdetKernelParams P;
     P.a = a;
-    uint8_t gsel[17];
-    cdet_group_table(a.n, kCdetThreads, gsel);
-    P.gsel = 0ull;
-    for (int k = 0; k <= 16; ++k) P.gsel |= static_cast<unsigned long long>(gsel[k] & 7) << (3 * k);
+    P.gsel = cdet_gsel_packed(a.n);
     const bool smem_arrays = a.n <= cdet_smem_max_n(a.two_mats != 0);
     const int grid = cdet_grid(a.n, a.batch, a.two_mats != 0, smem_arrays, &err);
     if (err) return err;
@@ -535,6 +636,79 @@ int launch_fpm_cdet(const CdetArgs &a, cudaStream_t s) {
         fpm_cdet_kernel<true><<<grid, kCdetThreads, smem, s>>>(P);
     else
         fpm_cdet_kernel<false><<<grid, kCdetThreads, smem, s>>>(P);
+    return static_cast<int>(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// uneven batches
+// ---------------------------------------------------------------------------
+
+constexpr int kVarlenSmemMaxN = 12;
+
+static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+int cdet_varlen_grid(bool two_mats, int *err) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t smem = cdet_smem_bytes(kVarlenSmemMaxN, two_mats, true);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(fpm_cdet_varlen_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(smem));
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fpm_cdet_varlen_kernel, kCdetThreads, smem);
+    if (e != cudaSuccess || per_sm < 1) {
+        *err = e != cudaSuccess ? static_cast<int>(e) : static_cast<int>(cudaErrorInvalidConfiguration);
+        return 0;
+    }
+    *err = 0;
+    return sms * per_sm;
+}
+
+// Workspace of an uneven batch: [counter 256 B][order: batch int32][per-CTA slots]
+size_t cdet_varlen_workspace(int n_max, int64_t batch, bool two_mats, int *err) {
+    size_t bytes = 256 + align256(static_cast<size_t>(batch) * sizeof(int));
+    if (n_max > kVarlenSmemMaxN) {
+        const int grid = cdet_varlen_grid(two_mats, err);
+        if (*err) return 0;
+        bytes += static_cast<size_t>(grid) * slot_doubles(n_max) * sizeof(double);
+    } else {
+        *err = 0;
+    }
+    return bytes;
+}
+
+int launch_order(const int *n_arr, int64_t batch, int n_max, int *order, unsigned *ctr, cudaStream_t s) {
+    varlen_order_kernel<<<1, 1024, 0, s>>>(n_arr, batch, n_max, order, ctr);
+    return static_cast<int>(cudaGetLastError());
+}
+
+int launch_cdet_varlen(const CdetArgs &a, const int64_t *a_off, const int *n_arr, const int64_t *c_off,
+                       int n_max, void *workspace, cudaStream_t s) {
+    int err = ensure_tables();
+    if (err) return err;
+    const bool two = a.two_mats != 0;
+    const int grid = cdet_varlen_grid(two, &err);
+    if (err) return err;
+    unsigned char *ws = static_cast<unsigned char *>(workspace);
+    unsigned *ctr = reinterpret_cast<unsigned *>(ws);
+    int *order = reinterpret_cast<int *>(ws + 256);
+    double *slots = reinterpret_cast<double *>(ws + 256 + align256(static_cast<size_t>(a.batch) * sizeof(int)));
+    err = launch_order(n_arr, a.batch, n_max, order, ctr, s);
+    if (err) return err;
+    VarlenParams V;
+    V.a = a;
+    V.a.gscratch = n_max > kVarlenSmemMaxN ? slots : nullptr;
+    V.a_off = a_off;
+    V.n_arr = n_arr;
+    V.c_off = c_off;
+    V.order = order;
+    V.ctr = ctr;
+    V.smem_max_n = kVarlenSmemMaxN;
+    V.n_max = n_max;
+    for (int n = 0; n <= 16; ++n) V.gsel[n] = cdet_gsel_packed(n);
+    const int64_t g = a.batch < grid ? a.batch : grid;
+    fpm_cdet_varlen_kernel<<<static_cast<int>(g), kCdetThreads, cdet_smem_bytes(kVarlenSmemMaxN, two, true), s>>>(V);
     return static_cast<int>(cudaGetLastError());
 }
 

@@ -166,6 +166,68 @@ __device__ void kel_tail(int s, int n, double2 det0, int depth0, bool want_part,
     __syncwarp();
 }
 
+// One matrix of order n (whole warp): writes sum[2], partial[(n+1)*2] (if not
+// NULL) and the status word.
+__device__ __forceinline__ void kel_matrix(const double2 *A, int n, bool sgn, double *sum_out,
+                                           double *partial_out, uint32_t *status_out, double2 *stack,
+                                           KelWarpSmem &w, int lane) {
+    const bool want_part = partial_out != nullptr;
+    const int s = n < kKelTail ? n : kKelTail;
+    const int D = n - s;
+    const int m0 = 2 * n;
+    int bad = 0, nonfin = 0;
+    for (int e = lane; e < m0 * m0; e += 32) {
+        const double2 v = A[e];
+        if (!isfinite(v.x) || !isfinite(v.y)) nonfin = 1;
+    }
+    nonfin = __any_sync(0xffffffffu, nonfin);
+    if (lane <= n) w.part[lane] = make_double2(lane == 0 ? 1.0 : 0.0, 0.0);
+    if (lane == 0) w.pdet[0] = make_double2(1.0, 0.0);
+    __syncwarp();
+    if (D == 0) {
+        for (int e = lane; e < m0 * m0; e += 32) w.bufE[e] = A[e];
+        __syncwarp();
+        kel_tail(s, n, make_double2(1.0, 0.0), 0, want_part, sgn, w, lane, bad);
+    } else {
+        for (int64_t t = 0; t < (int64_t(1) << D); ++t) {
+            // first depth whose index changed from t-1 to t (vertex 0 <-> top bit)
+            const int d0 = t == 0 ? 0 : D - __ffsll(t);
+            size_t off = 0;  // stack offset of depth d0 (depths 1..D-1 are stacked)
+            for (int d = 1; d < d0; ++d) off += static_cast<size_t>(2 * (n - d)) * (2 * (n - d));
+            for (int d = d0; d < D; ++d) {
+                const int alpha = static_cast<int>((t >> (D - 1 - d)) & 1);
+                const int m = 2 * (n - d);
+                const double2 *src = d == 0 ? A : stack + off;
+                if (d > 0) off += static_cast<size_t>(m) * m;
+                double2 *dst = (d + 1 == D) ? w.bufE : stack + off;
+                double2 piv;
+                kel_schur(src, m, alpha, dst, w, lane, piv, bad);
+                if (lane == 0) {
+                    const double2 pd = cneg_if(cmul(w.pdet[d], piv), sgn && alpha);
+                    w.pdet[d + 1] = pd;
+                    if (want_part) w.part[d + 1] = cadd(w.part[d + 1], pd);
+                }
+                __syncwarp();
+            }
+            kel_tail(s, n, w.pdet[D], D, want_part, sgn, w, lane, bad);
+        }
+    }
+    bad = __any_sync(0xffffffffu, bad);
+    const double nanv = __longlong_as_double(0x7ff8000000000000ll);
+    if (lane == 0) {
+        const double2 r = (bad || nonfin) ? make_double2(nanv, nanv) : w.part[n];
+        sum_out[0] = r.x;
+        sum_out[1] = r.y;
+        if (status_out) *status_out = (bad ? APM_ST_ZERO_PIVOT : 0u) | (nonfin ? APM_ST_NONFINITE_INPUT : 0u);
+    }
+    if (want_part && lane <= n) {
+        const double2 r = (bad || nonfin) ? make_double2(nanv, nanv) : w.part[lane];
+        partial_out[2 * lane] = r.x;
+        partial_out[2 * lane + 1] = r.y;
+    }
+    __syncwarp();
+}
+
 __global__ void __launch_bounds__(kKelWarps * 32) keldysh_kernel(
     const double2 *__restrict__ Mt, int n, int64_t batch, int sgn_flag, double *sum, double *partial,
     uint32_t *status, double2 *stack_base, size_t stack_per_warp) {
@@ -175,65 +237,52 @@ __global__ void __launch_bounds__(kKelWarps * 32) keldysh_kernel(
     const int64_t gw = static_cast<int64_t>(blockIdx.x) * kKelWarps + wid;
     const int64_t nw = static_cast<int64_t>(gridDim.x) * kKelWarps;
     double2 *stack = stack_base + gw * stack_per_warp;
-    const bool sgn = sgn_flag != 0;
-    const bool want_part = partial != nullptr;
-    const int s = n < kKelTail ? n : kKelTail;
-    const int D = n - s;
-    const int m0 = 2 * n;
-    for (int64_t b = gw; b < batch; b += nw) {
-        const double2 *A = Mt + b * static_cast<int64_t>(m0) * m0;
-        int bad = 0, nonfin = 0;
-        for (int e = lane; e < m0 * m0; e += 32) {
-            const double2 v = A[e];
-            if (!isfinite(v.x) || !isfinite(v.y)) nonfin = 1;
+    const int64_t m0 = 2 * n;
+    for (int64_t b = gw; b < batch; b += nw)
+        kel_matrix(Mt + b * m0 * m0, n, sgn_flag != 0, sum + 2 * b,
+                   partial ? partial + b * (n + 1) * 2 : nullptr, status ? status + b : nullptr, stack, w,
+                   lane);
+}
+
+// Uneven batch: warps take matrices longest-first from `order` through a
+// global counter. partial rows have 17 complex entries per matrix.
+__global__ void __launch_bounds__(kKelWarps * 32) keldysh_varlen_kernel(
+    const double2 *__restrict__ Mt, const int64_t *__restrict__ m_off, const int *__restrict__ n_arr,
+    int64_t batch, int n_max, int sgn_flag, double *sum, double *partial, uint32_t *status,
+    double2 *stack_base, size_t stack_per_warp, const int *__restrict__ order, unsigned *ctr) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    KelWarpSmem &w = reinterpret_cast<KelWarpSmem *>(smem_raw)[wid];
+    const int64_t gw = static_cast<int64_t>(blockIdx.x) * kKelWarps + wid;
+    double2 *stack = stack_base ? stack_base + gw * stack_per_warp : nullptr;
+    while (true) {
+        int item = 0;
+        if (lane == 0) item = static_cast<int>(atomicAdd(ctr, 1u));
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= batch) break;
+        const int b = order[item];
+        const int n = n_arr[b];
+        if (n < 1 || n > n_max) {
+            if (lane == 0 && status) status[b] = APM_ST_BAD_ORDER;
+            continue;
         }
-        nonfin = __any_sync(0xffffffffu, nonfin);
-        if (lane <= n) w.part[lane] = make_double2(lane == 0 ? 1.0 : 0.0, 0.0);
-        if (lane == 0) w.pdet[0] = make_double2(1.0, 0.0);
-        __syncwarp();
-        if (D == 0) {
-            for (int e = lane; e < m0 * m0; e += 32) w.bufE[e] = A[e];
-            __syncwarp();
-            kel_tail(s, n, make_double2(1.0, 0.0), 0, want_part, sgn, w, lane, bad);
-        } else {
-            // per-depth offsets of the stack (depth 1..D-1)
-            for (int64_t t = 0; t < (int64_t(1) << D); ++t) {
-                const int d0 = t == 0 ? 0 : D - 1 - __ffsll(t) + 1;
-                size_t off = 0;
-                for (int d = 1; d < d0; ++d) off += static_cast<size_t>(2 * (n - d)) * (2 * (n - d));
-                for (int d = d0; d < D; ++d) {
-                    const int alpha = static_cast<int>((t >> (D - 1 - d)) & 1);
-                    const int m = 2 * (n - d);
-                    const double2 *src = d == 0 ? A : stack + off;
-                    if (d > 0) off += static_cast<size_t>(m) * m;
-                    double2 *dst = (d + 1 == D) ? w.bufE : stack + off;
-                    double2 piv;
-                    kel_schur(src, m, alpha, dst, w, lane, piv, bad);
-                    if (lane == 0) {
-                        const double2 pd = cneg_if(cmul(w.pdet[d], piv), sgn && alpha);
-                        w.pdet[d + 1] = pd;
-                        if (want_part) w.part[d + 1] = cadd(w.part[d + 1], pd);
-                    }
-                    __syncwarp();
-                }
-                kel_tail(s, n, w.pdet[D], D, want_part, sgn, w, lane, bad);
-            }
-        }
-        bad = __any_sync(0xffffffffu, bad);
-        const double nanv = __longlong_as_double(0x7ff8000000000000ll);
-        if (lane == 0) {
-            const double2 r = (bad || nonfin) ? make_double2(nanv, nanv) : w.part[n];
-            sum[2 * b] = r.x;
-            sum[2 * b + 1] = r.y;
-            if (status) status[b] = (bad ? APM_ST_ZERO_PIVOT : 0u) | (nonfin ? APM_ST_NONFINITE_INPUT : 0u);
-        }
-        if (want_part && lane <= n) {
-            const double2 r = (bad || nonfin) ? make_double2(nanv, nanv) : w.part[lane];
-            partial[(b * (n + 1) + lane) * 2] = r.x;
-            partial[(b * (n + 1) + lane) * 2 + 1] = r.y;
-        }
-        __syncwarp();
+        kel_matrix(Mt + m_off[b], n, sgn_flag != 0, sum + 2 * static_cast<int64_t>(b),
+                   partial ? partial + static_cast<int64_t>(b) * 17 * 2 : nullptr, status ? status + b : nullptr,
+                   stack, w, lane);
     }
+}
+
+int launch_keldysh_varlen(const double *Mt, const int64_t *m_off, const int *n_arr, int64_t batch, int n_max,
+                          int sgn, double *sum, double *partial, uint32_t *status, void *stack,
+                          const int *order, unsigned *ctr, cudaStream_t s) {
+    int err = 0;
+    const int grid = keldysh_grid(batch, &err);
+    if (err) return err;
+    const size_t smem = kKelWarps * sizeof(KelWarpSmem);
+    keldysh_varlen_kernel<<<grid, kKelWarps * 32, smem, s>>>(
+        reinterpret_cast<const double2 *>(Mt), m_off, n_arr, batch, n_max, sgn, sum, partial, status,
+        static_cast<double2 *>(stack), kel_stack_entries(n_max), order, ctr);
+    return static_cast<int>(cudaGetLastError());
 }
 
 size_t keldysh_stack_entries(int n) { return kel_stack_entries(n); }

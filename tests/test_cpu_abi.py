@@ -55,3 +55,25 @@ def test_host_side_argument_errors(lib):
     assert b"WORKSPACE" in lib.apm_status_string(6)
     lib.apm_version.restype = ctypes.c_int
     assert lib.apm_version() >= 100
+
+
+def test_tune_tables_host_side(lib):
+    """The cost-model lane-group table is valid for every order, and invalid
+    tables are rejected on the host."""
+    P = ctypes.c_void_p
+    lib.apm_cdet_tune_get.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)]
+    lib.apm_cdet_tune_get.restype = ctypes.c_int
+    lib.apm_cdet_tune_set.argtypes = [P]
+    lib.apm_cdet_tune_set.restype = ctypes.c_int
+    for n in range(17):
+        out = ctypes.c_uint64(0)
+        assert lib.apm_cdet_tune_get(n, ctypes.byref(out)) == 0
+        for k in range(17):
+            r = (out.value >> (3 * k)) & 7
+            assert r <= 5 and (r == 0 or 2 <= k <= n) and r <= max(k - 1, 0)
+    bad = (ctypes.c_uint64 * 17)(*([0] * 17))
+    bad[4] = 7 << (3 * 3)           # r = 7 > 5
+    assert lib.apm_cdet_tune_set(ctypes.cast(bad, P)) == 1
+    bad[4] = 3 << (3 * 2)           # layer k = 2 allows r <= 1
+    assert lib.apm_cdet_tune_set(ctypes.cast(bad, P)) == 1
+    assert lib.apm_cdet_tune_set(None) == 0
