@@ -261,6 +261,84 @@ apm_status_t apm_keldysh_sum_varlen(const double *Mt, const int64_t *m_off, cons
 apm_status_t apm_cdet_tune_set(const uint64_t *table);
 apm_status_t apm_cdet_tune_get(int n, uint64_t *packed);
 
+/* ------------------------------------------------------------------------
+ * Learned Monte Carlo proposal (no counterpart in the paper: the paper's
+ * Monte Carlo context is the power series of Section V, Eq. series, sampled
+ * over vertex configurations with single-vertex moves, Section V.E).
+ *
+ * Walkers: X is [W][n][3] int32 vertices (x, y, m): a site of a win x win window
+ * and an imaginary-time grid index m in [0, mtau). The weight of a walker is
+ * |c_n(X)|, the full-set connected sum of apm_cdet_connected on the matrix
+ * M_ij = G0(r_i - r_j, tau_i - tau_j) built by apm_mc_build_matrices.
+ * Uniform random numbers are inputs (generated by the caller).
+ * ------------------------------------------------------------------------ */
+
+/* Xp = X with, for each walker w, vertex floor(u[w][0] n) redrawn uniformly
+ * from (u[w][1], u[w][2], u[w][3]). u: [W][4] float in [0,1). */
+apm_status_t apm_mc_propose(const int32_t *X, int W, int n, int win, int mtau, const float *u, int32_t *Xp,
+                            apm_stream_t stream);
+
+/* A[k] (n x n, FP64) = G0 matrix of walker idx[k] (idx NULL: walker k), k < count:
+ * A_ij = g0[|x_i-x_j|][|y_i-y_j|][m_i - m_j + mtau - 1]; g0 is [win][win][2 mtau - 1]
+ * FP64 (the table value at m_i = m_j is the tau -> 0^- limit). */
+apm_status_t apm_mc_build_matrices(const int32_t *X, const int32_t *idx, int count, int n, int win, int mtau,
+                                   const double *g0, double *A, apm_stream_t stream);
+
+/* Network inputs F [Bp][64] BF16 (raw uint16 storage) of walkers idx[k] (or k),
+ * k < count; rows count..Bp-1 are zero. Vertices sorted by time, shifted by the
+ * first, scaled by 1/win and 1/mtau: 3 values per vertex in 14 slots, then n/14.
+ * n <= 14. */
+apm_status_t apm_mc_features(const int32_t *X, const int32_t *idx, int count, int n, int win, int mtau,
+                             uint16_t *F, int Bp, apm_stream_t stream);
+
+/* Delayed acceptance, stage 1: walker w survives with probability
+ * min(1, exp(s_new[w] - s_old[w])) (u1[w] uniform); the survivors' indices are
+ * appended to idx (order unspecified) and their number written to *count
+ * (device int32, zeroed by the call). */
+apm_status_t apm_mc_stage1(const float *s_new, const float *s_old, const float *u1, int W, int32_t *idx,
+                           int32_t *count, apm_stream_t stream);
+
+/* Acceptance of the exactly evaluated candidates k < count (walker idx[k], or k
+ * when idx is NULL); c_full[k*stride] is the proposal's exact connected sum.
+ * Plain Metropolis (s_new NULL): accept if u2[w] < |c|/weight[w]. Delayed
+ * acceptance, stage 2: accept if u2[w] < |c| exp(s_cur[w]) / (weight[w] exp(s_new[w])).
+ * On acceptance X[w] = Xp[w], weight[w] = |c|, sign[w] = sign(c), s_cur[w] = s_new[w],
+ * and *accepted (device int32) is incremented. */
+apm_status_t apm_mc_accept(int32_t *X, const int32_t *Xp, double *weight, double *sign, float *s_cur,
+                           const float *s_new, const double *c_full, int64_t stride, const int32_t *idx, int count,
+                           const float *u2, int n, int32_t *accepted, apm_stream_t stream);
+
+/* Surrogate network: in 64 -> 256 -> 256 -> 256 -> 1 with ReLU, BF16 weights
+ * and activations, FP32 accumulation (mma.sync BF16 tensor-core tiles), FP32
+ * master weights and Adam moments. Parameter layout (APM_MLP_PARAMS floats):
+ * W1 [256][64], b1 [256], W2 [256][256], b2, W3 [256][256], b3, w4 [256], b4 [1],
+ * 7 floats padding; weight matrices stored [out][in]. All buffers device memory
+ * owned by the caller. */
+#define APM_MLP_IN 64
+#define APM_MLP_HIDDEN 256
+#define APM_MLP_PARAMS 148488
+typedef struct {
+    float *param;          /* [APM_MLP_PARAMS] FP32 master copy */
+    uint16_t *param_bf16;  /* [APM_MLP_PARAMS] BF16 copy read by the forward pass */
+    float *grad;           /* [APM_MLP_PARAMS] */
+    float *adam_m;         /* [APM_MLP_PARAMS] */
+    float *adam_v;         /* [APM_MLP_PARAMS] */
+} apm_mlp;
+
+/* scratch for a batch of batch_padded rows (a multiple of 64) */
+apm_status_t apm_mlp_workspace_size(int batch_padded, size_t *bytes);
+/* refresh param_bf16 from param (after the caller initialises param) */
+apm_status_t apm_mlp_sync_bf16(const apm_mlp *net, apm_stream_t stream);
+/* y[b] (FP32) = network(X[b]) for b < batch_padded; X [batch_padded][64] BF16 */
+apm_status_t apm_mlp_forward(const apm_mlp *net, const uint16_t *X, int batch_padded, float *y, void *workspace,
+                             size_t workspace_bytes, apm_stream_t stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr, step >= 1
+ * for the bias correction) on the mean squared error over the first batch_valid
+ * rows; adds the loss to *loss_acc (device float). */
+apm_status_t apm_mlp_train_step(const apm_mlp *net, const uint16_t *X, const float *target, int batch_padded,
+                                int batch_valid, float lr, int step, float *loss_acc, void *workspace,
+                                size_t workspace_bytes, apm_stream_t stream);
+
 /*
  * apm_workspace_size -- bytes of device scratch the call `op` needs for orders up
  * to n_max and `batch` matrices on the current device (0 when none is needed).

@@ -72,6 +72,39 @@ int launch_keldysh_varlen(const double *Mt, const int64_t *m_off, const int *n_a
                           int sgn, double *sum, double *partial, uint32_t *status, void *stack,
                           const int *order, unsigned *ctr, cudaStream_t s);
 
+// surrogate network
+constexpr int kMlpIn = 64, kMlpH = 256;
+constexpr int kOffW1 = 0;
+constexpr int kOffB1 = kOffW1 + kMlpH * kMlpIn;
+constexpr int kOffW2 = kOffB1 + kMlpH;
+constexpr int kOffB2 = kOffW2 + kMlpH * kMlpH;
+constexpr int kOffW3 = kOffB2 + kMlpH;
+constexpr int kOffB3 = kOffW3 + kMlpH * kMlpH;
+constexpr int kOffW4 = kOffB3 + kMlpH;
+constexpr int kOffB4 = kOffW4 + kMlpH;
+constexpr int kMlpParams = kOffB4 + 8;
+static_assert(kMlpParams == APM_MLP_PARAMS, "parameter count");
+}  // namespace apm
+#include <cuda_bf16.h>
+namespace apm {
+struct MlpParams {
+    float *param, *grad, *m, *v;
+    __nv_bfloat16 *pb;
+    const __nv_bfloat16 *w1b, *w2b, *w3b, *w4b;
+    const float *b1, *b2, *b3, *b4;
+};
+struct MlpWork {
+    __nv_bfloat16 *h1, *h2, *h3, *dzb, *t1, *t2, *wt;
+    float *y, *dy, *dz32, *dh32;
+};
+size_t mlp_workspace_bytes(int Bp);
+void mlp_bind(const apm_mlp *net, MlpParams &P);
+void mlp_work(void *ws, int Bp, MlpWork &w);
+int mlp_forward(const MlpParams &P, const __nv_bfloat16 *X, int Bp, float *y, MlpWork &w, cudaStream_t s);
+int mlp_train_step(MlpParams &P, const __nv_bfloat16 *X, const float *target, int Bp, int B_valid, MlpWork &w,
+                   float lr, int step, float *loss_acc, cudaStream_t s);
+int mlp_refresh_bf16(MlpParams &P, cudaStream_t s);
+
 int launch_fp64_probe(double *sink, int blocks, int threads, int iters, cudaStream_t s);
 
 }  // namespace apm

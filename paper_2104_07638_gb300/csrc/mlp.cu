@@ -1,0 +1,327 @@
+// Surrogate network of the learned Monte Carlo proposal: a 4-layer MLP
+// (in 64 -> 256 -> 256 -> 256 -> 1, ReLU) with BF16 weights and activations,
+// FP32 accumulation and FP32 master weights trained by Adam.
+//
+// GEMMs are "TN": C[M x N] = A[M x K] * Bt[N x K]^T (both operands K-contiguous
+// BF16), computed with warp-level mma.sync m16n8k16 BF16 -> FP32 on 64x64 CTA
+// tiles (4 warps, 32x32 each), K staged through shared memory in steps of 32.
+// M, N multiples of 64, K a multiple of 32. The network is tiny next to the
+// FP64 minor kernels; these kernels only need to be correct and cheap.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "apm_internal.cuh"
+
+namespace apm {
+
+constexpr int kTile = 64;
+constexpr int kKStep = 32;
+constexpr int kPad = 8;  // bf16 padding per shared row (bank-conflict relief)
+
+__device__ __forceinline__ uint32_t ld_pair(const __nv_bfloat16 *p) {
+    return *reinterpret_cast<const uint32_t *>(p);
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// C = A * Bt^T (+ bias) (ReLU if relu); writes C32 (if not NULL) and Cb (bf16, if not NULL)
+__global__ void __launch_bounds__(128) gemm_tn_kernel(const __nv_bfloat16 *__restrict__ A,
+                                                      const __nv_bfloat16 *__restrict__ Bt,
+                                                      const float *__restrict__ bias, float *C32,
+                                                      __nv_bfloat16 *Cb, int M, int N, int K, int relu) {
+    __shared__ __align__(16) __nv_bfloat16 As[kTile][kKStep + kPad];
+    __shared__ __align__(16) __nv_bfloat16 Bs[kTile][kKStep + kPad];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp >> 1, wn = warp & 1;
+    const int g = lane >> 2, t = lane & 3;
+    const int m0 = blockIdx.y * kTile, n0 = blockIdx.x * kTile;
+    float acc[2][4][4] = {};
+    for (int k0 = 0; k0 < K; k0 += kKStep) {
+        // 64 rows x 32 bf16 = 256 chunks of 8 bf16 (16 B) per operand; 2 per thread
+        for (int c = tid; c < 256; c += 128) {
+            const int r = c >> 2, q = (c & 3) * 8;
+            *reinterpret_cast<uint4 *>(&As[r][q]) =
+                *reinterpret_cast<const uint4 *>(A + static_cast<size_t>(m0 + r) * K + k0 + q);
+            *reinterpret_cast<uint4 *>(&Bs[r][q]) =
+                *reinterpret_cast<const uint4 *>(Bt + static_cast<size_t>(n0 + r) * K + k0 + q);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < kKStep; kk += 16) {
+            uint32_t af[2][4], bfr[4][2];
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                const int r = wm * 32 + mt * 16 + g;
+                af[mt][0] = ld_pair(&As[r][kk + 2 * t]);
+                af[mt][1] = ld_pair(&As[r + 8][kk + 2 * t]);
+                af[mt][2] = ld_pair(&As[r][kk + 2 * t + 8]);
+                af[mt][3] = ld_pair(&As[r + 8][kk + 2 * t + 8]);
+            }
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+                const int r = wn * 32 + nt * 8 + g;
+                bfr[nt][0] = ld_pair(&Bs[r][kk + 2 * t]);
+                bfr[nt][1] = ld_pair(&Bs[r][kk + 2 * t + 8]);
+            }
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt)
+                    mma_bf16(acc[mt][nt], af[mt][0], af[mt][1], af[mt][2], af[mt][3], bfr[nt][0], bfr[nt][1]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int row = m0 + wm * 32 + mt * 16 + g + 8 * h;
+                const int col = n0 + wn * 32 + nt * 8 + 2 * t;
+                float v0 = acc[mt][nt][2 * h], v1 = acc[mt][nt][2 * h + 1];
+                if (bias) {
+                    v0 += bias[col];
+                    v1 += bias[col + 1];
+                }
+                if (relu) {
+                    v0 = fmaxf(v0, 0.f);
+                    v1 = fmaxf(v1, 0.f);
+                }
+                const size_t o = static_cast<size_t>(row) * N + col;
+                if (C32) {
+                    C32[o] = v0;
+                    C32[o + 1] = v1;
+                }
+                if (Cb) *reinterpret_cast<__nv_bfloat162 *>(Cb + o) = __floats2bfloat162_rn(v0, v1);
+            }
+}
+
+// bf16 transpose: out[c][r] = in[r][c], in is R x C
+__global__ void transpose_bf16_kernel(const __nv_bfloat16 *__restrict__ in, __nv_bfloat16 *out, int R, int C) {
+    __shared__ __nv_bfloat16 tile[32][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int r = r0 + i, c = c0 + threadIdx.x;
+        if (r < R && c < C) tile[i][threadIdx.x] = in[static_cast<size_t>(r) * C + c];
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int c = c0 + i, r = r0 + threadIdx.x;
+        if (r < R && c < C) out[static_cast<size_t>(c) * R + r] = tile[threadIdx.x][i];
+    }
+}
+
+// last layer: y[b] = sum_i H[b][i] w[i] + b0 (one warp per row, 256 inputs)
+__global__ void head_forward_kernel(const __nv_bfloat16 *__restrict__ H, const __nv_bfloat16 *__restrict__ w,
+                                    const float *__restrict__ b0, float *y, int B, int D) {
+    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= B) return;
+    float s = 0.f;
+    for (int i = lane; i < D; i += 32)
+        s = fmaf(__bfloat162float(H[static_cast<size_t>(row) * D + i]), __bfloat162float(w[i]), s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) y[row] = s + b0[0];
+}
+
+// dy = 2 (y - target) / B_valid for rows < B_valid (0 for padding rows); loss partial sums
+__global__ void mse_grad_kernel(const float *__restrict__ y, const float *__restrict__ target, float *dy,
+                                int Bp, int B_valid, float *loss_acc) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Bp) return;
+    float d = 0.f;
+    if (i < B_valid) {
+        const float e = y[i] - target[i];
+        d = 2.f * e / static_cast<float>(B_valid);
+        atomicAdd(loss_acc, e * e / static_cast<float>(B_valid));
+    }
+    dy[i] = d;
+}
+
+// head backward: dZ[b][i] = (H[b][i] > 0) ? dy[b] * w[i] : 0 (fp32 and bf16);
+// dw[i] += sum_b dy[b] H[b][i]; db += sum_b dy[b]; dbz[i] += sum_b dZ[b][i]
+// (atomic partial sums per block of rows)
+__global__ void head_backward_kernel(const __nv_bfloat16 *__restrict__ H, const __nv_bfloat16 *__restrict__ w,
+                                     const float *__restrict__ dy, float *dZ32, __nv_bfloat16 *dZb, float *dw,
+                                     float *db, float *dbz, int Bp, int D, int rows_per_block) {
+    const int i = threadIdx.x;  // column, blockDim.x == D
+    const int r0 = blockIdx.x * rows_per_block;
+    float accw = 0.f, accb = 0.f, accz = 0.f;
+    const float wi = __bfloat162float(w[i]);
+    for (int r = r0; r < r0 + rows_per_block && r < Bp; ++r) {
+        const float h = __bfloat162float(H[static_cast<size_t>(r) * D + i]);
+        const float g = dy[r];
+        const float z = h > 0.f ? g * wi : 0.f;
+        dZ32[static_cast<size_t>(r) * D + i] = z;
+        dZb[static_cast<size_t>(r) * D + i] = __float2bfloat16_rn(z);
+        accw = fmaf(g, h, accw);
+        accb += g;
+        accz += z;
+    }
+    atomicAdd(&dw[i], accw);
+    atomicAdd(&dbz[i], accz);
+    if (i == 0) atomicAdd(db, accb);
+}
+
+// dZ = dH * (H > 0) (fp32 in, fp32 + bf16 out) and column sums into db
+__global__ void relu_backward_kernel(const float *__restrict__ dH, const __nv_bfloat16 *__restrict__ H,
+                                     float *dZ32, __nv_bfloat16 *dZb, float *db, int Bp, int D,
+                                     int rows_per_block) {
+    const int i = threadIdx.x;
+    const int r0 = blockIdx.x * rows_per_block;
+    float acc = 0.f;
+    for (int r = r0; r < r0 + rows_per_block && r < Bp; ++r) {
+        const size_t o = static_cast<size_t>(r) * D + i;
+        const float z = __bfloat162float(H[o]) > 0.f ? dH[o] : 0.f;
+        dZ32[o] = z;
+        dZb[o] = __float2bfloat16_rn(z);
+        acc += z;
+    }
+    atomicAdd(&db[i], acc);
+}
+
+// Adam on the flat fp32 parameter vector; refreshes the bf16 copy
+__global__ void adam_kernel(float *p, const float *g, float *m, float *v, __nv_bfloat16 *pb, int count, float lr,
+                            float b1, float b2, float eps, float c1, float c2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    p[i] = pi;
+    pb[i] = __float2bfloat16_rn(pi);
+}
+
+__global__ void f32_to_bf16_kernel(const float *in, __nv_bfloat16 *out, int count) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) out[i] = __float2bfloat16_rn(in[i]);
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+static size_t al(size_t x) { return (x + 255) & ~size_t(255); }
+
+size_t mlp_workspace_bytes(int Bp) {
+    const size_t act = static_cast<size_t>(Bp) * kMlpH;
+    return 3 * al(act * 2) + 2 * al(static_cast<size_t>(Bp) * 4) + 2 * al(act * 4) + al(act * 2) +
+           2 * al(act * 2) + al(static_cast<size_t>(kMlpH) * kMlpH * 2);
+}
+
+void mlp_work(void *ws, int Bp, MlpWork &w) {
+    unsigned char *p = static_cast<unsigned char *>(ws);
+    const size_t act = static_cast<size_t>(Bp) * kMlpH;
+    auto take = [&](size_t bytes) {
+        unsigned char *q = p;
+        p += al(bytes);
+        return q;
+    };
+    w.h1 = reinterpret_cast<__nv_bfloat16 *>(take(act * 2));
+    w.h2 = reinterpret_cast<__nv_bfloat16 *>(take(act * 2));
+    w.h3 = reinterpret_cast<__nv_bfloat16 *>(take(act * 2));
+    w.y = reinterpret_cast<float *>(take(static_cast<size_t>(Bp) * 4));
+    w.dy = reinterpret_cast<float *>(take(static_cast<size_t>(Bp) * 4));
+    w.dz32 = reinterpret_cast<float *>(take(act * 4));
+    w.dh32 = reinterpret_cast<float *>(take(act * 4));
+    w.dzb = reinterpret_cast<__nv_bfloat16 *>(take(act * 2));
+    w.t1 = reinterpret_cast<__nv_bfloat16 *>(take(act * 2));
+    w.t2 = reinterpret_cast<__nv_bfloat16 *>(take(act * 2));
+    w.wt = reinterpret_cast<__nv_bfloat16 *>(take(static_cast<size_t>(kMlpH) * kMlpH * 2));
+}
+
+void mlp_bind(const apm_mlp *net, MlpParams &P) {
+    P.param = net->param;
+    P.grad = net->grad;
+    P.m = net->adam_m;
+    P.v = net->adam_v;
+    P.pb = reinterpret_cast<__nv_bfloat16 *>(net->param_bf16);
+    P.w1b = P.pb + kOffW1;
+    P.w2b = P.pb + kOffW2;
+    P.w3b = P.pb + kOffW3;
+    P.w4b = P.pb + kOffW4;
+    P.b1 = P.param + kOffB1;
+    P.b2 = P.param + kOffB2;
+    P.b3 = P.param + kOffB3;
+    P.b4 = P.param + kOffB4;
+}
+
+static int gemm_tn(const __nv_bfloat16 *A, const __nv_bfloat16 *Bt, const float *bias, float *C32,
+                   __nv_bfloat16 *Cb, int M, int N, int K, int relu, cudaStream_t s) {
+    dim3 grid(N / kTile, M / kTile);
+    gemm_tn_kernel<<<grid, 128, 0, s>>>(A, Bt, bias, C32, Cb, M, N, K, relu);
+    return static_cast<int>(cudaGetLastError());
+}
+
+static int transpose(const __nv_bfloat16 *in, __nv_bfloat16 *out, int R, int C, cudaStream_t s) {
+    dim3 grid((C + 31) / 32, (R + 31) / 32);
+    transpose_bf16_kernel<<<grid, dim3(32, 8), 0, s>>>(in, out, R, C);
+    return static_cast<int>(cudaGetLastError());
+}
+
+int mlp_forward(const MlpParams &P, const __nv_bfloat16 *X, int Bp, float *y, MlpWork &w, cudaStream_t s) {
+    int e;
+    if ((e = gemm_tn(X, P.w1b, P.b1, nullptr, w.h1, Bp, kMlpH, kMlpIn, 1, s))) return e;
+    if ((e = gemm_tn(w.h1, P.w2b, P.b2, nullptr, w.h2, Bp, kMlpH, kMlpH, 1, s))) return e;
+    if ((e = gemm_tn(w.h2, P.w3b, P.b3, nullptr, w.h3, Bp, kMlpH, kMlpH, 1, s))) return e;
+    head_forward_kernel<<<(Bp + 7) / 8, 256, 0, s>>>(w.h3, P.w4b, P.b4, y, Bp, kMlpH);
+    return static_cast<int>(cudaGetLastError());
+}
+
+int mlp_train_step(MlpParams &P, const __nv_bfloat16 *X, const float *target, int Bp, int B_valid, MlpWork &w,
+                   float lr, int step, float *loss_acc, cudaStream_t s) {
+    int e;
+    if ((e = mlp_forward(P, X, Bp, w.y, w, s))) return e;
+    cudaMemsetAsync(P.grad, 0, sizeof(float) * kMlpParams, s);
+    mse_grad_kernel<<<(Bp + 255) / 256, 256, 0, s>>>(w.y, target, w.dy, Bp, B_valid, loss_acc);
+    const int rpb = 64;
+    float *g = P.grad;
+    float *gw1 = g + kOffW1, *gb1 = g + kOffB1, *gw2 = g + kOffW2, *gb2 = g + kOffB2;
+    float *gw3 = g + kOffW3, *gb3 = g + kOffB3, *gw4 = g + kOffW4, *gb4 = g + kOffB4;
+    // head: dZ3 = dH3 * (H3 > 0), dw4, db4, db3 = column sums of dZ3
+    head_backward_kernel<<<(Bp + rpb - 1) / rpb, kMlpH, 0, s>>>(w.h3, P.w4b, w.dy, w.dz32, w.dzb, gw4, gb4, gb3,
+                                                                Bp, kMlpH, rpb);
+    // layer 3: dW3 = dZ3^T H2 ; dH2 = dZ3 W3
+    if ((e = transpose(w.dzb, w.t1, Bp, kMlpH, s))) return e;  // dZ3^T [256 x Bp]
+    if ((e = transpose(w.h2, w.t2, Bp, kMlpH, s))) return e;   // H2^T  [256 x Bp]
+    if ((e = gemm_tn(w.t1, w.t2, nullptr, gw3, nullptr, kMlpH, kMlpH, Bp, 0, s))) return e;
+    if ((e = transpose(P.w3b, w.wt, kMlpH, kMlpH, s))) return e;  // W3 stored [out x in] -> [in x out]
+    if ((e = gemm_tn(w.dzb, w.wt, nullptr, w.dh32, nullptr, Bp, kMlpH, kMlpH, 0, s))) return e;
+    // layer 2
+    relu_backward_kernel<<<(Bp + rpb - 1) / rpb, kMlpH, 0, s>>>(w.dh32, w.h2, w.dz32, w.dzb, gb2, Bp, kMlpH, rpb);
+    if ((e = transpose(w.dzb, w.t1, Bp, kMlpH, s))) return e;  // dZ2^T
+    if ((e = transpose(w.h1, w.t2, Bp, kMlpH, s))) return e;   // H1^T
+    if ((e = gemm_tn(w.t1, w.t2, nullptr, gw2, nullptr, kMlpH, kMlpH, Bp, 0, s))) return e;
+    if ((e = transpose(P.w2b, w.wt, kMlpH, kMlpH, s))) return e;
+    if ((e = gemm_tn(w.dzb, w.wt, nullptr, w.dh32, nullptr, Bp, kMlpH, kMlpH, 0, s))) return e;
+    // layer 1
+    relu_backward_kernel<<<(Bp + rpb - 1) / rpb, kMlpH, 0, s>>>(w.dh32, w.h1, w.dz32, w.dzb, gb1, Bp, kMlpH, rpb);
+    if ((e = transpose(w.dzb, w.t1, Bp, kMlpH, s))) return e;  // dZ1^T [256 x Bp]
+    if ((e = transpose(X, w.t2, Bp, kMlpIn, s))) return e;     // X^T   [64 x Bp]
+    if ((e = gemm_tn(w.t1, w.t2, nullptr, gw1, nullptr, kMlpH, kMlpIn, Bp, 0, s))) return e;
+    // Adam
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    const float c1 = 1.f - powf(b1, static_cast<float>(step)), c2 = 1.f - powf(b2, static_cast<float>(step));
+    adam_kernel<<<(kMlpParams + 255) / 256, 256, 0, s>>>(P.param, P.grad, P.m, P.v, P.pb, kMlpParams, lr, b1, b2,
+                                                         eps, c1, c2);
+    return static_cast<int>(cudaGetLastError());
+}
+
+int mlp_refresh_bf16(MlpParams &P, cudaStream_t s) {
+    f32_to_bf16_kernel<<<(kMlpParams + 255) / 256, 256, 0, s>>>(P.param, P.pb, kMlpParams);
+    return static_cast<int>(cudaGetLastError());
+}
+
+}  // namespace apm
