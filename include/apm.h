@@ -286,10 +286,11 @@ apm_status_t apm_mc_build_matrices(const int32_t *X, const int32_t *idx, int cou
 
 /* Network inputs F [Bp][64] BF16 (raw uint16 storage) of walkers idx[k] (or k),
  * k < count; rows count..Bp-1 are zero. Vertices sorted by time, shifted by the
- * first, scaled by 1/win and 1/mtau: 3 values per vertex in 14 slots, then n/14.
- * n <= 14. */
+ * first, scaled by 1/win and 1/mtau: 3 values per vertex in 14 slots (0..41),
+ * n/14 (42), then in 14 slots (43..56) the ascending values of
+ * 0.25 log10 sum_{j != i} |G0(X_i - X_j)| (g0 table as above). n <= 14. */
 apm_status_t apm_mc_features(const int32_t *X, const int32_t *idx, int count, int n, int win, int mtau,
-                             uint16_t *F, int Bp, apm_stream_t stream);
+                             const double *g0, uint16_t *F, int Bp, apm_stream_t stream);
 
 /* Delayed acceptance, stage 1: walker w survives with probability
  * min(1, exp(s_new[w] - s_old[w])) (u1[w] uniform); the survivors' indices are

@@ -52,9 +52,12 @@ __global__ void mc_build_kernel(const int *__restrict__ X, const int *__restrict
 }
 
 // network input of walker idx[k] (or k): vertices sorted by time, shifted by
-// the first one, scaled to [-1, 1]; 14 vertex slots x 3, then n/14; zero padding
+// the first one, scaled to [-1, 1] (14 vertex slots x 3); then n/14; then, in
+// 14 slots sorted ascending, log10 of each vertex's coupling to the others,
+// sum_{j != i} |G0(X_i - X_j)| (a weakly coupled vertex makes the connected sum
+// small); zero padding.
 __global__ void mc_features_kernel(const int *__restrict__ X, const int *__restrict__ idx, int count, int n,
-                                   int win, int mtau, __nv_bfloat16 *F, int Bp) {
+                                   int win, int mtau, const double *__restrict__ g0, __nv_bfloat16 *F, int Bp) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= Bp) return;
     __nv_bfloat16 *f = F + static_cast<size_t>(k) * kMlpIn;
@@ -82,6 +85,27 @@ __global__ void mc_features_kernel(const int *__restrict__ X, const int *__restr
         f[3 * i + 2] = __float2bfloat16_rn((xw[3 * o + 2] - m0) * sm);
     }
     f[42] = __float2bfloat16_rn(n / 14.f);
+    float cpl[16];
+    for (int i = 0; i < n; ++i) {
+        double sum = 0.0;
+        for (int j = 0; j < n; ++j) {
+            if (j == i) continue;
+            const int dx = abs(xw[3 * i] - xw[3 * j]), dy = abs(xw[3 * i + 1] - xw[3 * j + 1]);
+            const int dm = xw[3 * i + 2] - xw[3 * j + 2] + mtau - 1;
+            sum += fabs(g0[(static_cast<size_t>(dx) * win + dy) * (2 * mtau - 1) + dm]);
+        }
+        cpl[i] = log10f(static_cast<float>(sum) + 1e-30f);
+    }
+    for (int i = 1; i < n; ++i) {  // ascending
+        const float v = cpl[i];
+        int j = i - 1;
+        while (j >= 0 && cpl[j] > v) {
+            cpl[j + 1] = cpl[j];
+            --j;
+        }
+        cpl[j + 1] = v;
+    }
+    for (int i = 0; i < n && i < 14; ++i) f[43 + i] = __float2bfloat16_rn(0.25f * cpl[i]);
 }
 
 // stage 1 of delayed acceptance: compacted list of surviving walkers
@@ -144,12 +168,12 @@ apm_status_t apm_mc_build_matrices(const int32_t *X, const int32_t *idx, int cou
 }
 
 apm_status_t apm_mc_features(const int32_t *X, const int32_t *idx, int count, int n, int win, int mtau,
-                             uint16_t *F, int Bp, apm_stream_t stream) {
+                             const double *g0, uint16_t *F, int Bp, apm_stream_t stream) {
     if (count < 0 || Bp < count || n < 1 || n > 14 || win < 1 || mtau < 1) return APM_ERR_ARG;
     if (Bp == 0) return APM_OK;
-    if (!X || !F) return APM_ERR_ARG;
+    if (!X || !F || !g0) return APM_ERR_ARG;
     mc_features_kernel<<<(Bp + 127) / 128, 128, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
-        X, idx, count, n, win, mtau, reinterpret_cast<__nv_bfloat16 *>(F), Bp);
+        X, idx, count, n, win, mtau, g0, reinterpret_cast<__nv_bfloat16 *>(F), Bp);
     return cudaGetLastError() == cudaSuccess ? APM_OK : APM_ERR_CUDA;
 }
 

@@ -39,7 +39,7 @@ def _sig(L):
     for name, args in {
         "apm_mc_propose": [P, i32, i32, i32, i32, P, P, P],
         "apm_mc_build_matrices": [P, P, i32, i32, i32, i32, P, P, P],
-        "apm_mc_features": [P, P, i32, i32, i32, i32, P, i32, P],
+        "apm_mc_features": [P, P, i32, i32, i32, i32, P, P, i32, P],
         "apm_mc_stage1": [P, P, P, i32, P, P, P],
         "apm_mc_accept": [P, P, P, P, P, P, P, i64, P, i32, P, i32, P, P],
         "apm_mlp_workspace_size": [i32, ctypes.POINTER(sz)],
@@ -178,8 +178,8 @@ class Walkers:
 
     def features(self, X, F, idx=None, count=None):
         count = self.W if count is None else count
-        apm._check(lib().apm_mc_features(_p(X), _p(idx), count, self.n, self.win, self.mtau, _p(F), F.shape[0],
-                                         _s(X)), "apm_mc_features")
+        apm._check(lib().apm_mc_features(_p(X), _p(idx), count, self.n, self.win, self.mtau, _p(self.g0), _p(F),
+                                         F.shape[0], _s(X)), "apm_mc_features")
 
     def step_plain(self, record=None):
         self._propose()

@@ -32,7 +32,7 @@ def test_forward_and_gradients_match_fp64_reference(mc):
     rng = np.random.default_rng(8)
     B = 256
     X = torch.as_tensor(rng.standard_normal((B, 64)) * 0.5, dtype=torch.float32)
-    X[:, 43:] = 0.0
+    X[:, 57:] = 0.0
     Xb = bf16_bits(X).cuda()
     t = torch.as_tensor(rng.standard_normal(B), dtype=torch.float32).cuda()
     flat = net.param.cpu().numpy().astype(np.float64)
