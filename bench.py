@@ -68,6 +68,9 @@ def parse():
     ap.add_argument("--batch", type=int, default=BATCH)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-rows", action="store_true",
+                    help="skip the per-row measurements of the other hot-path steps")
+    ap.add_argument("--mc-steps", type=int, default=100)
     return ap.parse_args()
 
 
@@ -126,6 +129,125 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def keldysh_flops(n: int) -> int:
+    """Algorithmic flops of one Keldysh sum: complex FMAs of every Schur step of
+    the XOR tree (8 real flops each), pivot reciprocals/products, leaf sums."""
+    return (8 * sum((1 << (l + 1)) * (2 * (n - l - 1)) ** 2 for l in range(n - 1))
+            + 12 * (2 ** (n + 1) - 2) + 2 * 2 ** n)
+
+
+def perm_flops(n: int) -> int:
+    """Algorithmic flops of all permanent minors: one product and one addition
+    per (T subset of S) pair, plus the row sums."""
+    return 2 * 3 ** n + n * 2 ** n
+
+
+def _event_ms(fn, reps=3):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def measure_rows(args, dev, peak):
+    """One measurement per remaining hot-path step on its configuration."""
+    import numpy as np
+    import torch
+    from paper_2104_07638_gb300 import apm, inputs, mc
+    from paper_2104_07638_gb300.batch import CdetVarlenGraph, KeldyshVarlenGraph
+    rows = {}
+    # a7: uneven batch of 131072 walkers, n uniform in 4..16, minors + connected sums, graph replay
+    orders = inputs.varlen_orders(131072, 4, 16, seed=3)
+    flat, off = inputs.hubbard_varlen(orders, seed=3)
+    A = torch.as_tensor(flat).to(dev)
+    a_off = torch.as_tensor(off).to(dev)
+    n_t = torch.as_tensor(orders).to(dev)
+    g = CdetVarlenGraph(A, a_off, n_t)
+    ms = _event_ms(g.replay)
+    fl = sum(flops_per_set(int(k)) for k in orders)
+    rows["a7_cdet_uneven_131072_n4to16"] = {
+        "value": orders.size / (ms * 1e-3), "unit": "minor-sets/s", "ms": ms,
+        "tflops": fl / (ms * 1e-3) / 1e12, "frac_fp64_peak": fl / (ms * 1e-3) / 1e12 / peak,
+        "launch": "CUDA graph: counting sort by order + one persistent longest-first kernel"}
+    del g, A
+    # a5 on the same uneven orders: Keldysh sums of 1D-chain real-time G0
+    kflat, koff = inputs.keldysh_varlen(orders, seed=3)
+    Mt = torch.as_tensor(kflat).to(dev)
+    m_off = torch.as_tensor(koff).to(dev)
+    kg = KeldyshVarlenGraph(Mt, m_off, n_t)
+    ms = _event_ms(kg.replay)
+    fl = sum(keldysh_flops(int(k)) for k in orders)
+    rows["a5_keldysh_uneven_131072_n4to16"] = {
+        "value": orders.size / (ms * 1e-3), "unit": "sums/s", "ms": ms,
+        "tflops": fl / (ms * 1e-3) / 1e12, "frac_fp64_peak": fl / (ms * 1e-3) / 1e12 / peak}
+    del kg, Mt
+    # a6: permanent minors, 4096 masked-uniform matrices of order 14
+    P = torch.as_tensor(inputs.perm_batch(14, 4096, seed=4)).to(dev)
+    ms = _event_ms(lambda: apm.perm_minors(P))
+    fl = 4096 * perm_flops(14)
+    rows["a6_perm_minors_4096_n14"] = {
+        "value": 4096 / (ms * 1e-3), "unit": "perm-minor-sets/s", "ms": ms,
+        "tflops": fl / (ms * 1e-3) / 1e12, "frac_fp64_peak": fl / (ms * 1e-3) / 1e12 / peak}
+    del P
+    # a8: learned proposal vs plain, 16384 walkers at each order 10..14
+    G = torch.as_tensor(inputs.hubbard_g0_table()).to(dev)
+    W, T = 16384, args.mc_steps
+    walkers, feats, targs = {}, [], []
+    t_collect = 0.0
+    for n in range(10, 15):
+        wk = mc.Walkers(W, n, G, inputs.HUB_WIN, inputs.HUB_MTAU, seed=100 + n)
+        (F, t), dt = mc.timed(lambda: wk.collect(30))
+        t_collect += dt
+        feats.append(F)
+        targs.append(t)
+        walkers[n] = wk
+    net = mc.Surrogate(seed=7, max_batch=W)
+    losses, t_train = mc.timed(lambda: net.train(torch.cat(feats), torch.cat(targs), epochs=4, batch=4096,
+                                                 lr=1e-3))
+    per_n = {}
+    tot = {"plain_ess": 0.0, "plain_s": 0.0, "learned_ess": 0.0, "learned_s": 0.0}
+    for n, wk in walkers.items():
+        X0, w0, s0 = wk.X.clone(), wk.weight.clone(), wk.sign.clone()
+        rec = []
+        e0 = wk.exact_evals
+        _, tp = mc.timed(lambda: [wk.step_plain(rec) for _ in range(T)])
+        ep, ess_p = wk.exact_evals - e0, mc.ess(rec, 1)
+        wk.X.copy_(X0); wk.weight.copy_(w0); wk.sign.copy_(s0)
+        rec = []
+        e0 = wk.exact_evals
+
+        def run_learned():
+            wk.init_surrogate(net)
+            for _ in range(T):
+                wk.step_da(net, rec)
+        _, tl = mc.timed(run_learned)
+        el, ess_l = wk.exact_evals - e0, mc.ess(rec, 1)
+        per_n[str(n)] = {"plain_ess_per_s": ess_p / tp, "learned_ess_per_s": ess_l / tl,
+                         "plain_exact_evals_per_ess": ep / ess_p, "learned_exact_evals_per_ess": el / ess_l}
+        tot["plain_ess"] += ess_p
+        tot["plain_s"] += tp
+        tot["learned_ess"] += ess_l
+        tot["learned_s"] += tl
+    t_net = t_train  # the training pairs come from plain steps that also sample; only training is extra
+    rows["a8_learned_proposal_16384_walkers_n10to14"] = {
+        "metric": "effective samples/s of log|c_n| (Sokal window), all orders 10..14",
+        "plain_ess_per_s": tot["plain_ess"] / tot["plain_s"],
+        "learned_ess_per_s": tot["learned_ess"] / tot["learned_s"],
+        "learned_ess_per_s_incl_training": tot["learned_ess"] / (tot["learned_s"] + t_net),
+        "gain": (tot["learned_ess"] / tot["learned_s"]) / (tot["plain_ess"] / tot["plain_s"]),
+        "gain_incl_training": (tot["learned_ess"] / (tot["learned_s"] + t_net)) /
+                              (tot["plain_ess"] / tot["plain_s"]),
+        "steps_per_chain": T, "train_s": t_train, "collect_s": t_collect,
+        "final_train_loss": float(np.mean(losses[-5:])), "per_order": per_n}
+    return rows
 
 
 def cpu_oracle_rate(A_np, seconds: float):
@@ -318,6 +440,8 @@ def main():
         "clocks": clocks,
         "wall_s_timed_region": t_wall,
     }
+    if rank == 0 and not args.no_rows:
+        result["rows"] = measure_rows(args, dev, peak)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r, threads, count, dt = cpu_oracle_rate(A_np, args.cpu_seconds)
         result["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": threads, "kind": "oracle",
