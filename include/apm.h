@@ -194,8 +194,8 @@ apm_status_t apm_keldysh_sum_noalloc(const double *Mt, int n, int64_t batch, int
  *   n      1..APM_MAX_N_PERM.
  *   workspace / workspace_bytes: unused (pass NULL, 0); kept for a uniform
  *          signature with the other batched calls.
- *   Summation order differs from run to run (products from different T are
- *   accumulated with atomic adds), so results agree to rounding, not bitwise.
+ *   The output rows double as accumulators; the summation order is fixed, so
+ *   repeated calls give bit-identical results.
  */
 apm_status_t apm_perm_minors(const double *A, int n, int64_t batch, double *perms,
                              void *workspace, size_t workspace_bytes, apm_stream_t stream);

@@ -1,181 +1,311 @@
 // All permanent principal minors in O(3^n) (FP64).
 //
 // Paper: Section IV. Ryser's formula restricted to a subset S (Eq. ryser with
-// the sum over column subsets T of S), the row sums r_i(T) = sum_{j in T} A_ij
-// shared by every S containing T, and the products over S built one element at
-// a time (Pi[S] = Pi[S \ {i}] * r_i(T)), O(3^n) in total. With the sign that
-// makes Ryser's formula the permanent,
+// the sum over column subsets T of S), with the row sums r_i(T) = sum_{j in T}
+// A_ij shared by every S containing T and the products over S built one
+// element at a time, O(3^n) in total. With the sign that makes Ryser's formula
+// the permanent:
 //     perm(A[S]) = sum_{T subset of S} prod_{i in S} u_i(T),
-//     u_i(T) = r_i(T) for i in T, -r_i(T) for i not in T,
-// (the factor (-1)^{|S|-|T|} distributed over the |S \ T| rows outside T).
+//     u_i(T) = r_i(T) if i in T, -r_i(T) otherwise.
 //
-// Mapping: one CTA per matrix (persistent), 16 warps. Each warp takes chunks of
-// 64 consecutive column subsets T in Gray-code order (dynamic chunk counter),
-// so r_i(T) (lane i) changes by one +-A_ij per step. For one T the warp expands
-// all supersets S = T u R, R a subset of the free elements F = complement(T):
-// lane t fixes membership of the 5 highest free elements by its bits (a
-// product of at most 5 factors), then walks the subsets of the remaining free
-// elements with one multiplication per subset (a fully unrolled binary
-// recursion over up to 6 elements, an outer loop above that). Every product is
-// added into perm[S] with a shared-memory atomic (the S of one T are distinct,
-// different warps' T overlap); above n = 14 the accumulator is the output row in
-// global memory.
+// Split every subset into a low part (elements 0..l-1, l = min(n,7)) and a high
+// part (the other h = n-l elements): S = S_H u S_L, T = T_H u T_L. Then
+//     perm[S_H u S_L] = sum_{T_H subset of S_H} sum_{T_L subset of S_L}
+//                       alpha_{T_H,S_H}(T_L) * B_{T_H}(T_L, S_L),
+//     alpha = prod_{i in S_H} u_i(T),   B = prod_{i in S_L} u_i(T),   T = T_H u T_L.
+// For each T_H (outer loop, CTA-wide): the table U[T_L][i] = u_i(T_H u T_L) (one
+// add per entry from precomputed row sums), then the 3^l entries of B, level by
+// level over |S_L \ T_L|, one multiply each (B(T_L, S_L) = B(T_L, S_L \ {e})
+// * u_e). For each S_H containing T_H (one warp per S_H): alpha for all T_L
+// (|S_H| multiplies each), then for every S_L the sum over its submasks T_L, one
+// FMA per (T, S) pair, with the 3^l terms cut into pieces of at most 24 and
+// spread over the lanes by a precomputed longest-first assignment; the pieces of
+// one S_L are added in a fixed order and the owning warp updates perm[S] in the
+// output row (no two warps touch one S within a T_H step, and steps are
+// separated by CTA barriers, so no atomics and a deterministic result).
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <mutex>
+#include <vector>
 
 #include "apm_internal.cuh"
 
 namespace apm {
 
-constexpr int kPpmWarps = 16;
-constexpr int kPpmChunk = 64;
-constexpr int kPpmSmemMaxN = 14;
+constexpr int kPpmWarps = 8;
+constexpr int kPpmMaxL = 7;
+constexpr int kPpmPiece = 24;
+constexpr int kPpmMaxPieces = 200;
+constexpr int kPpmBp = 2187;  // 3^7
 
-template <int K, int G>
-struct PpmExpand {
-    static __device__ __forceinline__ void run(double *perm, double val, int S, const double (&ul)[6],
-                                               const int (&el)[6]) {
-        const double v2 = val * ul[K];
-        atomicAdd(perm + (S | el[K]), v2);
-        PpmExpand<K + 1, G>::run(perm, v2, S | el[K], ul, el);
-        PpmExpand<K + 1, G>::run(perm, val, S, ul, el);
-    }
-};
-template <int G>
-struct PpmExpand<G, G> {
-    static __device__ __forceinline__ void run(double *, double, int, const double (&)[6], const int (&)[6]) {}
+// Schedules for l = 1..7, packed into one int array on the device.
+struct PpmSched {
+    int off;        // [2^l] packed offset of S_L in the B table
+    int lvl;        // [l+2] start of each level in the entry list
+    int ent;        // [3^l][2] entries: (dst | src << 16), (e | T << 8); src 0xffff at level 0
+    int piece;      // [npieces] S | k0 << 8 | cnt << 16, lane-major
+    int lane;       // [33] first piece of each lane
+    int comb;       // [2^l + 1] CSR offsets of the pieces of each S_L
+    int combidx;    // [npieces] piece ids per S_L
+    int npieces;
 };
 
-__device__ __forceinline__ void ppm_expand(int G, double *perm, double val, int S, const double (&ul)[6],
-                                           const int (&el)[6]) {
-    switch (G) {
-        case 1: PpmExpand<0, 1>::run(perm, val, S, ul, el); break;
-        case 2: PpmExpand<0, 2>::run(perm, val, S, ul, el); break;
-        case 3: PpmExpand<0, 3>::run(perm, val, S, ul, el); break;
-        case 4: PpmExpand<0, 4>::run(perm, val, S, ul, el); break;
-        case 5: PpmExpand<0, 5>::run(perm, val, S, ul, el); break;
-        case 6: PpmExpand<0, 6>::run(perm, val, S, ul, el); break;
-        default: break;
-    }
+__device__ __align__(16) int g_ppm_sched[40000];
+static PpmSched h_sched[kPpmMaxL + 1];
+
+static int popc(unsigned x) { return __builtin_popcount(x); }
+
+static int pext_host(unsigned T, unsigned S) {
+    int r = 0, k = 0;
+    for (int b = 0; b < 32; ++b)
+        if ((S >> b) & 1u) {
+            if ((T >> b) & 1u) r |= 1 << k;
+            ++k;
+        }
+    return r;
 }
 
-// Contribution of one nonempty column subset T to every superset S.
-__device__ __forceinline__ void ppm_one_T(double *perm, int n, int T, double r, int lane) {
-    const bool inT = lane < n && ((T >> lane) & 1);
-    const double u = lane < n ? (inT ? r : -r) : 1.0;
-    // pre = prod_{i in T} u_i (lanes 0..15 hold the n <= 16 rows)
-    double v = inT ? u : 1.0;
-    v *= __shfl_xor_sync(0xffffffffu, v, 1);
-    v *= __shfl_xor_sync(0xffffffffu, v, 2);
-    v *= __shfl_xor_sync(0xffffffffu, v, 4);
-    v *= __shfl_xor_sync(0xffffffffu, v, 8);
-    const double pre = __shfl_sync(0xffffffffu, v, 0);
-    int F = (~T) & ((1 << n) - 1);
-    const int f = __popc(F);
-    const int k = f < 5 ? f : 5;
-    double val = pre;
-    int Sb = T;
-    for (int m = 0; m < k; ++m) {
-        const int e = 31 - __clz(F);
-        F ^= 1 << e;
-        const double ue = __shfl_sync(0xffffffffu, u, e);
-        if ((lane >> m) & 1) {
-            val *= ue;
-            Sb |= 1 << e;
+static void build_schedules(std::vector<int> &buf) {
+    buf.clear();
+    for (int l = 1; l <= kPpmMaxL; ++l) {
+        PpmSched &s = h_sched[l];
+        const int NL = 1 << l;
+        std::vector<int> off(NL);
+        int o = 0;
+        for (int S = 0; S < NL; ++S) {
+            off[S] = o;
+            o += 1 << popc(S);
         }
-    }
-    const bool active = lane < (1 << k);
-    // remaining free elements F: the lowest G = min(|F|, 6) go to the unrolled
-    // expansion, the rest (mid) to an outer loop
-    const int g = __popc(F);
-    const int G = g < 6 ? g : 6;
-    double ul[6];
-    int el[6];
-    int Fl = F;
-#pragma unroll
-    for (int q = 0; q < 6; ++q) {
-        int e = 0;
-        if (q < G) {
-            e = __ffs(Fl) - 1;
-            Fl ^= 1 << e;
-        }
-        ul[q] = __shfl_sync(0xffffffffu, u, e);
-        el[q] = 1 << e;
-    }
-    const int mid = Fl;  // elements above the lowest G
-    const int nmid = __popc(mid);
-    for (int t = 0; t < (1 << nmid); ++t) {
-        double vm = val;
-        int Sm = Sb;
-        int mm = mid;
-        for (int q = 0; q < nmid; ++q) {
-            const int e = __ffs(mm) - 1;
-            mm ^= 1 << e;
-            const double ue = __shfl_sync(0xffffffffu, u, e);
-            if ((t >> q) & 1) {
-                vm *= ue;
-                Sm |= 1 << e;
-            }
-        }
-        if (active) {
-            atomicAdd(perm + Sm, vm);
-            ppm_expand(G, perm, vm, Sm, ul, el);
-        }
-    }
-}
-
-__global__ void __launch_bounds__(kPpmWarps * 32) ppm_kernel(const double *__restrict__ A, int n,
-                                                             int64_t batch, double *perms,
-                                                             int smem_arrays) {
-    extern __shared__ __align__(16) double ppm_smem[];
-    __shared__ int chunk_ctr;
-    const int tid = threadIdx.x, lane = tid & 31;
-    const int N = 1 << n;
-    const int nn_pad = (n * n + 1) & ~1;
-    double *sA = ppm_smem;
-    for (int64_t b = blockIdx.x; b < batch; b += gridDim.x) {
-        double *perm = smem_arrays ? ppm_smem + nn_pad : perms + b * N;
-        for (int t = tid; t < n * n; t += blockDim.x) sA[t] = __ldg(A + b * n * n + t);
-        for (int t = tid; t < N; t += blockDim.x) perm[t] = t == 0 ? 1.0 : 0.0;
-        if (tid == 0) chunk_ctr = 0;
-        __syncthreads();
-        const int nchunks = (N + kPpmChunk - 1) / kPpmChunk;
-        while (true) {
-            int k = 0;
-            if (lane == 0) k = atomicAdd(&chunk_ctr, 1);
-            k = __shfl_sync(0xffffffffu, k, 0);
-            if (k >= nchunks) break;
-            const int g0 = k * kPpmChunk;
-            const int g1 = g0 + kPpmChunk < N ? g0 + kPpmChunk : N;
-            int T = g0 ^ (g0 >> 1);
-            double r = 0.0;
-            if (lane < n)
-                for (int j = 0; j < n; ++j)
-                    if ((T >> j) & 1) r += sA[lane * n + j];
-            for (int gi = g0; gi < g1; ++gi) {
-                if (gi > g0) {
-                    const int j = __ffs(gi) - 1;
-                    T ^= 1 << j;
-                    if (lane < n) r += ((T >> j) & 1) ? sA[lane * n + j] : -sA[lane * n + j];
+        s.off = static_cast<int>(buf.size());
+        buf.insert(buf.end(), off.begin(), off.end());
+        // entries by level d = |S \ T|
+        std::vector<int> lvl(l + 2, 0), ent;
+        for (int d = 0; d <= l; ++d) {
+            lvl[d] = static_cast<int>(ent.size() / 2);
+            for (int S = 0; S < NL; ++S)
+                for (int T = S;; T = (T - 1) & S) {
+                    if (popc(S ^ T) == d) {
+                        const int dst = off[S] + pext_host(T, S);
+                        int src = 0xffff, e = 0;
+                        if (d > 0) {
+                            e = 31 - __builtin_clz(static_cast<unsigned>(S ^ T));
+                            const int Sp = S ^ (1 << e);
+                            src = off[Sp] + pext_host(T, Sp);
+                        }
+                        ent.push_back(dst | (src << 16));
+                        ent.push_back(e | (T << 8));
+                    }
+                    if (T == 0) break;
                 }
-                if (T != 0) ppm_one_T(perm, n, T, r, lane);
+        }
+        lvl[l + 1] = static_cast<int>(ent.size() / 2);
+        s.lvl = static_cast<int>(buf.size());
+        buf.insert(buf.end(), lvl.begin(), lvl.end());
+        if (buf.size() & 1) buf.push_back(0);  // the entries are read as int2 (8-byte aligned)
+        s.ent = static_cast<int>(buf.size());
+        buf.insert(buf.end(), ent.begin(), ent.end());
+        // pieces, longest first onto the least loaded lane
+        struct P { int S, k0, cnt; };
+        std::vector<P> pieces;
+        for (int S = 0; S < NL; ++S) {
+            const int terms = 1 << popc(S);
+            for (int k0 = 0; k0 < terms; k0 += kPpmPiece)
+                pieces.push_back({S, k0, terms - k0 < kPpmPiece ? terms - k0 : kPpmPiece});
+        }
+        std::vector<int> order(pieces.size());
+        for (size_t i = 0; i < order.size(); ++i) order[i] = static_cast<int>(i);
+        for (size_t i = 1; i < order.size(); ++i)  // stable insertion sort by decreasing count
+            for (size_t j = i; j > 0 && pieces[order[j]].cnt > pieces[order[j - 1]].cnt; --j)
+                std::swap(order[j], order[j - 1]);
+        std::vector<std::vector<int>> per_lane(32);
+        int load[32] = {};
+        for (int id : order) {
+            int best = 0;
+            for (int ln = 1; ln < 32; ++ln)
+                if (load[ln] < load[best]) best = ln;
+            per_lane[best].push_back(id);
+            load[best] += pieces[id].cnt;
+        }
+        std::vector<int> piece_words, lane_off(33), piece_pos(pieces.size());
+        for (int ln = 0; ln < 32; ++ln) {
+            lane_off[ln] = static_cast<int>(piece_words.size());
+            for (int id : per_lane[ln]) {
+                piece_pos[id] = static_cast<int>(piece_words.size());
+                piece_words.push_back(pieces[id].S | (pieces[id].k0 << 8) | (pieces[id].cnt << 16));
             }
         }
-        __syncthreads();
-        if (smem_arrays) {
-            double *out = perms + b * N;
-            for (int t = tid; t < N; t += blockDim.x) out[t] = perm[t];
+        lane_off[32] = static_cast<int>(piece_words.size());
+        std::vector<int> comb(NL + 1, 0), combidx;
+        for (int S = 0; S < NL; ++S) {
+            comb[S] = static_cast<int>(combidx.size());
+            for (size_t id = 0; id < pieces.size(); ++id)
+                if (pieces[id].S == S) combidx.push_back(piece_pos[id]);
         }
-        __syncthreads();
+        comb[NL] = static_cast<int>(combidx.size());
+        s.piece = static_cast<int>(buf.size());
+        buf.insert(buf.end(), piece_words.begin(), piece_words.end());
+        s.lane = static_cast<int>(buf.size());
+        buf.insert(buf.end(), lane_off.begin(), lane_off.end());
+        s.comb = static_cast<int>(buf.size());
+        buf.insert(buf.end(), comb.begin(), comb.end());
+        s.combidx = static_cast<int>(buf.size());
+        buf.insert(buf.end(), combidx.begin(), combidx.end());
+        s.npieces = static_cast<int>(pieces.size());
     }
+}
+
+static bool schedules_fit() {
+    for (int l = 1; l <= kPpmMaxL; ++l)
+        if (h_sched[l].npieces > kPpmMaxPieces) return false;
+    return true;
+}
+
+__device__ __forceinline__ int pdep_dev(int k, int S) {
+    int r = 0;
+    for (int m = S; m; m &= m - 1) {
+        if (k & 1) r |= m & (-m);
+        k >>= 1;
+    }
+    return r;
+}
+
+struct PpmSmem {
+    double U[128 * 16];
+    double RL[128 * 16];
+    double Bp[kPpmBp];
+    double alpha[kPpmWarps][128];
+    double part[kPpmWarps][kPpmMaxPieces];
+    double A[256];
+    double RH[16];
+};
+
+__global__ void __launch_bounds__(kPpmWarps * 32) ppm_kernel(const double *__restrict__ Ag, int n, int64_t batch,
+                                                             double *perms, const PpmSched sc) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PpmSmem &sm = *reinterpret_cast<PpmSmem *>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, T = blockDim.x;
+    const int l = n < kPpmMaxL ? n : kPpmMaxL, h = n - l, NL = 1 << l;
+    const int N = 1 << n;
+    const int *off = g_ppm_sched + sc.off;
+    const int *lvl = g_ppm_sched + sc.lvl;
+    const int2 *ent = reinterpret_cast<const int2 *>(g_ppm_sched + sc.ent);
+    const int *pieces = g_ppm_sched + sc.piece;
+    const int *lane_off = g_ppm_sched + sc.lane;
+    const int *comb = g_ppm_sched + sc.comb;
+    const int *combidx = g_ppm_sched + sc.combidx;
+    for (int64_t b = blockIdx.x; b < batch; b += gridDim.x) {
+        double *perm = perms + b * N;
+        for (int t = tid; t < N; t += T) perm[t] = 0.0;
+        for (int t = tid; t < n * n; t += T) sm.A[t] = __ldg(Ag + b * n * n + t);
+        __syncthreads();
+        // low row sums r_i(T_L), T_L over elements 0..l-1
+        for (int t = tid; t < NL * n; t += T) {
+            const int TL = t / n, i = t - TL * n;
+            double s = 0.0;
+            for (int j = 0; j < l; ++j)
+                if ((TL >> j) & 1) s += sm.A[i * n + j];
+            sm.RL[TL * 16 + i] = s;
+        }
+        for (int TH = 0; TH < (1 << h); ++TH) {
+            if (tid < n) {
+                double s = 0.0;
+                for (int j = 0; j < h; ++j)
+                    if ((TH >> j) & 1) s += sm.A[tid * n + l + j];
+                sm.RH[tid] = s;
+            }
+            __syncthreads();  // RH ready; previous step's U/Bp readers done
+            for (int t = tid; t < NL * n; t += T) {
+                const int TL = t / n, i = t - TL * n;
+                const double rr = sm.RH[i] + sm.RL[TL * 16 + i];
+                const bool inT = i < l ? ((TL >> i) & 1) : ((TH >> (i - l)) & 1);
+                sm.U[TL * 16 + i] = inT ? rr : -rr;
+            }
+            __syncthreads();
+            // B(T_L, S_L) = prod_{i in S_L} u_i, level by level over |S_L \ T_L|
+            for (int d = 0; d <= l; ++d) {
+                for (int e = lvl[d] + tid; e < lvl[d + 1]; e += T) {
+                    const int2 w = ent[e];
+                    const int dst = w.x & 0xffff, src = (w.x >> 16) & 0xffff;
+                    const int el = w.y & 0xff, TL = w.y >> 8;
+                    double v;
+                    if (d == 0) {
+                        v = 1.0;
+                        for (int i = 0; i < l; ++i)
+                            if ((TL >> i) & 1) v *= sm.U[TL * 16 + i];
+                    } else {
+                        v = sm.Bp[src] * sm.U[TL * 16 + el];
+                    }
+                    sm.Bp[dst] = v;
+                }
+                __syncthreads();
+            }
+            // one warp per S_H containing T_H
+            const int freeH = ((1 << h) - 1) & ~TH;
+            const int items = 1 << __popc(freeH);
+            for (int it = warp; it < items; it += kPpmWarps) {
+                const int SH = TH | pdep_dev(it, freeH);
+                for (int TL = lane; TL < NL; TL += 32) {
+                    double a = 1.0;
+                    for (int i = 0; i < h; ++i)
+                        if ((SH >> i) & 1) a *= sm.U[TL * 16 + l + i];
+                    sm.alpha[warp][TL] = a;
+                }
+                __syncwarp();
+                for (int p = lane_off[lane]; p < lane_off[lane + 1]; ++p) {
+                    const int w = pieces[p];
+                    const int S = w & 0xff, k0 = (w >> 8) & 0xff, cnt = w >> 16;
+                    int TLs = pdep_dev(k0, S);
+                    const double *bp = sm.Bp + off[S] + k0;
+                    double acc = 0.0;
+                    for (int k = 0; k < cnt; ++k) {
+                        acc = fma(sm.alpha[warp][TLs], bp[k], acc);
+                        TLs = (TLs - S) & S;  // next submask in increasing order
+                    }
+                    sm.part[warp][p] = acc;
+                }
+                __syncwarp();
+                for (int S = lane; S < NL; S += 32) {
+                    double tot = 0.0;
+                    for (int q = comb[S]; q < comb[S + 1]; ++q) tot += sm.part[warp][combidx[q]];
+                    perm[(SH << l) | S] += tot;
+                }
+                __syncwarp();
+            }
+            __syncthreads();  // perm updates of this step visible before the next
+        }
+    }
+}
+
+static std::mutex g_sched_mu;
+static int g_sched_dev_mask = 0;
+static bool g_sched_built = false;
+static std::vector<int> g_sched_buf;
+
+static int ensure_ppm_schedules() {
+    std::lock_guard<std::mutex> lk(g_sched_mu);
+    if (!g_sched_built) {
+        build_schedules(g_sched_buf);
+        g_sched_built = true;
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 32 && ((g_sched_dev_mask >> dev) & 1)) return 0;
+    if (g_sched_buf.size() > 40000 || !schedules_fit()) return static_cast<int>(cudaErrorInvalidValue);
+    e = cudaMemcpyToSymbol(g_ppm_sched, g_sched_buf.data(), g_sched_buf.size() * sizeof(int));
+    if (e != cudaSuccess) return e;
+    if (dev < 32) g_sched_dev_mask |= 1 << dev;
+    return 0;
 }
 
 int launch_ppm(const double *A, int n, int64_t batch, double *perms, cudaStream_t s) {
+    int err = ensure_ppm_schedules();
+    if (err) return err;
     int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int smem_arrays = n <= kPpmSmemMaxN ? 1 : 0;
-    const size_t smem = sizeof(double) * (((n * n + 1) & ~1) + (smem_arrays ? (size_t(1) << n) : 0));
+    const size_t smem = sizeof(PpmSmem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(ppm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e == cudaSuccess)
@@ -184,7 +314,8 @@ int launch_ppm(const double *A, int n, int64_t batch, double *perms, cudaStream_
     if (per_sm < 1) return static_cast<int>(cudaErrorInvalidConfiguration);
     int64_t g = static_cast<int64_t>(sms) * per_sm;
     if (batch < g) g = batch;
-    ppm_kernel<<<static_cast<int>(g), kPpmWarps * 32, smem, s>>>(A, n, batch, perms, smem_arrays);
+    const int l = n < kPpmMaxL ? n : kPpmMaxL;
+    ppm_kernel<<<static_cast<int>(g), kPpmWarps * 32, smem, s>>>(A, n, batch, perms, h_sched[l]);
     return static_cast<int>(cudaGetLastError());
 }
 
