@@ -59,6 +59,23 @@ def bytes_per_set(n: int) -> int:
     return 8 * n * n + 16 * (1 << n)
 
 
+def max_over_ranks(seconds: float, world: int) -> float:
+    """Slowest rank's time (the whole job finishes when the last rank does).
+    Uses the already-initialised process group (gloo: host tensors only)."""
+    if world <= 1:
+        return seconds
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([seconds], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(per_rank_units: int, world: int, steps: int, seconds: float) -> float:
+    """Units processed by all ranks per second (weak scaling: each rank has its own batch)."""
+    return world * per_rank_units * steps / seconds
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -71,6 +88,9 @@ def parse():
     ap.add_argument("--no-rows", action="store_true",
                     help="skip the per-row measurements of the other hot-path steps")
     ap.add_argument("--mc-steps", type=int, default=100)
+    ap.add_argument("--case", default=None,
+                    choices=["cdet_n12", "cdet_n16", "keldysh_n12", "ppm_n14", "cdet_uneven"],
+                    help="run 3 launches of one kernel on a small case (for profiling) and exit")
     return ap.parse_args()
 
 
@@ -301,8 +321,43 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def profile_case(name: str):
+    """Three launches of one kernel on a small case whose inputs and outputs
+    exceed L2 (129 MB) while staying a few GB on the device."""
+    import numpy as np
+    import torch
+    from paper_2104_07638_gb300 import apm, inputs
+    dev = torch.device("cuda", 0)
+    if name == "cdet_n12":
+        A = torch.as_tensor(inputs.hubbard_batch(4096, 12, seed=2)).to(dev)
+        run = lambda: apm.cdet_connected(A, return_minors=True)
+    elif name == "cdet_n16":
+        A = torch.as_tensor(inputs.hubbard_batch(304, 16, seed=2)).to(dev)
+        run = lambda: apm.cdet_connected(A, return_minors=True)
+    elif name == "keldysh_n12":
+        M = torch.as_tensor(inputs.keldysh_batch(8192, 12, seed=3)).to(dev)
+        run = lambda: apm.keldysh_sum(M)
+    elif name == "ppm_n14":
+        P = torch.as_tensor(inputs.perm_batch(14, 1024, seed=4)).to(dev)
+        run = lambda: apm.perm_minors(P)
+    else:
+        orders = inputs.varlen_orders(16384, 4, 16, seed=3)
+        flat, off = inputs.hubbard_varlen(orders, seed=3)
+        A = torch.as_tensor(flat).to(dev)
+        a_off = torch.as_tensor(off).to(dev)
+        n_t = torch.as_tensor(orders).to(dev)
+        run = lambda: apm.cdet_connected_varlen(A, a_off, n_t)
+    for _ in range(3):
+        run()
+    torch.cuda.synchronize()
+    print(json.dumps({"case": name, "ok": True}))
+
+
 def main():
     args = parse()
+    if args.case:
+        profile_case(args.case)
+        return
     rank, world, local = dist_env()
     if world > 1:
         import torch.distributed as dist
@@ -361,13 +416,8 @@ def main():
         torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall0
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    dev_s = sum(step_ms) * 1e-3
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([dev_s], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dev_s = float(t.item())
-    value = world * B * args.steps / dev_s
+    dev_s = max_over_ranks(sum(step_ms) * 1e-3, world)
+    value = job_throughput(B, world, args.steps, dev_s)
     ms_per_step = 1000.0 * dev_s / args.steps
 
     # ---- end to end through the public API from pinned host memory ----
@@ -400,13 +450,8 @@ def main():
     for _ in range(e2e_steps):
         e2e_step()
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_s], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * B * e2e_steps / e2e_s
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    e2e_value = job_throughput(B, world, e2e_steps, e2e_s)
     # spot check of the end-to-end result against the device-timed one
     assert torch.equal(c_host[:4].to(dev), c[:4]) if rank == 0 else True
 
