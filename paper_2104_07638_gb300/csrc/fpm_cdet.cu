@@ -245,8 +245,15 @@ __device__ __forceinline__ void fpm_tree(const double *__restrict__ Ag, int n, d
     __syncthreads();
     for (int l = 0; l < L; ++l) {
         const int s = n - l, s1 = s - 1, ss = s * s, ss1 = s1 * s1, P = 1 << l;
-        const double *Wl = APM_BUF(l);
+        double *Wl = APM_BUF(l);
         double *Wn = APM_BUF(l + 1);
+        // pivot row of every node scaled by 1/p (Wl[0] holds 1/p); row 0 is not
+        // part of the left child, so it can be scaled in place
+        for (int t = tid; t < P * s1; t += T) {
+            const int m = t / s1, q = t - m * s1;
+            Wl[m * ss + q + 1] *= Wl[m * ss];
+        }
+        __syncthreads();
         const int E = 2 * P * ss1;
         const bool pivot_next = (l + 1) < L;
         for (int e = tid; e < E; e += T) {
@@ -256,10 +263,8 @@ __device__ __forceinline__ void fpm_tree(const double *__restrict__ Ag, int n, d
             const int q = rem - p * s1;
             const double *Wp = Wl + (x & (P - 1)) * ss;
             double v = Wp[(p + 1) * s + q + 1];
-            if (x >> l) {  // right child: Schur complement w.r.t. the pivot (Wp[0] holds 1/p)
-                const double t = Wp[(p + 1) * s] * Wp[0];
-                v = fma(-t, Wp[q + 1], v);
-            }
+            if (x >> l)  // right child: Schur complement w.r.t. the pivot
+                v = fma(-Wp[(p + 1) * s], Wp[q + 1], v);
             if (rem == 0 && pivot_next) node_pivot(x, l + 1, v, MA, thr, shift, h);
             Wn[x * ss1 + rem] = v;
         }
@@ -298,8 +303,9 @@ __device__ __forceinline__ void fpm_tree(const double *__restrict__ Ag, int n, d
 __device__ __forceinline__ void cdet_layers(const double *a, double *c, int n, unsigned long long gsel) {
     const int tid = threadIdx.x, T = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nw = T >> 5;
+    for (int t = tid; t < (1 << n); t += T) c[t] = 0.0;
+    __syncthreads();
     for (int x = tid; x < n; x += T) c[1 << x] = a[1 << x];
-    if (tid == 0) c[0] = 0.0;
     __syncthreads();
     for (int k = 2; k <= n; ++k) {
         const int cnt = c_binom[n][k];
@@ -321,19 +327,16 @@ __device__ __forceinline__ void cdet_layers(const double *a, double *c, int n, u
                 if ((gl >> i) & 1) UL |= bt;
             }
             const int H = Sp ^ low;
-            double acc0 = 0.0, acc1 = 0.0;
+            // c[S] itself (U = Sp) is still 0 here (c[] of this layer is zeroed
+            // before the layer), so the term U = Sp adds exactly 0 and needs no test
+            double acc = 0.0;
             int UH = H;
             while (true) {
-                int U = UL | UH;
-                if (U != Sp) acc0 = fma(c[j | U], a[Sp ^ U], acc0);
-                if (UH == 0) break;
-                UH = (UH - 1) & H;
-                U = UL | UH;
-                acc1 = fma(c[j | U], a[Sp ^ U], acc1);
+                const int U = UL | UH;
+                acc = fma(c[j | U], a[Sp ^ U], acc);
                 if (UH == 0) break;
                 UH = (UH - 1) & H;
             }
-            double acc = acc0 + acc1;
             for (int o = (1 << r) >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
             if (act && gl == 0) c[S] = a[S] - acc;
         }
@@ -403,7 +406,7 @@ __device__ __forceinline__ void cdet_item(const CdetArgs &p, int n, const double
 }
 
 template <bool kSmemArrays>
-__global__ void __launch_bounds__(kCdetThreads) fpm_cdet_kernel(const CdetKernelParams P) {
+__global__ void __launch_bounds__(kCdetThreads, 3) fpm_cdet_kernel(const CdetKernelParams P) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     CdetSmemHdr &h = *reinterpret_cast<CdetSmemHdr *>(smem_raw);
     const CdetArgs &p = P.a;
@@ -431,7 +434,7 @@ __global__ void __launch_bounds__(kCdetThreads) fpm_cdet_kernel(const CdetKernel
 
 // Uneven batch: items taken longest-first from `order` through a global
 // counter; arrays on chip for n <= smem_max_n, else in the CTA's scratch slot.
-__global__ void __launch_bounds__(kCdetThreads) fpm_cdet_varlen_kernel(const VarlenParams V) {
+__global__ void __launch_bounds__(kCdetThreads, 3) fpm_cdet_varlen_kernel(const VarlenParams V) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     CdetSmemHdr &h = *reinterpret_cast<CdetSmemHdr *>(smem_raw);
     __shared__ unsigned long long gsel_s[17];
