@@ -42,6 +42,8 @@
 
 namespace apm {
 
+constexpr int kBlkB = 10;  // low elements per block of the blocked recursion (orders above 12)
+
 __device__ uint16_t g_popmasks[1 << 16];  // masks < 2^16 ordered by (popcount, value)
 __device__ int g_popoff[18];              // first index of each popcount class
 __constant__ int c_binom[17][17];
@@ -65,7 +67,8 @@ __host__ __device__ inline size_t slot_doubles(int n) {
 
 struct CdetKernelParams {
     CdetArgs a;
-    unsigned long long gsel;  // 3 bits per popcount layer k: log2 of the lane-group size
+    unsigned long long gsel;    // 3 bits per popcount layer k: log2 of the lane-group size
+    unsigned long long gsel_b;  // the same for blocks of kBlkB elements (orders above 12)
 };
 
 struct VarlenParams {
@@ -299,13 +302,15 @@ __device__ __forceinline__ void fpm_tree(const double *__restrict__ Ag, int n, d
     if (nc > 0 && tid == 0) h.flags |= APM_ST_PIVOT_CORRECTED;
 }
 
-// Connected sums from a[] (MA) into c[] (MC).
-__device__ __forceinline__ void cdet_layers(const double *a, double *c, int n, unsigned long long gsel) {
+// Connected sums c[S] = init[S] - sum_{U proper subset of S'} c[{j} u U] a[S' \ U]
+// (init = a for the plain recursion) for all masks of n elements.
+__device__ __forceinline__ void cdet_layers(const double *init, const double *a, double *c, int n,
+                                            unsigned long long gsel) {
     const int tid = threadIdx.x, T = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nw = T >> 5;
     for (int t = tid; t < (1 << n); t += T) c[t] = 0.0;
     __syncthreads();
-    for (int x = tid; x < n; x += T) c[1 << x] = a[1 << x];
+    for (int x = tid; x < n; x += T) c[1 << x] = init[1 << x];
     __syncthreads();
     for (int k = 2; k <= n; ++k) {
         const int cnt = c_binom[n][k];
@@ -338,8 +343,92 @@ __device__ __forceinline__ void cdet_layers(const double *a, double *c, int n, u
                 UH = (UH - 1) & H;
             }
             for (int o = (1 << r) >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (act && gl == 0) c[S] = a[S] - acc;
+            if (act && gl == 0) c[S] = init[S] - acc;
         }
+        __syncthreads();
+    }
+}
+
+// acc[S] += sum over all U subset of S' of cb[{j} u U] ab[S' \ U] for every
+// nonempty mask S of b elements (j = lowest element of S, S' = S \ {j}): the
+// contribution of one off-diagonal block pair of the blocked recursion. All
+// masks are independent; lane groups as in cdet_layers.
+__device__ __forceinline__ void block_conv(const double *cb, const double *ab, double *acc, int b,
+                                           unsigned long long gsel) {
+    const int tid = threadIdx.x, T = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nw = T >> 5;
+    for (int k = 1; k <= b; ++k) {
+        const int cnt = c_binom[b][k];
+        const uint16_t *masks = g_popmasks + g_popoff[k];
+        const int r = static_cast<int>((gsel >> (3 * k)) & 7ull);
+        const int spw = 32 >> r;
+        const int gl = lane & ((1 << r) - 1);
+        for (int base = warp * spw; base < cnt; base += nw * spw) {
+            const int G = base + (lane >> r);
+            const bool act = G < cnt;
+            const int S = masks[act ? G : cnt - 1];
+            const int j = S & (-S);
+            const int Sp = S ^ j;
+            int UL = 0, low = 0, tmp = Sp;
+            for (int i = 0; i < r; ++i) {
+                const int bt = tmp & (-tmp);
+                tmp ^= bt;
+                low |= bt;
+                if ((gl >> i) & 1) UL |= bt;
+            }
+            const int H = Sp ^ low;
+            double sum = 0.0;
+            int UH = H;
+            while (true) {
+                const int U = UL | UH;
+                sum = fma(cb[j | U], ab[Sp ^ U], sum);
+                if (UH == 0) break;
+                UH = (UH - 1) & H;
+            }
+            for (int o = (1 << r) >> 1; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+            if (act && gl == 0) acc[S] += sum;
+        }
+    }
+}
+
+// Connected sums for n > kBlkB, blocked over the lowest kBlkB elements:
+// S = S_H u S_L. For each S_H (increasing), every proper T_H of S_H contributes
+// the block convolution of c[T_H u .] with a[(S_H \ T_H) u .] (with j in the
+// low part, T_L = S_L allowed), the S_L = {} entry only when the lowest element
+// of S_H lies in T_H; then the diagonal block solves its own recursion with
+// init a[S_H u S_L] - acc[S_L] and the pure-low block a[0 u .]. a (global) and
+// c (global output row) are read block-wise into shared memory (blk: 6 x 2^kBlkB).
+__device__ void cdet_blocked(const double *a, double *c, int n, double *blk, unsigned long long gsel_b) {
+    const int tid = threadIdx.x, T = blockDim.x;
+    const int b = kBlkB, NB = 1 << kBlkB, h = n - b;
+    double *cb = blk, *ab = blk + NB, *acc = blk + 2 * NB, *cs = blk + 3 * NB, *as = blk + 4 * NB,
+           *a0 = blk + 5 * NB;
+    for (int t = tid; t < NB; t += T) a0[t] = a[t];
+    for (int SH = 0; SH < (1 << h); ++SH) {
+        for (int t = tid; t < NB; t += T) {
+            acc[t] = 0.0;
+            as[t] = a[(static_cast<size_t>(SH) << b) + t];
+        }
+        const int jH = SH & (-SH);
+        __syncthreads();
+        if (SH) {
+            for (int TH = (SH - 1) & SH;; TH = (TH - 1) & SH) {
+                for (int t = tid; t < NB; t += T) {
+                    cb[t] = c[(static_cast<size_t>(TH) << b) + t];
+                    ab[t] = a[(static_cast<size_t>(SH ^ TH) << b) + t];
+                }
+                __syncthreads();
+                block_conv(cb, ab, acc, b, gsel_b);
+                if (tid == 0 && (TH & jH)) acc[0] = fma(cb[0], ab[0], acc[0]);
+                __syncthreads();
+                if (TH == 0) break;
+            }
+        }
+        for (int t = tid; t < NB; t += T) as[t] -= acc[t];
+        __syncthreads();
+        cdet_layers(as, a0, cs, b, gsel_b);
+        for (int t = tid; t < NB; t += T)
+            c[(static_cast<size_t>(SH) << b) + t] = (t == 0) ? (SH ? as[0] : 0.0) : cs[t];
         __syncthreads();
     }
 }
@@ -349,7 +438,8 @@ __device__ __forceinline__ void cdet_layers(const double *a, double *c, int n, u
 __device__ __forceinline__ void cdet_item(const CdetArgs &p, int n, const double *Au, const double *Ad,
                                           const double *ain, double *mo, double *co, uint32_t *st,
                                           double *MA, double *MC, double *MU, bool in_smem,
-                                          unsigned long long gsel, CdetSmemHdr &h) {
+                                          unsigned long long gsel, unsigned long long gsel_b, double *blk,
+                                          CdetSmemHdr &h) {
     const int tid = threadIdx.x;
     const int N = 1 << n;
     if (tid == 0) bulk_wait_read();  // the previous item's bulk stores have read their source
@@ -396,11 +486,11 @@ __device__ __forceinline__ void cdet_item(const CdetArgs &p, int n, const double
         }
         __syncthreads();
     }
-    cdet_layers(MA, MC, n, gsel);
     if (in_smem) {
+        cdet_layers(MA, MA, MC, n, gsel);
         if (tid == 0) bulk_store(co, MC, N * 8u);
     } else {
-        for (int t = tid; t < N; t += blockDim.x) co[t] = MC[t];
+        cdet_blocked(MA, co, n, blk, gsel_b);
     }
     // the next item's first barrier orders these reads before any overwrite
 }
@@ -413,9 +503,10 @@ __global__ void __launch_bounds__(kCdetThreads, 3) fpm_cdet_kernel(const CdetKer
     const int n = p.n;
     const int N = 1 << n;
     const int NC = N > 16 ? N : 16;
+    double *const sbase = reinterpret_cast<double *>(smem_raw + ((sizeof(CdetSmemHdr) + 127) & ~size_t(127)));
     double *base;
     if (kSmemArrays)
-        base = reinterpret_cast<double *>(smem_raw + ((sizeof(CdetSmemHdr) + 127) & ~size_t(127)));
+        base = sbase;
     else
         base = p.gscratch + static_cast<size_t>(blockIdx.x) * slot_doubles(n);
     double *MA = base;
@@ -427,7 +518,7 @@ __global__ void __launch_bounds__(kCdetThreads, 3) fpm_cdet_kernel(const CdetKer
                   p.a_in ? p.a_in + b * N : nullptr,
                   p.minors_out ? p.minors_out + b * (p.two_mats ? 2 * N : N) : nullptr,
                   p.c_out ? p.c_out + b * N : nullptr, p.status ? p.status + b : nullptr, MA, MC, MU,
-                  kSmemArrays, P.gsel, h);
+                  kSmemArrays, P.gsel, P.gsel_b, sbase, h);
     }
     if (threadIdx.x == 0) bulk_wait_all();
 }
@@ -466,7 +557,7 @@ __global__ void __launch_bounds__(kCdetThreads, 3) fpm_cdet_varlen_kernel(const 
                   p.a_in ? p.a_in + co : nullptr,
                   p.minors_out ? p.minors_out + (p.two_mats ? 2 * co : co) : nullptr,
                   p.c_out ? p.c_out + co : nullptr, p.status ? p.status + b : nullptr, MA, MC, MU, in_smem,
-                  gsel_s[n], h);
+                  gsel_s[n], gsel_s[kBlkB], sbase, h);
     }
     if (threadIdx.x == 0) bulk_wait_all();
 }
@@ -511,16 +602,14 @@ static inline size_t hdr_bytes() { return (sizeof(CdetSmemHdr) + 127) & ~size_t(
 size_t cdet_slot_doubles(int n) { return slot_doubles(n); }
 
 size_t cdet_smem_bytes(int n, bool two_mats, bool smem_arrays) {
-    if (!smem_arrays) return hdr_bytes();
+    if (!smem_arrays) return hdr_bytes() + 6 * sizeof(double) * (size_t(1) << kBlkB);
     const size_t N = size_t(1) << n;
     return hdr_bytes() + 8 * ((two_mats ? 2 : 1) * N + (N > 16 ? N : 16));
 }
 
 int cdet_smem_max_n(bool two_mats) {
-    int best = 0;
-    for (int n = 1; n <= 16; ++n)
-        if (cdet_smem_bytes(n, two_mats, true) <= 227 * 1024) best = n;
-    return best;
+    (void)two_mats;
+    return 12;  // above: a[] and c[] in global memory, recursion blocked through shared memory
 }
 
 void cdet_group_table(int n, int threads, uint8_t *gsel) {
@@ -582,9 +671,11 @@ int cdet_grid(int n, int64_t batch, bool two_mats, bool smem_arrays, int *err) {
                 e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fpm_cdet_kernel<true>,
                                                                   kCdetThreads, smem);
         } else {
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fpm_cdet_kernel<false>,
-                                                              kCdetThreads, smem);
-            if (per_sm > 2) per_sm = 2;  // bounds the scratch and keeps it L2-resident
+            e = cudaFuncSetAttribute(fpm_cdet_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     static_cast<int>(smem));
+            if (e == cudaSuccess)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fpm_cdet_kernel<false>,
+                                                                  kCdetThreads, smem);
         }
     }
     if (e != cudaSuccess || per_sm < 1) {
@@ -631,6 +722,7 @@ int launch_fpm_cdet(const CdetArgs &a, cudaStream_t s) {
     CdetKernelParams P;
     P.a = a;
     P.gsel = cdet_gsel_packed(a.n);
+    P.gsel_b = cdet_gsel_packed(kBlkB);
     const bool smem_arrays = a.n <= cdet_smem_max_n(a.two_mats != 0);
     const int grid = cdet_grid(a.n, a.batch, a.two_mats != 0, smem_arrays, &err);
     if (err) return err;
