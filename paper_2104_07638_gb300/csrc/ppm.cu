@@ -37,21 +37,21 @@ constexpr int kPpmWarps = 8;
 constexpr int kPpmMaxL = 7;
 constexpr int kPpmPiece = 24;
 constexpr int kPpmMaxPieces = 200;
-constexpr int kPpmBp = 2187;  // 3^7
+constexpr int kPpmBpSlots = 2560;  // lane-interleaved B table: 32 x (longest lane <= 80)
 
 // Schedules for l = 1..7, packed into one int array on the device.
 struct PpmSched {
-    int off;        // [2^l] packed offset of S_L in the B table
     int lvl;        // [l+2] start of each level in the entry list
     int ent;        // [3^l][2] entries: (dst | src << 16), (e | T << 8); src 0xffff at level 0
-    int piece;      // [npieces] S | k0 << 8 | cnt << 16, lane-major
-    int lane;       // [33] first piece of each lane
+    int term;       // [maxlen][32] per lane term q: T_L | 0x80 if q starts a piece | S_L << 8; -1 past the end
+    int lane;       // [33] first piece of each lane (pieces numbered lane by lane)
     int comb;       // [2^l + 1] CSR offsets of the pieces of each S_L
     int combidx;    // [npieces] piece ids per S_L
     int npieces;
+    int maxlen;     // terms of the longest lane
 };
 
-__device__ __align__(16) int g_ppm_sched[40000];
+__device__ __align__(16) int g_ppm_sched[60000];
 static PpmSched h_sched[kPpmMaxL + 1];
 
 static int popc(unsigned x) { return __builtin_popcount(x); }
@@ -71,41 +71,8 @@ static void build_schedules(std::vector<int> &buf) {
     for (int l = 1; l <= kPpmMaxL; ++l) {
         PpmSched &s = h_sched[l];
         const int NL = 1 << l;
-        std::vector<int> off(NL);
-        int o = 0;
-        for (int S = 0; S < NL; ++S) {
-            off[S] = o;
-            o += 1 << popc(S);
-        }
-        s.off = static_cast<int>(buf.size());
-        buf.insert(buf.end(), off.begin(), off.end());
-        // entries by level d = |S \ T|
-        std::vector<int> lvl(l + 2, 0), ent;
-        for (int d = 0; d <= l; ++d) {
-            lvl[d] = static_cast<int>(ent.size() / 2);
-            for (int S = 0; S < NL; ++S)
-                for (int T = S;; T = (T - 1) & S) {
-                    if (popc(S ^ T) == d) {
-                        const int dst = off[S] + pext_host(T, S);
-                        int src = 0xffff, e = 0;
-                        if (d > 0) {
-                            e = 31 - __builtin_clz(static_cast<unsigned>(S ^ T));
-                            const int Sp = S ^ (1 << e);
-                            src = off[Sp] + pext_host(T, Sp);
-                        }
-                        ent.push_back(dst | (src << 16));
-                        ent.push_back(e | (T << 8));
-                    }
-                    if (T == 0) break;
-                }
-        }
-        lvl[l + 1] = static_cast<int>(ent.size() / 2);
-        s.lvl = static_cast<int>(buf.size());
-        buf.insert(buf.end(), lvl.begin(), lvl.end());
-        if (buf.size() & 1) buf.push_back(0);  // the entries are read as int2 (8-byte aligned)
-        s.ent = static_cast<int>(buf.size());
-        buf.insert(buf.end(), ent.begin(), ent.end());
-        // pieces, longest first onto the least loaded lane
+        // pieces of at most kPpmPiece consecutive submasks of one S_L, longest
+        // first onto the least loaded lane
         struct P { int S, k0, cnt; };
         std::vector<P> pieces;
         for (int S = 0; S < NL; ++S) {
@@ -127,24 +94,66 @@ static void build_schedules(std::vector<int> &buf) {
             per_lane[best].push_back(id);
             load[best] += pieces[id].cnt;
         }
-        std::vector<int> piece_words, lane_off(33), piece_pos(pieces.size());
+        int maxlen = 0;
+        for (int ln = 0; ln < 32; ++ln) maxlen = load[ln] > maxlen ? load[ln] : maxlen;
+        // B entry (S, rank k) lives at q*32 + lane, q = its position in the lane's term list
+        std::vector<int> pos_of(3279 * 0 + (1 << (2 * l)), -1);  // indexed S * 2^l + k
+        std::vector<int> term(static_cast<size_t>(maxlen) * 32, -1), lane_off(33), piece_id(pieces.size());
+        int pid = 0;
         for (int ln = 0; ln < 32; ++ln) {
-            lane_off[ln] = static_cast<int>(piece_words.size());
+            lane_off[ln] = pid;
+            int q = 0;
             for (int id : per_lane[ln]) {
-                piece_pos[id] = static_cast<int>(piece_words.size());
-                piece_words.push_back(pieces[id].S | (pieces[id].k0 << 8) | (pieces[id].cnt << 16));
+                piece_id[id] = pid++;
+                const P &pc = pieces[id];
+                for (int k = pc.k0; k < pc.k0 + pc.cnt; ++k, ++q) {
+                    // T_L = the k-th submask of S in increasing order
+                    int T = 0, kk = k;
+                    for (int m = pc.S; m; m &= m - 1) {
+                        if (kk & 1) T |= m & (-m);
+                        kk >>= 1;
+                    }
+                    term[static_cast<size_t>(q) * 32 + ln] = T | (k == pc.k0 ? 0x80 : 0) | (pc.S << 8);
+                    pos_of[pc.S * NL + k] = q * 32 + ln;
+                }
             }
         }
-        lane_off[32] = static_cast<int>(piece_words.size());
+        lane_off[32] = pid;
+        // B entries level by level over d = |S \ T|
+        std::vector<int> lvl(l + 2, 0), ent;
+        for (int d = 0; d <= l; ++d) {
+            lvl[d] = static_cast<int>(ent.size() / 2);
+            for (int S = 0; S < NL; ++S)
+                for (int T = S;; T = (T - 1) & S) {
+                    if (popc(S ^ T) == d) {
+                        const int dst = pos_of[S * NL + pext_host(T, S)];
+                        int src = 0xffff, e = 0;
+                        if (d > 0) {
+                            e = 31 - __builtin_clz(static_cast<unsigned>(S ^ T));
+                            const int Sp = S ^ (1 << e);
+                            src = pos_of[Sp * NL + pext_host(T, Sp)];
+                        }
+                        ent.push_back(dst | (src << 16));
+                        ent.push_back(e | (T << 8));
+                    }
+                    if (T == 0) break;
+                }
+        }
+        lvl[l + 1] = static_cast<int>(ent.size() / 2);
         std::vector<int> comb(NL + 1, 0), combidx;
         for (int S = 0; S < NL; ++S) {
             comb[S] = static_cast<int>(combidx.size());
             for (size_t id = 0; id < pieces.size(); ++id)
-                if (pieces[id].S == S) combidx.push_back(piece_pos[id]);
+                if (pieces[id].S == S) combidx.push_back(piece_id[id]);
         }
         comb[NL] = static_cast<int>(combidx.size());
-        s.piece = static_cast<int>(buf.size());
-        buf.insert(buf.end(), piece_words.begin(), piece_words.end());
+        s.lvl = static_cast<int>(buf.size());
+        buf.insert(buf.end(), lvl.begin(), lvl.end());
+        if (buf.size() & 1) buf.push_back(0);  // the entries are read as int2 (8-byte aligned)
+        s.ent = static_cast<int>(buf.size());
+        buf.insert(buf.end(), ent.begin(), ent.end());
+        s.term = static_cast<int>(buf.size());
+        buf.insert(buf.end(), term.begin(), term.end());
         s.lane = static_cast<int>(buf.size());
         buf.insert(buf.end(), lane_off.begin(), lane_off.end());
         s.comb = static_cast<int>(buf.size());
@@ -152,16 +161,17 @@ static void build_schedules(std::vector<int> &buf) {
         s.combidx = static_cast<int>(buf.size());
         buf.insert(buf.end(), combidx.begin(), combidx.end());
         s.npieces = static_cast<int>(pieces.size());
+        s.maxlen = maxlen;
     }
 }
 
 static bool schedules_fit() {
     for (int l = 1; l <= kPpmMaxL; ++l)
-        if (h_sched[l].npieces > kPpmMaxPieces) return false;
+        if (h_sched[l].npieces > kPpmMaxPieces || h_sched[l].maxlen * 32 > kPpmBpSlots) return false;
     return true;
 }
 
-__device__ __forceinline__ int pdep_dev(int k, int S) {
+__device__ __forceinline__ int pdep_dev(int k, int S) {  // k-th submask of S (increasing order)
     int r = 0;
     for (int m = S; m; m &= m - 1) {
         if (k & 1) r |= m & (-m);
@@ -171,9 +181,10 @@ __device__ __forceinline__ int pdep_dev(int k, int S) {
 }
 
 struct PpmSmem {
-    double U[128 * 16];
-    double RL[128 * 16];
-    double Bp[kPpmBp];
+    double U[16 * 128];   // [i][T_L]
+    double RL[16 * 128];  // [i][T_L]
+    double Bp[kPpmBpSlots];
+    double PT[128];       // prod_{i in T_H} u_i(T_H u T_L)
     double alpha[kPpmWarps][128];
     double part[kPpmWarps][kPpmMaxPieces];
     double A[256];
@@ -187,13 +198,13 @@ __global__ void __launch_bounds__(kPpmWarps * 32) ppm_kernel(const double *__res
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, T = blockDim.x;
     const int l = n < kPpmMaxL ? n : kPpmMaxL, h = n - l, NL = 1 << l;
     const int N = 1 << n;
-    const int *off = g_ppm_sched + sc.off;
     const int *lvl = g_ppm_sched + sc.lvl;
     const int2 *ent = reinterpret_cast<const int2 *>(g_ppm_sched + sc.ent);
-    const int *pieces = g_ppm_sched + sc.piece;
+    const int *term = g_ppm_sched + sc.term;
     const int *lane_off = g_ppm_sched + sc.lane;
     const int *comb = g_ppm_sched + sc.comb;
     const int *combidx = g_ppm_sched + sc.combidx;
+    const int maxlen = sc.maxlen;
     for (int64_t b = blockIdx.x; b < batch; b += gridDim.x) {
         double *perm = perms + b * N;
         for (int t = tid; t < N; t += T) perm[t] = 0.0;
@@ -201,11 +212,11 @@ __global__ void __launch_bounds__(kPpmWarps * 32) ppm_kernel(const double *__res
         __syncthreads();
         // low row sums r_i(T_L), T_L over elements 0..l-1
         for (int t = tid; t < NL * n; t += T) {
-            const int TL = t / n, i = t - TL * n;
+            const int i = t / NL, TL = t - i * NL;
             double s = 0.0;
             for (int j = 0; j < l; ++j)
                 if ((TL >> j) & 1) s += sm.A[i * n + j];
-            sm.RL[TL * 16 + i] = s;
+            sm.RL[i * 128 + TL] = s;
         }
         for (int TH = 0; TH < (1 << h); ++TH) {
             if (tid < n) {
@@ -216,12 +227,19 @@ __global__ void __launch_bounds__(kPpmWarps * 32) ppm_kernel(const double *__res
             }
             __syncthreads();  // RH ready; previous step's U/Bp readers done
             for (int t = tid; t < NL * n; t += T) {
-                const int TL = t / n, i = t - TL * n;
-                const double rr = sm.RH[i] + sm.RL[TL * 16 + i];
+                const int i = t / NL, TL = t - i * NL;
+                const double rr = sm.RH[i] + sm.RL[i * 128 + TL];
                 const bool inT = i < l ? ((TL >> i) & 1) : ((TH >> (i - l)) & 1);
-                sm.U[TL * 16 + i] = inT ? rr : -rr;
+                sm.U[i * 128 + TL] = inT ? rr : -rr;
             }
             __syncthreads();
+            // prefix product over the high column subset, shared by all its S_H
+            for (int TL = tid; TL < NL; TL += T) {
+                double v = 1.0;
+                for (int i = 0; i < h; ++i)
+                    if ((TH >> i) & 1) v *= sm.U[(l + i) * 128 + TL];
+                sm.PT[TL] = v;
+            }
             // B(T_L, S_L) = prod_{i in S_L} u_i, level by level over |S_L \ T_L|
             for (int d = 0; d <= l; ++d) {
                 for (int e = lvl[d] + tid; e < lvl[d + 1]; e += T) {
@@ -232,9 +250,9 @@ __global__ void __launch_bounds__(kPpmWarps * 32) ppm_kernel(const double *__res
                     if (d == 0) {
                         v = 1.0;
                         for (int i = 0; i < l; ++i)
-                            if ((TL >> i) & 1) v *= sm.U[TL * 16 + i];
+                            if ((TL >> i) & 1) v *= sm.U[i * 128 + TL];
                     } else {
-                        v = sm.Bp[src] * sm.U[TL * 16 + el];
+                        v = sm.Bp[src] * sm.U[el * 128 + TL];
                     }
                     sm.Bp[dst] = v;
                 }
@@ -244,26 +262,28 @@ __global__ void __launch_bounds__(kPpmWarps * 32) ppm_kernel(const double *__res
             const int freeH = ((1 << h) - 1) & ~TH;
             const int items = 1 << __popc(freeH);
             for (int it = warp; it < items; it += kPpmWarps) {
-                const int SH = TH | pdep_dev(it, freeH);
+                const int R = pdep_dev(it, freeH);
+                const int SH = TH | R;
                 for (int TL = lane; TL < NL; TL += 32) {
-                    double a = 1.0;
-                    for (int i = 0; i < h; ++i)
-                        if ((SH >> i) & 1) a *= sm.U[TL * 16 + l + i];
+                    double a = sm.PT[TL];
+                    for (int m = R; m; m &= m - 1)
+                        a *= sm.U[(l + __ffs(m) - 1) * 128 + TL];
                     sm.alpha[warp][TL] = a;
                 }
                 __syncwarp();
-                for (int p = lane_off[lane]; p < lane_off[lane + 1]; ++p) {
-                    const int w = pieces[p];
-                    const int S = w & 0xff, k0 = (w >> 8) & 0xff, cnt = w >> 16;
-                    int TLs = pdep_dev(k0, S);
-                    const double *bp = sm.Bp + off[S] + k0;
-                    double acc = 0.0;
-                    for (int k = 0; k < cnt; ++k) {
-                        acc = fma(sm.alpha[warp][TLs], bp[k], acc);
-                        TLs = (TLs - S) & S;  // next submask in increasing order
+                // this lane's terms, lane-interleaved: conflict-free B reads
+                int p = lane_off[lane];
+                double acc = 0.0;
+                for (int q = 0; q < maxlen; ++q) {
+                    const int w = term[q * 32 + lane];
+                    if (w < 0) break;
+                    if ((w & 0x80) && q > 0) {
+                        sm.part[warp][p++] = acc;
+                        acc = 0.0;
                     }
-                    sm.part[warp][p] = acc;
+                    acc = fma(sm.alpha[warp][w & 0x7f], sm.Bp[q * 32 + lane], acc);
                 }
+                if (lane_off[lane + 1] > lane_off[lane]) sm.part[warp][p] = acc;
                 __syncwarp();
                 for (int S = lane; S < NL; S += 32) {
                     double tot = 0.0;
@@ -292,7 +312,7 @@ static int ensure_ppm_schedules() {
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 32 && ((g_sched_dev_mask >> dev) & 1)) return 0;
-    if (g_sched_buf.size() > 40000 || !schedules_fit()) return static_cast<int>(cudaErrorInvalidValue);
+    if (g_sched_buf.size() > 60000 || !schedules_fit()) return static_cast<int>(cudaErrorInvalidValue);
     e = cudaMemcpyToSymbol(g_ppm_sched, g_sched_buf.data(), g_sched_buf.size() * sizeof(int));
     if (e != cudaSuccess) return e;
     if (dev < 32) g_sched_dev_mask |= 1 << dev;
