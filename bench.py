@@ -37,10 +37,10 @@ SM_MAX_MHZ = 2070.0
 FP64_FLOP_PER_CLK_SM = 4.0   # 1.25 TFLOP/s nominal FP64 / (152 SMs x 2.07 GHz), 2 DFMA/clk/SM
 METRIC = "minor-sets/sec at n=12 FP64 (% of roofline)"
 # DRAM bytes (read + write) per matrix of the fused kernel from one ncu capture
-# (profiles/fpm_cdet_n12_hubbard.md: 213.7 MB per 4096 matrices), valid only for
+# (profiles/fpm_cdet_n12_hubbard.md: 211.3 MB per 4096 matrices), valid only for
 # the kernel source it was taken on (sha256 prefix below).
-TRAFFIC_PER_SET = 213.7e6 / 4096
-TRAFFIC_SRC_SHA = "a7ca5ba3fddba388"
+TRAFFIC_PER_SET = 211.27e6 / 4096
+TRAFFIC_SRC_SHA = "726041c0b4d97c33"
 UNIT = "minor-sets/s"
 
 
