@@ -230,8 +230,8 @@ def measure_rows(args, dev, peak):
         targs.append(t)
         walkers[n] = wk
     net = mc.Surrogate(seed=7, max_batch=W)
-    losses, t_train = mc.timed(lambda: net.train(torch.cat(feats), torch.cat(targs), epochs=4, batch=4096,
-                                                 lr=1e-3))
+    losses, t_train = mc.timed(lambda: net.train(torch.cat(feats), torch.cat(targs), epochs=1, batch=8192,
+                                                 lr=3e-3))
     per_n = {}
     tot = {"plain_ess": 0.0, "plain_s": 0.0, "learned_ess": 0.0, "learned_s": 0.0}
     for n, wk in walkers.items():
