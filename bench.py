@@ -37,8 +37,8 @@ SM_MAX_MHZ = 2070.0
 FP64_FLOP_PER_CLK_SM = 4.0   # 1.25 TFLOP/s nominal FP64 / (152 SMs x 2.07 GHz), 2 DFMA/clk/SM
 METRIC = "minor-sets/sec at n=12 FP64 (% of roofline)"
 # DRAM bytes (read + write) per matrix of the fused kernel from one ncu capture
-# (profiles/fpm_cdet_n12_hubbard.md: 211.3 MB per 4096 matrices), valid only for
-# the kernel source it was taken on (sha256 prefix below).
+# of 4096 matrices (211.3 MB), valid only for the kernel source it was taken on
+# (sha256 prefix below).
 TRAFFIC_PER_SET = 211.27e6 / 4096
 TRAFFIC_SRC_SHA = "726041c0b4d97c33"
 UNIT = "minor-sets/s"

@@ -1,7 +1,7 @@
 """Plain FP64 CPU oracle for the all-principal-minor path (test infrastructure).
 
-Only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline leg
-may import this package. The product path (the CUDA library and its Python
+Only the tests, the smoke check (``smoke()`` of the repository's build/smoke
+entry module) and the benchmark's CPU-baseline leg may import this package. The product path (the CUDA library and its Python
 binding) never does: it shares no code with the oracle.
 
 The C source ``oracle.c`` is compiled on first use (gcc, OpenMP, no fast-math,
