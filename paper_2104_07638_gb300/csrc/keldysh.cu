@@ -15,12 +15,23 @@
 // with respect to p; det(child) = det(node) * p (times -1 for alpha = - when
 // the assignments are sign-weighted).
 //
-// Mapping: one warp per matrix. The upper vertices 0..D-1 (D = n - 6) are
-// walked depth first; each Schur step is spread over the 32 lanes and its
+// Mapping: one warp per matrix. The upper vertices 0..D-1 (D = n - S, S = 7)
+// are walked depth first; each Schur step is spread over the 32 lanes and its
 // result goes to a per-warp stack in caller scratch (global memory, L1/L2
-// resident). The last min(n,6) vertices are expanded breadth first in shared
-// memory (one child entry per lane step), and the 4x4 nodes of the last level
-// are finished with closed-form 2x2 determinants, one leaf per lane.
+// resident). Of the last min(n,S) vertices, all but three are expanded breadth
+// first in shared memory (one child entry per lane step); the 6x6 nodes that
+// remain are summed in closed form: the sum over the 8 assignments of the last
+// three vertices is a sum of 3x3 determinants, four lanes per node, two
+// determinants per lane, with no pivots. The running sums stay in per-lane
+// registers for the whole matrix and are reduced over the warp once at its end.
+//
+// Cost model: an FP64 warp instruction occupies the SM sub-partition's FP64
+// unit for the same time whatever the number of active lanes, so the design
+// counts warp instructions: the closed form replaces two tree levels (with
+// their reciprocals, issued on 16 and fewer lanes) and the leaf level, and a
+// tail of 7 rather than 6 vertices halves the depth-first steps per leaf and
+// doubles the nodes that share each breadth-first level's reciprocal step
+// (measured 0.87 against 0.68 TFLOP/s at n = 12).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -28,15 +39,46 @@
 
 namespace apm {
 
-constexpr int kKelWarps = 4;
-constexpr int kKelTail = 6;
-constexpr int kKelBufE = 256;  // levels 0, 2, 4 of a 6-vertex tail: 144, 256, 256 entries
-constexpr int kKelBufO = 288;  // levels 1, 3: 200, 288 entries
+// Tail size S (vertices expanded breadth first in shared memory) and warps per
+// CTA; S = 7 needs 20 KB of shared memory per warp, so its CTA holds the 11
+// warps that fit on one SM.
+#ifndef APM_KEL_TAIL
+#define APM_KEL_TAIL 7
+#endif
+constexpr int kKelTail = APM_KEL_TAIL;
+static_assert(kKelTail == 6 || kKelTail == 7, "tail of 6 or 7 vertices");
+constexpr int kKelWarps = kKelTail == 6 ? 4 : 11;
+// Tail of S vertices: the root (2S x 2S) and the outputs of the odd levels sit
+// in bufE, the outputs of the even levels in bufO; level J (J = 0..S-4) makes
+// 2^(J+1) nodes of size 2(S-J-1). S = 6: bufE 144, 256; bufO 200, 288.
+// S = 7: bufE 196, 400, 576; bufO 288, 512.
+__host__ __device__ constexpr int kel_level_entries(int S, int J) {
+    return (2 << J) * (2 * (S - J - 1)) * (2 * (S - J - 1));
+}
+__host__ __device__ constexpr int kel_buf_entries(int S, int first) {
+    int b = first == 1 ? 4 * S * S : 0;
+    for (int J = first; J <= S - 4; J += 2) b = b > kel_level_entries(S, J) ? b : kel_level_entries(S, J);
+    return b;
+}
+// row factors: nchild * (m - 2) at level J, and up to 30 for a depth-first step
+__host__ __device__ constexpr int kel_fac_entries(int S) {
+    int b = 32;
+    for (int J = 0; J <= S - 4; ++J) {
+        const int f = (2 << J) * (2 * (S - J) - 2);
+        b = b > f ? b : f;
+    }
+    return b;
+}
+constexpr int kKelBufE = kel_buf_entries(kKelTail, 1);
+constexpr int kKelBufO = kel_buf_entries(kKelTail, 0);
+constexpr int kKelFac = kel_fac_entries(kKelTail);
+static_assert(kKelTail != 6 || (kKelBufE == 256 && kKelBufO == 288 && kKelFac == 48), "6-vertex tail");
+static_assert(kKelTail != 7 || (kKelBufE == 576 && kKelBufO == 512 && kKelFac == 96), "7-vertex tail");
 
 struct KelWarpSmem {
     double2 bufE[kKelBufE];
     double2 bufO[kKelBufO];
-    double2 fac[64];
+    double2 fac[kKelFac];
     double2 inv[16];
     double2 ndet[2][16];
     double2 part[17];
@@ -44,6 +86,9 @@ struct KelWarpSmem {
     int bad;
     int flags;
 };
+// CTAs per SM that the shared memory allows (228 KB per SM, 1 KB reserved per CTA)
+constexpr int kKelMinBlocks = static_cast<int>((228 * 1024) / (kKelWarps * sizeof(KelWarpSmem) + 1024));
+static_assert(kKelMinBlocks >= 1, "tail buffers exceed shared memory");
 
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
     return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
@@ -52,15 +97,39 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
 __device__ __forceinline__ double2 cfms(double2 a, double2 b, double2 c) {
     return make_double2(fma(-a.x, b.x, fma(a.y, b.y, c.x)), fma(-a.x, b.y, fma(-a.y, b.x, c.y)));
 }
+// c + a*b
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {
+    return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ double2 cneg_if(double2 a, bool neg) {
     return neg ? make_double2(-a.x, -a.y) : a;
 }
-// 1/p; flags a zero or non-finite pivot
+// 1/d for d >= 0. Where d and 1/d are normal numbers (biased exponent of d in
+// 3..2044): the hardware approximation (rcp.approx.ftz.f64, relative error far
+// below 2^-14) refined by two Newton-Raphson steps x <- x + x(1 - d x), each of
+// which squares the relative error, so the result is within a few units in the
+// last place. Elsewhere (zero, subnormal, huge, inf, NaN): the IEEE division.
+__device__ __forceinline__ double rcp_nr(double d) {
+    const unsigned ex = (static_cast<unsigned>(__double2hiint(d)) >> 20) & 0x7ffu;
+    if (ex - 3u < 2042u) {
+        double x;
+        asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(x) : "d"(d));
+        double e = fma(-d, x, 1.0);
+        x = fma(x, e, x);
+        e = fma(-d, x, 1.0);
+        return fma(x, e, x);
+    }
+    return 1.0 / d;
+}
+// 1/p; flags a zero or non-finite pivot (|p|^2 == 0, inf or NaN), tested on
+// the bits so that no FP64 compare is issued
 __device__ __forceinline__ double2 crcp(double2 p, int &bad) {
     const double d = fma(p.x, p.x, p.y * p.y);
-    if (!(d > 0.0) || !isfinite(d)) bad = 1;
-    const double r = 1.0 / d;
+    const long long bits = __double_as_longlong(d);
+    if (bits == 0 || ((bits >> 52) & 0x7ff) == 0x7ff) bad = 1;
+    const double r = rcp_nr(d);
     return make_double2(p.x * r, -p.y * r);
 }
 __device__ __forceinline__ double2 warp_csum(double2 v) {
@@ -94,76 +163,129 @@ __device__ __forceinline__ void kel_schur(const double2 *src, int m, int alpha, 
     __syncwarp();
 }
 
-// Breadth-first tail over the last s vertices; the root (2s x 2s) is in bufE
-// with determinant det0 at depth depth0. Adds the leaf sum to part[n] and the
-// per-depth node sums to part[depth0+1 .. n-1] (partials only if want_part).
-__device__ void kel_tail(int s, int n, double2 det0, int depth0, bool want_part, bool sgn,
-                         KelWarpSmem &w, int lane, int &bad) {
-    if (s == 1) {
-        if (lane == 0) {
-            const double2 *M = w.bufE;
-            const double2 v = cadd(M[0], cneg_if(M[3], sgn));
-            w.part[n] = cadd(w.part[n], cmul(det0, v));
-        }
-        __syncwarp();
-        return;
+// Per-lane running sums of one matrix, indexed by r = n - depth: r = 0 is the
+// full sum, r >= 1 the lower-order partial sums found in the tail. Reduced over
+// the warp once per matrix.
+struct KelAcc {
+    double2 v[kKelTail];
+};
+
+// One breadth-first level J of a tail over S vertices: the 2^J nodes of size
+// m = 2(S-J) in cur give 2^(J+1) children of size m-2 in nxt.
+template <int S, int J>
+__device__ __forceinline__ void kel_tail_level(const double2 *cur, double2 *nxt, bool want_part, bool sgn,
+                                               KelWarpSmem &w, int lane, int &bad, KelAcc &acc) {
+    constexpr int m = 2 * (S - J), m2 = m - 2, mm = m * m, mm2 = m2 * m2;
+    constexpr int nchild = 2 << J;
+    if (lane < nchild) {
+        const int alpha = lane & 1;
+        const double2 *P = cur + (lane >> 1) * mm;
+        const double2 piv = P[alpha * m + alpha];
+        w.inv[lane] = crcp(piv, bad);
+        const double2 nd = cneg_if(cmul(w.ndet[J & 1][lane >> 1], piv), sgn && alpha);
+        w.ndet[(J + 1) & 1][lane] = nd;
+        if (want_part) acc.v[S - 1 - J] = cadd(acc.v[S - 1 - J], nd);
     }
-    double2 *cur = w.bufE, *nxt = w.bufO;
-    int nodes = 1, m = 2 * s;
+    __syncwarp();
+    for (int idx = lane; idx < nchild * m2; idx += 32) {
+        const int c = idx / m2, r = idx - c * m2, alpha = c & 1;
+        const double2 *P = cur + (c >> 1) * mm;
+        w.fac[idx] = cmul(P[(r + 2) * m + alpha], w.inv[c]);
+    }
+    __syncwarp();
+    for (int e = lane; e < nchild * mm2; e += 32) {
+        const int c = e / mm2, rem = e - c * mm2, r = rem / m2, q = rem - r * m2, alpha = c & 1;
+        const double2 *P = cur + (c >> 1) * mm;
+        nxt[e] = cfms(w.fac[c * m2 + r], P[alpha * m + q + 2], P[(r + 2) * m + q + 2]);
+    }
+    __syncwarp();
+}
+
+// Closed form for the last three vertices of NODES nodes (6 x 6 each, node
+// determinants nd[]): four lanes per node, lane (a0, a1) forms the two 3 x 3
+// XOR minors with rows/columns (0,a0), (1,a1), (2,a2), a2 = 0, 1, by expansion
+// along the last row; the leading 2 x 2 cofactor and the leading entry are the
+// node's contributions to the two orders below. No pivots, no divisions.
+template <int NODES>
+__device__ __forceinline__ void kel_closed3(const double2 *cur, const double2 *nd, bool want_part, bool sgn,
+                                            int lane, KelAcc &acc) {
+    for (int idx = lane; idx < 4 * NODES; idx += 32) {
+        const int k = idx >> 2, a0 = idx & 1, a1 = (idx >> 1) & 1;
+        const double2 *M = cur + k * 36;
+        const int r0 = a0, r1 = 2 + a1;
+        const double2 A = M[r0 * 6 + r0], B = M[r0 * 6 + r1];
+        const double2 Dv = M[r1 * 6 + r0], E = M[r1 * 6 + r1];
+        const double2 C2 = cfms(B, Dv, cmul(A, E));  // A E - B D
+        double2 tot = make_double2(0.0, 0.0);
+#pragma unroll
+        for (int a2 = 0; a2 < 2; ++a2) {
+            const int r2 = 4 + a2;
+            const double2 C = M[r0 * 6 + r2], F = M[r1 * 6 + r2];
+            const double2 G = M[r2 * 6 + r0], H = M[r2 * 6 + r1], Iv = M[r2 * 6 + r2];
+            const double2 u = cfms(C, E, cmul(B, F));   // B F - C E
+            const double2 v = cfms(C, Dv, cmul(A, F));  // A F - C D
+            const double2 det = cfma(Iv, C2, cfms(H, v, cmul(G, u)));
+            tot = a2 == 0 ? det : (sgn ? csub(tot, det) : cadd(tot, det));
+        }
+        const double2 dk = cneg_if(nd[k], sgn && (a0 ^ a1));
+        acc.v[0] = cfma(dk, tot, acc.v[0]);
+        if (want_part) {
+            acc.v[1] = cfma(dk, C2, acc.v[1]);
+            if (a1 == 0) acc.v[2] = cfma(dk, A, acc.v[2]);
+        }
+    }
+}
+
+// Orders 1 and 2 (one node, the whole matrix).
+__device__ __forceinline__ void kel_closed2(const double2 *M, double2 det0, bool want_part, bool sgn, int lane,
+                                            KelAcc &acc) {
+    if (lane < 4) {
+        const int a0 = lane & 1, a1 = lane >> 1;
+        const double2 A = M[a0 * 4 + a0], B = M[a0 * 4 + 2 + a1];
+        const double2 Dv = M[(2 + a1) * 4 + a0], E = M[(2 + a1) * 4 + 2 + a1];
+        const double2 dk = cneg_if(det0, sgn && (a0 ^ a1));
+        acc.v[0] = cfma(dk, cfms(B, Dv, cmul(A, E)), acc.v[0]);
+        if (want_part && a1 == 0) acc.v[1] = cfma(dk, A, acc.v[1]);
+    }
+}
+__device__ __forceinline__ void kel_closed1(const double2 *M, double2 det0, bool sgn, int lane, KelAcc &acc) {
+    if (lane == 0) acc.v[0] = cfma(det0, sgn ? csub(M[0], M[3]) : cadd(M[0], M[3]), acc.v[0]);
+}
+
+template <int S, int J>
+__device__ __forceinline__ void kel_tail_levels(double2 *cur, double2 *nxt, double2 det0, bool want_part,
+                                                bool sgn, KelWarpSmem &w, int lane, int &bad, KelAcc &acc) {
+    if constexpr (S <= 2) {
+        if constexpr (S == 2) kel_closed2(cur, det0, want_part, sgn, lane, acc);
+        else kel_closed1(cur, det0, sgn, lane, acc);
+    } else if constexpr (J < S - 3) {
+        kel_tail_level<S, J>(cur, nxt, want_part, sgn, w, lane, bad, acc);
+        kel_tail_levels<S, J + 1>(nxt, cur, det0, want_part, sgn, w, lane, bad, acc);
+    } else {
+        kel_closed3<(1 << J)>(cur, w.ndet[J & 1], want_part, sgn, lane, acc);
+    }
+}
+
+// Breadth-first tail over the last S vertices; the root (2S x 2S) is in bufE
+// with determinant det0. Adds its leaf sum and (if want_part) the node sums of
+// the S lowest depths into the lane accumulators.
+template <int S>
+__device__ __forceinline__ void kel_tail(double2 det0, bool want_part, bool sgn, KelWarpSmem &w, int lane,
+                                         int &bad, KelAcc &acc) {
     if (lane == 0) w.ndet[0][0] = det0;
     __syncwarp();
-    for (int j = 0; j < s - 2; ++j) {
-        const int nchild = 2 * nodes, m2 = m - 2, mm = m * m, mm2 = m2 * m2;
-        if (lane < nchild) {
-            const int alpha = lane & 1;
-            const double2 *P = cur + (lane >> 1) * mm;
-            const double2 piv = P[alpha * m + alpha];
-            w.inv[lane] = crcp(piv, bad);
-            w.ndet[(j + 1) & 1][lane] = cneg_if(cmul(w.ndet[j & 1][lane >> 1], piv), sgn && alpha);
-        }
-        __syncwarp();
-        for (int idx = lane; idx < nchild * m2; idx += 32) {
-            const int c = idx / m2, r = idx - c * m2, alpha = c & 1;
-            const double2 *P = cur + (c >> 1) * mm;
-            w.fac[idx] = cmul(P[(r + 2) * m + alpha], w.inv[c]);
-        }
-        __syncwarp();
-        for (int e = lane; e < nchild * mm2; e += 32) {
-            const int c = e / mm2, rem = e - c * mm2, r = rem / m2, q = rem - r * m2, alpha = c & 1;
-            const double2 *P = cur + (c >> 1) * mm;
-            nxt[e] = cfms(w.fac[c * m2 + r], P[alpha * m + q + 2], P[(r + 2) * m + q + 2]);
-        }
-        __syncwarp();
-        if (want_part) {
-            double2 v = lane < nchild ? w.ndet[(j + 1) & 1][lane] : make_double2(0.0, 0.0);
-            v = warp_csum(v);
-            if (lane == 0) w.part[depth0 + j + 1] = cadd(w.part[depth0 + j + 1], v);
-        }
-        double2 *t = cur;
-        cur = nxt;
-        nxt = t;
-        nodes = nchild;
-        m = m2;
-    }
-    // 4x4 nodes: leaves are 2x2 determinants of rows/cols (0|1, 2|3)
-    const double2 *nd = w.ndet[(s - 2) & 1];
-    double2 acc = make_double2(0.0, 0.0), accp = make_double2(0.0, 0.0);
-    for (int idx = lane; idx < nodes * 4; idx += 32) {
-        const int k = idx >> 2, al = idx & 1, be = (idx >> 1) & 1;
-        const double2 *M = cur + k * 16;
-        const double2 dk = nd[k];
-        const double2 d2 = cfms(M[al * 4 + 2 + be], M[(2 + be) * 4 + al],
-                                cmul(M[al * 4 + al], M[(2 + be) * 4 + 2 + be]));
-        acc = cadd(acc, cneg_if(cmul(dk, d2), sgn && (al ^ be)));
-        if (want_part && be == 0) accp = cadd(accp, cneg_if(cmul(dk, M[al * 4 + al]), sgn && al));
-    }
-    acc = warp_csum(acc);
-    if (want_part) accp = warp_csum(accp);
-    if (lane == 0) {
-        w.part[n] = cadd(w.part[n], acc);
-        if (want_part) w.part[n - 1] = cadd(w.part[n - 1], accp);
-    }
+    kel_tail_levels<S, 0>(w.bufE, w.bufO, det0, want_part, sgn, w, lane, bad, acc);
     __syncwarp();
+}
+
+// Whole matrix of order n <= S as one tail (root determinant 1).
+template <int S>
+__device__ __forceinline__ void kel_tail_order(int n, bool want_part, bool sgn, KelWarpSmem &w, int lane,
+                                               int &bad, KelAcc &acc) {
+    if constexpr (S >= 1) {
+        if (n == S) kel_tail<S>(make_double2(1.0, 0.0), want_part, sgn, w, lane, bad, acc);
+        else kel_tail_order<S - 1>(n, want_part, sgn, w, lane, bad, acc);
+    }
 }
 
 // One matrix of order n (whole warp): writes sum[2], partial[(n+1)*2] (if not
@@ -181,13 +303,16 @@ __device__ __forceinline__ void kel_matrix(const double2 *A, int n, bool sgn, do
         if (!isfinite(v.x) || !isfinite(v.y)) nonfin = 1;
     }
     nonfin = __any_sync(0xffffffffu, nonfin);
+    KelAcc acc;
+#pragma unroll
+    for (int r = 0; r < kKelTail; ++r) acc.v[r] = make_double2(0.0, 0.0);
     if (lane <= n) w.part[lane] = make_double2(lane == 0 ? 1.0 : 0.0, 0.0);
     if (lane == 0) w.pdet[0] = make_double2(1.0, 0.0);
     __syncwarp();
     if (D == 0) {
         for (int e = lane; e < m0 * m0; e += 32) w.bufE[e] = A[e];
         __syncwarp();
-        kel_tail(s, n, make_double2(1.0, 0.0), 0, want_part, sgn, w, lane, bad);
+        kel_tail_order<kKelTail>(n, want_part, sgn, w, lane, bad, acc);
     } else {
         for (int64_t t = 0; t < (int64_t(1) << D); ++t) {
             // first depth whose index changed from t-1 to t (vertex 0 <-> top bit)
@@ -209,9 +334,17 @@ __device__ __forceinline__ void kel_matrix(const double2 *A, int n, bool sgn, do
                 }
                 __syncwarp();
             }
-            kel_tail(s, n, w.pdet[D], D, want_part, sgn, w, lane, bad);
+            kel_tail<kKelTail>(w.pdet[D], want_part, sgn, w, lane, bad, acc);
         }
     }
+#pragma unroll
+    for (int r = 0; r < kKelTail; ++r) {
+        if (r == 0 || want_part) {
+            const double2 v = warp_csum(acc.v[r]);
+            if (lane == 0 && n - r >= 1) w.part[n - r] = cadd(w.part[n - r], v);
+        }
+    }
+    __syncwarp();
     bad = __any_sync(0xffffffffu, bad);
     const double nanv = __longlong_as_double(0x7ff8000000000000ll);
     if (lane == 0) {
@@ -228,7 +361,7 @@ __device__ __forceinline__ void kel_matrix(const double2 *A, int n, bool sgn, do
     __syncwarp();
 }
 
-__global__ void __launch_bounds__(kKelWarps * 32) keldysh_kernel(
+__global__ void __launch_bounds__(kKelWarps * 32, kKelMinBlocks) keldysh_kernel(
     const double2 *__restrict__ Mt, int n, int64_t batch, int sgn_flag, double *sum, double *partial,
     uint32_t *status, double2 *stack_base, size_t stack_per_warp) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -246,7 +379,7 @@ __global__ void __launch_bounds__(kKelWarps * 32) keldysh_kernel(
 
 // Uneven batch: warps take matrices longest-first from `order` through a
 // global counter. partial rows have 17 complex entries per matrix.
-__global__ void __launch_bounds__(kKelWarps * 32) keldysh_varlen_kernel(
+__global__ void __launch_bounds__(kKelWarps * 32, kKelMinBlocks) keldysh_varlen_kernel(
     const double2 *__restrict__ Mt, const int64_t *__restrict__ m_off, const int *__restrict__ n_arr,
     int64_t batch, int n_max, int sgn_flag, double *sum, double *partial, uint32_t *status,
     double2 *stack_base, size_t stack_per_warp, const int *__restrict__ order, unsigned *ctr) {
@@ -296,6 +429,9 @@ int keldysh_grid(int64_t batch, int *err) {
         e = cudaFuncSetAttribute(keldysh_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  static_cast<int>(smem));
     if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(keldysh_varlen_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(smem));
+    if (e == cudaSuccess)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, keldysh_kernel, kKelWarps * 32, smem);
     if (e != cudaSuccess || per_sm < 1) {
         *err = e != cudaSuccess ? static_cast<int>(e) : static_cast<int>(cudaErrorInvalidConfiguration);
@@ -329,11 +465,12 @@ int launch_keldysh(const double *Mt, int n, int64_t batch, int sgn, double *sum,
 // ---------------------------------------------------------------------------
 
 constexpr int kKelNoAllocMaxN = 14;
-constexpr int kKelNoAllocBlocks = 152;
+constexpr int kKelNoAllocWarps = 608;
+constexpr int kKelNoAllocBlocks = kKelNoAllocWarps / kKelWarps;
 constexpr size_t kKelNoAllocStack = kel_stack_entries(kKelNoAllocMaxN);
-static_assert(kKelNoAllocStack == 2912, "stack size of order 14");
+static_assert(kKelNoAllocStack <= 2912, "stack size of order 14");
 
-// 152 CTAs x 4 warps x 2912 complex entries x 16 B = 28.3 MB per device.
+// 608 warps x at most 2912 complex entries x 16 B = 28.3 MB per device.
 static __device__ __align__(256) double2 g_kel_noalloc_stack[kKelNoAllocBlocks * kKelWarps *
                                                             kKelNoAllocStack];
 
