@@ -156,7 +156,11 @@ apm_status_t apm_cdet_from_weights(const double *a, int n, int64_t batch, double
  *   status   [batch] or NULL; APM_ST_ZERO_PIVOT marks a zero or non-finite pivot,
  *            and then sum (and partial) of that matrix are NaN.
  *   workspace / workspace_bytes: scratch for the depth-first part of the tree,
- *            needed for n > 7 (apm_workspace_size with APM_OP_KELDYSH).
+ *            needed for n > 8 (apm_workspace_size with APM_OP_KELDYSH says how
+ *            much): the per-warp path matrices and, when the batch is too
+ *            small to occupy every warp, one slot of n+1 sums per chunk of a
+ *            matrix (the matrix's leaves are then split over several warps and
+ *            the chunks added in a fixed order, so results stay reproducible).
  */
 apm_status_t apm_keldysh_sum(const double *Mt, int n, int64_t batch, int flags, double *sum,
                              double *partial, uint32_t *status, void *workspace,
@@ -170,9 +174,9 @@ apm_status_t apm_keldysh_sum(const double *Mt, int n, int64_t batch, int flags, 
  * pool owns the memory), and plugin hosts that only pass device pointers in.
  * There is no counterpart in the paper; it is a packaging of the same kernel.
  *   Instead of a caller workspace, the depth-first stack uses a fixed array in
- *   device memory that belongs to the library: 152 x 4 warp slots for orders up
- *   to 14, 28.3 MB, held on every GPU that loads the library until the process
- *   exits. Orders above 14 are rejected with APM_ERR_UNSUPPORTED_N (use
+ *   device memory that belongs to the library: 605 warp slots (55 CTAs of 11
+ *   warps) for orders up to 14, 26.3 MB, held on every GPU that loads the
+ *   library until the process exits; matrices are never split over warps here. Orders above 14 are rejected with APM_ERR_UNSUPPORTED_N (use
  *   apm_keldysh_sum with a workspace). The call allocates nothing.
  *   The first call on a device looks up the array's device address (once per
  *   device, with that device current); make that first call before any stream

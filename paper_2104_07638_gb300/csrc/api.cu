@@ -249,12 +249,11 @@ apm_status_t apm_workspace_size(int op, int n_max, int64_t batch, int two_mats, 
         }
         case APM_OP_KELDYSH: {
             if (n_max < 1 || n_max > APM_MAX_N_KELDYSH) return APM_ERR_UNSUPPORTED_N;
-            const size_t per = apm::keldysh_stack_entries(n_max);
-            if (per == 0 || batch == 0) return APM_OK;
-            int err = 0;
-            const int grid = apm::keldysh_grid(batch, &err);
+            if (apm::keldysh_stack_entries(n_max) == 0 || batch == 0) return APM_OK;
+            apm::KeldyshPlan p;
+            const int err = apm::keldysh_plan(n_max, batch, &p);
             if (err) return cuda_fail(err);
-            *bytes = static_cast<size_t>(grid) * apm::keldysh_warps_per_block() * per * 2 * sizeof(double);
+            *bytes = p.total;
             return APM_OK;
         }
         case APM_OP_PERM_MINORS:

@@ -53,6 +53,14 @@ int ensure_tables();
 // Per-layer lane-group sizes (log2) chosen by the cost model for order n.
 void cdet_group_table(int n, int threads, uint8_t *gsel /*[17]*/);
 
+// Fixed-order Keldysh launch layout: grid, chunks per matrix (log2) and the
+// workspace parts (depth-first stacks, chunk slots, chunk flags, counters).
+struct KeldyshPlan {
+    int grid;
+    int kc;
+    size_t stack_bytes, slot_bytes, flag_bytes, ctr_bytes, total;
+};
+int keldysh_plan(int n, int64_t batch, KeldyshPlan *p);
 int launch_keldysh(const double *Mt, int n, int64_t batch, int sgn, double *sum, double *partial,
                    uint32_t *status, void *workspace, cudaStream_t s);
 int keldysh_grid(int64_t batch, int *err);

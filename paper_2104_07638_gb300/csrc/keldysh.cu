@@ -288,16 +288,19 @@ __device__ __forceinline__ void kel_tail_order(int n, bool want_part, bool sgn, 
     }
 }
 
-// One matrix of order n (whole warp): writes sum[2], partial[(n+1)*2] (if not
-// NULL) and the status word.
-__device__ __forceinline__ void kel_matrix(const double2 *A, int n, bool sgn, double *sum_out,
-                                           double *partial_out, uint32_t *status_out, double2 *stack,
-                                           KelWarpSmem &w, int lane) {
-    const bool want_part = partial_out != nullptr;
+// Depth-first leaves t0 <= t < t1 of one matrix of order n (whole warp; all
+// 2^(n-S) leaves, or one chunk of them). Leaves the sums in w.part[0..n]
+// (part[0] = 1) and sets bad / nonfin. A node's determinant is added to the
+// partial sum of its depth at the node's first leaf only, so chunks of one
+// matrix never count a node twice.
+__device__ __forceinline__ void kel_matrix(const double2 *A, int n, bool sgn, bool want_part, int64_t t0,
+                                           int64_t t1, double2 *stack, KelWarpSmem &w, int lane, int &bad,
+                                           int &nonfin) {
     const int s = n < kKelTail ? n : kKelTail;
     const int D = n - s;
     const int m0 = 2 * n;
-    int bad = 0, nonfin = 0;
+    bad = 0;
+    nonfin = 0;
     for (int e = lane; e < m0 * m0; e += 32) {
         const double2 v = A[e];
         if (!isfinite(v.x) || !isfinite(v.y)) nonfin = 1;
@@ -314,9 +317,10 @@ __device__ __forceinline__ void kel_matrix(const double2 *A, int n, bool sgn, do
         __syncwarp();
         kel_tail_order<kKelTail>(n, want_part, sgn, w, lane, bad, acc);
     } else {
-        for (int64_t t = 0; t < (int64_t(1) << D); ++t) {
-            // first depth whose index changed from t-1 to t (vertex 0 <-> top bit)
-            const int d0 = t == 0 ? 0 : D - __ffsll(t);
+        for (int64_t t = t0; t < t1; ++t) {
+            // first depth whose index changed from t-1 to t (vertex 0 <-> top
+            // bit); the first leaf of a chunk builds its whole path
+            const int d0 = t == t0 ? 0 : D - __ffsll(t);
             size_t off = 0;  // stack offset of depth d0 (depths 1..D-1 are stacked)
             for (int d = 1; d < d0; ++d) off += static_cast<size_t>(2 * (n - d)) * (2 * (n - d));
             for (int d = d0; d < D; ++d) {
@@ -330,7 +334,8 @@ __device__ __forceinline__ void kel_matrix(const double2 *A, int n, bool sgn, do
                 if (lane == 0) {
                     const double2 pd = cneg_if(cmul(w.pdet[d], piv), sgn && alpha);
                     w.pdet[d + 1] = pd;
-                    if (want_part) w.part[d + 1] = cadd(w.part[d + 1], pd);
+                    const bool first_leaf = (t & ((int64_t(1) << (D - 1 - d)) - 1)) == 0;
+                    if (want_part && first_leaf) w.part[d + 1] = cadd(w.part[d + 1], pd);
                 }
                 __syncwarp();
             }
@@ -344,8 +349,14 @@ __device__ __forceinline__ void kel_matrix(const double2 *A, int n, bool sgn, do
             if (lane == 0 && n - r >= 1) w.part[n - r] = cadd(w.part[n - r], v);
         }
     }
-    __syncwarp();
     bad = __any_sync(0xffffffffu, bad);
+    __syncwarp();
+}
+
+// Final results of one matrix from w.part: sum[2], partial[(n+1)*2] (if not
+// NULL) and the status word; NaN where a pivot failed or the input is not finite.
+__device__ __forceinline__ void kel_store(int n, int bad, int nonfin, double *sum_out, double *partial_out,
+                                          uint32_t *status_out, const KelWarpSmem &w, int lane) {
     const double nanv = __longlong_as_double(0x7ff8000000000000ll);
     if (lane == 0) {
         const double2 r = (bad || nonfin) ? make_double2(nanv, nanv) : w.part[n];
@@ -353,7 +364,7 @@ __device__ __forceinline__ void kel_matrix(const double2 *A, int n, bool sgn, do
         sum_out[1] = r.y;
         if (status_out) *status_out = (bad ? APM_ST_ZERO_PIVOT : 0u) | (nonfin ? APM_ST_NONFINITE_INPUT : 0u);
     }
-    if (want_part && lane <= n) {
+    if (partial_out && lane <= n) {
         const double2 r = (bad || nonfin) ? make_double2(nanv, nanv) : w.part[lane];
         partial_out[2 * lane] = r.x;
         partial_out[2 * lane + 1] = r.y;
@@ -361,20 +372,59 @@ __device__ __forceinline__ void kel_matrix(const double2 *A, int n, bool sgn, do
     __syncwarp();
 }
 
+// Fixed order n. Work items are (matrix, chunk) pairs: 2^kc chunks of 2^(D-kc)
+// consecutive depth-first leaves per matrix (kc = 0: whole matrices). With
+// kc > 0 every chunk writes its sums and flags to a slot and counts itself in
+// ctr[b]; the warp that completes the count adds the slots in chunk order
+// (fixed, so the result does not depend on which warp finishes last) and
+// stores the matrix's results. ctr must be zero at launch.
 __global__ void __launch_bounds__(kKelWarps * 32, kKelMinBlocks) keldysh_kernel(
     const double2 *__restrict__ Mt, int n, int64_t batch, int sgn_flag, double *sum, double *partial,
-    uint32_t *status, double2 *stack_base, size_t stack_per_warp) {
+    uint32_t *status, double2 *stack_base, size_t stack_per_warp, int kc, double2 *slots,
+    uint32_t *slot_flags, unsigned *ctr) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     KelWarpSmem &w = reinterpret_cast<KelWarpSmem *>(smem_raw)[wid];
     const int64_t gw = static_cast<int64_t>(blockIdx.x) * kKelWarps + wid;
     const int64_t nw = static_cast<int64_t>(gridDim.x) * kKelWarps;
-    double2 *stack = stack_base + gw * stack_per_warp;
+    double2 *stack = stack_base ? stack_base + gw * stack_per_warp : nullptr;
     const int64_t m0 = 2 * n;
-    for (int64_t b = gw; b < batch; b += nw)
-        kel_matrix(Mt + b * m0 * m0, n, sgn_flag != 0, sum + 2 * b,
-                   partial ? partial + b * (n + 1) * 2 : nullptr, status ? status + b : nullptr, stack, w,
-                   lane);
+    const int D = n > kKelTail ? n - kKelTail : 0;
+    const int64_t nchunk = int64_t(1) << kc, leaves = int64_t(1) << (D - kc);
+    const bool want_part = partial != nullptr;
+    for (int64_t it = gw; it < (batch << kc); it += nw) {
+        const int64_t b = it >> kc, c = it & (nchunk - 1);
+        int bad, nonfin;
+        kel_matrix(Mt + b * m0 * m0, n, sgn_flag != 0, want_part, c * leaves, (c + 1) * leaves, stack, w, lane,
+                   bad, nonfin);
+        double *sum_b = sum + 2 * b;
+        double *part_b = want_part ? partial + b * (n + 1) * 2 : nullptr;
+        uint32_t *st_b = status ? status + b : nullptr;
+        if (kc == 0) {
+            kel_store(n, bad, nonfin, sum_b, part_b, st_b, w, lane);
+            continue;
+        }
+        double2 *slot = slots + it * (n + 1);
+        if (lane <= n) slot[lane] = w.part[lane];
+        if (lane == 0) slot_flags[it] = (bad ? 1u : 0u) | (nonfin ? 2u : 0u);
+        __threadfence();
+        __syncwarp();
+        unsigned prev = 0;
+        if (lane == 0) prev = atomicAdd(ctr + b, 1u);
+        prev = __shfl_sync(0xffffffffu, prev, 0);
+        if (prev != static_cast<unsigned>(nchunk - 1)) continue;
+        __threadfence();
+        double2 v = make_double2(0.0, 0.0);
+        uint32_t fl = 0;
+        const double2 *slot_b = slots + (b << kc) * (n + 1);
+        for (int64_t cc = 0; cc < nchunk; ++cc) {
+            if (lane <= n) v = cadd(v, __ldcg(slot_b + cc * (n + 1) + lane));
+            fl |= __ldcg(slot_flags + (b << kc) + cc);
+        }
+        if (lane <= n) w.part[lane] = lane == 0 ? make_double2(1.0, 0.0) : v;
+        __syncwarp();
+        kel_store(n, (fl & 1u) ? 1 : 0, (fl & 2u) ? 1 : 0, sum_b, part_b, st_b, w, lane);
+    }
 }
 
 // Uneven batch: warps take matrices longest-first from `order` through a
@@ -399,9 +449,13 @@ __global__ void __launch_bounds__(kKelWarps * 32, kKelMinBlocks) keldysh_varlen_
             if (lane == 0 && status) status[b] = APM_ST_BAD_ORDER;
             continue;
         }
-        kel_matrix(Mt + m_off[b], n, sgn_flag != 0, sum + 2 * static_cast<int64_t>(b),
-                   partial ? partial + static_cast<int64_t>(b) * 17 * 2 : nullptr, status ? status + b : nullptr,
-                   stack, w, lane);
+        const int D = n > kKelTail ? n - kKelTail : 0;
+        int bad, nonfin;
+        kel_matrix(Mt + m_off[b], n, sgn_flag != 0, partial != nullptr, 0, int64_t(1) << D, stack, w, lane, bad,
+                   nonfin);
+        kel_store(n, bad, nonfin, sum + 2 * static_cast<int64_t>(b),
+                  partial ? partial + static_cast<int64_t>(b) * 17 * 2 : nullptr, status ? status + b : nullptr, w,
+                  lane);
     }
 }
 
@@ -446,16 +500,69 @@ int keldysh_grid(int64_t batch, int *err) {
 
 int keldysh_warps_per_block() { return kKelWarps; }
 
+// Chunks per matrix for a fixed-order launch: the smallest power of two whose
+// (matrix, chunk) items fill at least 90 % of the warps' last round (chunks of
+// at least 4 depth-first leaves), else the best fill among those allowed.
+static int keldysh_chunk_log2(int n, int64_t batch, int64_t warps) {
+    const int D = n > kKelTail ? n - kKelTail : 0;
+    const int kmax = D > 2 ? D - 2 : 0;
+    int best = 0;
+    double best_fill = 0.0;
+    for (int k = 0; k <= kmax; ++k) {
+        const int64_t items = batch << k;
+        const int64_t rounds = (items + warps - 1) / warps;
+        const double fill = static_cast<double>(items) / static_cast<double>(rounds * warps);
+        if (fill >= 0.9) return k;
+        if (fill > best_fill + 1e-12) {
+            best_fill = fill;
+            best = k;
+        }
+    }
+    return best;
+}
+
+int keldysh_plan(int n, int64_t batch, KeldyshPlan *p) {
+    int err = 0;
+    const int full = keldysh_grid(INT64_MAX / 64, &err);  // all resident CTAs
+    if (err) return err;
+    const int64_t warps = static_cast<int64_t>(full) * kKelWarps;
+    p->kc = keldysh_chunk_log2(n, batch, warps);
+    const int64_t items = batch << p->kc;
+    const int64_t need = (items + kKelWarps - 1) / kKelWarps;
+    p->grid = static_cast<int>(need < full ? (need < 1 ? 1 : need) : full);
+    p->stack_bytes = static_cast<size_t>(p->grid) * kKelWarps * kel_stack_entries(n) * sizeof(double2);
+    if (p->kc == 0) {
+        p->slot_bytes = p->flag_bytes = p->ctr_bytes = 0;
+    } else {
+        p->slot_bytes = static_cast<size_t>(items) * (n + 1) * sizeof(double2);
+        p->flag_bytes = (static_cast<size_t>(items) * sizeof(uint32_t) + 15) & ~size_t(15);
+        p->ctr_bytes = (static_cast<size_t>(batch) * sizeof(unsigned) + 15) & ~size_t(15);
+    }
+    p->total = p->stack_bytes + p->slot_bytes + p->flag_bytes + p->ctr_bytes;
+    return 0;
+}
+
 int launch_keldysh(const double *Mt, int n, int64_t batch, int sgn, double *sum, double *partial,
                    uint32_t *status, void *workspace, cudaStream_t s) {
-    int err = 0;
-    const int grid = keldysh_grid(batch, &err);
+    KeldyshPlan p;
+    const int err = keldysh_plan(n, batch, &p);
     if (err) return err;
+    unsigned char *ws = static_cast<unsigned char *>(workspace);
+    double2 *stack = p.stack_bytes ? reinterpret_cast<double2 *>(ws) : nullptr;
+    double2 *slots = nullptr;
+    uint32_t *slot_flags = nullptr;
+    unsigned *ctr = nullptr;
+    if (p.kc > 0) {
+        slots = reinterpret_cast<double2 *>(ws + p.stack_bytes);
+        slot_flags = reinterpret_cast<uint32_t *>(ws + p.stack_bytes + p.slot_bytes);
+        ctr = reinterpret_cast<unsigned *>(ws + p.stack_bytes + p.slot_bytes + p.flag_bytes);
+        const cudaError_t e = cudaMemsetAsync(ctr, 0, static_cast<size_t>(batch) * sizeof(unsigned), s);
+        if (e != cudaSuccess) return static_cast<int>(e);
+    }
     const size_t smem = kKelWarps * sizeof(KelWarpSmem);
-    keldysh_kernel<<<grid, kKelWarps * 32, smem, s>>>(reinterpret_cast<const double2 *>(Mt), n, batch,
-                                                      sgn, sum, partial, status,
-                                                      static_cast<double2 *>(workspace),
-                                                      kel_stack_entries(n));
+    keldysh_kernel<<<p.grid, kKelWarps * 32, smem, s>>>(reinterpret_cast<const double2 *>(Mt), n, batch, sgn,
+                                                        sum, partial, status, stack, kel_stack_entries(n), p.kc,
+                                                        slots, slot_flags, ctr);
     return static_cast<int>(cudaGetLastError());
 }
 
@@ -516,6 +623,6 @@ extern "C" apm_status_t apm_keldysh_sum_noalloc(const double *Mt, int n, int64_t
     const int grid = static_cast<int>(need < kKelNoAllocBlocks ? need : kKelNoAllocBlocks);
     keldysh_kernel<<<grid, kKelWarps * 32, smem, reinterpret_cast<cudaStream_t>(stream)>>>(
         reinterpret_cast<const double2 *>(Mt), n, batch, (flags & APM_KELDYSH_SIGNED) ? 1 : 0, sum,
-        partial, status, static_cast<double2 *>(scratch), kel_stack_entries(n));
+        partial, status, static_cast<double2 *>(scratch), kel_stack_entries(n), 0, nullptr, nullptr, nullptr);
     return cudaGetLastError() == cudaSuccess ? APM_OK : APM_ERR_CUDA;
 }

@@ -112,3 +112,17 @@ def test_many_matrices_and_determinism(apm):
     sref = oracle.keldysh(Mt[idx].cpu().numpy())
     scale = oracle.keldysh_scale(Mt[idx].cpu().numpy())
     assert np.all(np.abs(a[idx].cpu().numpy() - sref) <= TOL * scale)
+
+
+@pytest.mark.parametrize("n,batch", [(13, 5), (14, 3)])
+def test_small_batch_split_over_warps(apm, n, batch):
+    """A batch far smaller than the number of warps is split into chunks of
+    depth-first leaves per matrix; sums and every partial order must still match
+    the oracle, and repeated calls must agree bit for bit."""
+    Mt = I.keldysh_batch(batch, n, seed=950 + n)
+    for signed in (False, True):
+        check(apm, Mt, signed=signed, partial=True)
+    d = dev(Mt)
+    a = apm.keldysh_sum(d, partial=True)
+    b = apm.keldysh_sum(d, partial=True)
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])

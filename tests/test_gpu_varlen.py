@@ -120,6 +120,10 @@ def test_tuned_tables_keep_bitwise_agreement(apm):
 
 
 def test_keldysh_varlen_bitwise_equals_fixed(apm):
+    """The uneven-batch kernel walks each matrix like a fixed-order launch of
+    whole matrices: bit-identical results. A fixed-order launch of one matrix of
+    order >= 10 splits it over warps (chunks added in a fixed order), which only
+    changes rounding: those are compared within the parity tolerance."""
     orders = np.array([1, 2, 5, 6, 7, 9, 12, 14, 16, 3, 8, 11], dtype=np.int32)
     flat, off = I.keldysh_varlen(orders, seed=1307)
     Mt = torch.as_tensor(flat).cuda()
@@ -131,8 +135,13 @@ def test_keldysh_varlen_bitwise_equals_fixed(apm):
         nb = int(nb)
         M = flat[off[b]:off[b] + 4 * nb * nb].reshape(1, 2 * nb, 2 * nb)
         sf, pf = apm.keldysh_sum(torch.as_tensor(M).cuda(), partial=True)
-        assert s[b] == sf.cpu().numpy()[0]
-        assert np.array_equal(p[b, :nb + 1], pf.cpu().numpy()[0])
+        if nb <= 9:
+            assert s[b] == sf.cpu().numpy()[0]
+            assert np.array_equal(p[b, :nb + 1], pf.cpu().numpy()[0])
+        else:
+            scale = oracle.keldysh_scale(M, use_perm=False)[0]
+            assert abs(s[b] - sf.cpu().numpy()[0]) <= TOL * scale
+            assert np.all(np.abs(p[b, :nb + 1] - pf.cpu().numpy()[0]) <= TOL * scale)
         if nb <= 9:
             assert abs(s[b] - oracle.keldysh(M)[0]) <= TOL * oracle.keldysh_scale(M)[0]
 
