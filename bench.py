@@ -338,7 +338,7 @@ def profile_case(name: str):
         M = torch.as_tensor(inputs.keldysh_batch(8192, 12, seed=3)).to(dev)
         run = lambda: apm.keldysh_sum(M)
     elif name == "ppm_n14":
-        P = torch.as_tensor(inputs.perm_batch(14, 1024, seed=4)).to(dev)
+        P = torch.as_tensor(inputs.perm_batch(14, 1368, seed=4)).to(dev)
         run = lambda: apm.perm_minors(P)
     else:
         orders = inputs.varlen_orders(16384, 4, 16, seed=3)
