@@ -22,17 +22,15 @@
 //    popcount), the 8 starting products base_b(T_L) = prod_{i in T_H u R_b} u_i
 //    over the subsets R_b of the lowest (up to) three high elements outside
 //    T_H, and the 3^l entries B(T_L, S_L) level by level over |S_L \ T_L|, one
-//    multiply each; products of several factors are balanced trees, because a
-//    dependent FP64 step costs hundreds of cycles while other CTAs keep the
-//    FP64 pipe busy. The owners of T_L are chosen so that the warps get equal
+//    multiply each. The owners of T_L are chosen so that the warps get equal
 //    shares.
 //  * products (warp b takes the S_H = T_H u R_b u R' for all R' over the
 //    remaining free high elements, depth first, so that each alpha vector is
 //    its parent's times one u_i; the path stays in registers): for every S_L
 //    the sum over its submasks T_L of alpha(T_L) B(T_L, S_L), one FMA per
 //    (T, S) pair. The 3^l terms are laid out over 64 term streams, two per
-//    lane, by McNaughton's wrap-around rule (every stream ceil(3^l/64) terms; at
-//    most 63 sets S_L cut between two streams), with the B entries stored
+//    lane, of at most ceil(3^l/64) terms each, by best fit (a set is cut
+//    between streams only where it fits in none), with the B entries stored
 //    stream-interleaved so that a lane reads its two as one 16-byte word, and
 //    the terms inside each run ordered so that the alpha gathers of a
 //    half-warp mostly hit distinct banks. A stream writes the sum of each run
@@ -104,9 +102,12 @@ static void build_schedules(std::vector<int> &buf) {
         int total = 1;
         for (int i = 0; i < l; ++i) total *= 3;
         const int cap = (total + kPpmVLanes - 1) / kPpmVLanes;
-        // wrap-around layout over 64 term streams (stream v = 2 lane + s):
-        // sets S_L by decreasing size, filling stream after stream up to cap
-        // terms; a set cut at a stream end gets one result slot per run
+        // layout over 64 term streams (stream v = 2 lane + s) of at most cap
+        // terms: sets S_L by decreasing size, each into the fullest stream it
+        // still fits in whole (best fit); a set that fits nowhere fills the
+        // emptiest stream and continues elsewhere (a cut set gets one result
+        // slot per run). Streams are then ordered by decreasing length, so
+        // that a lane's first stream is never the shorter one.
         std::vector<int> sets(NL);
         for (int S = 0; S < NL; ++S) sets[S] = S;
         for (int i = 1; i < NL; ++i)  // stable insertion sort by decreasing popcount
@@ -118,28 +119,47 @@ static void build_schedules(std::vector<int> &buf) {
         std::vector<std::vector<Run>> runs(kPpmVLanes);
         std::vector<std::vector<int>> slots_of(NL);
         {
-            int lane = 0, q = 0, nres0 = NL;
+            std::vector<int> freec(kPpmVLanes, cap);
+            int nres0 = NL;
             for (int S : sets) {
                 const int terms = 1 << popc(S);
-                const bool cut = q + terms > cap;
-                Run r{S, cut ? nres0++ : S, {}};
-                slots_of[S].push_back(r.slot);
-                for (int k = 0; k < terms; ++k) {
-                    r.Ts.push_back(pdep_host(k, S));
-                    if (++q == cap) {
-                        runs[lane].push_back(r);
-                        q = 0;
-                        ++lane;
-                        r = Run{S, -1, {}};
-                        if (k + 1 < terms) {
-                            r.slot = nres0++;
-                            slots_of[S].push_back(r.slot);
-                        }
+                int k = 0;
+                std::vector<std::pair<int, int>> parts;  // (stream, count)
+                while (k < terms) {
+                    const int rem = terms - k;
+                    int best = -1;
+                    for (int v = 0; v < kPpmVLanes; ++v)
+                        if (freec[v] >= rem && (best < 0 || freec[v] < freec[best])) best = v;
+                    if (best < 0) {
+                        best = 0;
+                        for (int v = 1; v < kPpmVLanes; ++v)
+                            if (freec[v] > freec[best]) best = v;
                     }
+                    const int take = rem < freec[best] ? rem : freec[best];
+                    parts.push_back({best, take});
+                    freec[best] -= take;
+                    k += take;
                 }
-                if (!r.Ts.empty()) runs[lane].push_back(r);
+                k = 0;
+                for (const auto &pt : parts) {
+                    Run r{S, parts.size() > 1 ? nres0++ : S, {}};
+                    slots_of[S].push_back(r.slot);
+                    for (int t = 0; t < pt.second; ++t, ++k) r.Ts.push_back(pdep_host(k, S));
+                    runs[pt.first].push_back(r);
+                }
             }
             s.nres = nres0;
+            std::vector<int> len0(kPpmVLanes), order(kPpmVLanes);
+            for (int v = 0; v < kPpmVLanes; ++v) {
+                len0[v] = cap - freec[v];
+                order[v] = v;
+            }
+            for (int a = 1; a < kPpmVLanes; ++a)  // stable sort by decreasing length
+                for (int b2 = a; b2 > 0 && len0[order[b2]] > len0[order[b2 - 1]]; --b2)
+                    std::swap(order[b2], order[b2 - 1]);
+            std::vector<std::vector<Run>> sorted(kPpmVLanes);
+            for (int v = 0; v < kPpmVLanes; ++v) sorted[v] = runs[order[v]];
+            runs.swap(sorted);
         }
         // order of the terms inside each run (free: the run's sum is the same
         // up to rounding, and the order is fixed): position by position, the
@@ -327,18 +347,13 @@ __device__ __forceinline__ double neg_bits(double x) {
     return __longlong_as_double(__double_as_longlong(x) ^ static_cast<long long>(0x8000000000000000ull));
 }
 
-// prod over the set bits e < K of mask of U[(row0 + e) * 128 + col], as a
-// balanced tree (depth log2 K instead of a chain; absent factors are 1)
-template <int K>
-__device__ __forceinline__ double tree_prod(const double *U, int row0, int mask, int col) {
-    double f[K];
-#pragma unroll
-    for (int e = 0; e < K; ++e) f[e] = ((mask >> e) & 1) ? U[(row0 + e) * 128 + col] : 1.0;
-#pragma unroll
-    for (int w = 1; w < K; w *= 2)
-#pragma unroll
-        for (int e = 0; e + w < K; e += 2 * w) f[e] *= f[e + w];
-    return f[0];
+// prod over the set bits e of mask of U[(row0 + e) * 128 + col] (1 for an empty
+// mask): |mask| - 1 multiplies
+__device__ __forceinline__ double set_prod(const double *U, int row0, int mask, int col) {
+    if (mask == 0) return 1.0;
+    double v = U[(row0 + __ffs(mask) - 1) * 128 + col];
+    for (int r = mask & (mask - 1); r; r &= r - 1) v *= U[(row0 + __ffs(r) - 1) * 128 + col];
+    return v;
 }
 
 struct PpmSmem {
@@ -415,7 +430,7 @@ __global__ void __launch_bounds__(kPpmWarps * 32, 3) ppm_kernel(const double *__
             __syncwarp();
             for (int k = lane; k < ntl; k += 32) {
                 const int TL = tllist[k];
-                const double pt = h <= 7 ? tree_prod<7>(sm.U, l, TH, TL) : tree_prod<9>(sm.U, l, TH, TL);
+                const double pt = set_prod(sm.U, l, TH, TL);
                 double *base = &sm.alpha[0][TL];  // base[bb * 128] for the lattice element subsets bb
                 base[0] = pt;
                 if (m >= 1) {
@@ -423,15 +438,16 @@ __global__ void __launch_bounds__(kPpmWarps * 32, 3) ppm_kernel(const double *__
                     base[128] = pt * u0;
                     if (m >= 2) {
                         const double u1 = sm.U[(l + e1) * 128 + TL];
-                        const double u01 = u0 * u1;
-                        base[2 * 128] = pt * u1;
-                        base[3 * 128] = pt * u01;
+                        const double b2 = pt * u1;
+                        base[2 * 128] = b2;
+                        base[3 * 128] = b2 * u0;
                         if (m >= 3) {
                             const double u2 = sm.U[(l + e2) * 128 + TL];
-                            base[4 * 128] = pt * u2;
-                            base[5 * 128] = pt * (u0 * u2);
-                            base[6 * 128] = pt * (u1 * u2);
-                            base[7 * 128] = pt * (u01 * u2);
+                            const double b4 = pt * u2, b6 = b4 * u1;
+                            base[4 * 128] = b4;
+                            base[5 * 128] = b4 * u0;
+                            base[6 * 128] = b6;
+                            base[7 * 128] = b6 * u0;
                         }
                     }
                 }
@@ -458,7 +474,7 @@ __global__ void __launch_bounds__(kPpmWarps * 32, 3) ppm_kernel(const double *__
                             const int2 w = cur[k];
                             const int dst = w.x & 0xffff, src = (w.x >> 16) & 0xffff;
                             const int el = w.y & 0xff, TL = w.y >> 8;
-                            sm.Bp[dst] = d == 0 ? tree_prod<7>(sm.U, 0, TL, TL) : sm.Bp[src] * sm.U[el * 128 + TL];
+                            sm.Bp[dst] = d == 0 ? set_prod(sm.U, 0, TL, TL) : sm.Bp[src] * sm.U[el * 128 + TL];
                         }
                     }
                     __syncwarp();
