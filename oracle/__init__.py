@@ -63,6 +63,8 @@ def _load():
                 "oracle_cdet_partition": [P, i32, i64, P, i32],
                 "oracle_keldysh": [P, i32, i64, i32, P, P, i32],
                 "oracle_keldysh_scale": [P, i32, i64, i32, P, i32],
+                "oracle_xnor_minors": [P, i32, i64, P, i32],
+                "oracle_xnor_scale": [P, i32, i64, i32, P, i32],
             }.items():
                 f = getattr(lib, name)
                 f.argtypes = args
@@ -195,4 +197,35 @@ def keldysh_scale(Mt, use_perm: bool | None = None, nthreads: int = 0) -> np.nda
         use_perm = n <= 10
     out = np.empty(b)
     _load().oracle_keldysh_scale(Mt.ctypes.data, n, b, int(use_perm), out.ctypes.data, nthreads)
+    return out[0] if single else out
+
+
+def _xnor_batch(M):
+    M = np.ascontiguousarray(M, dtype=np.float64)
+    single = M.ndim == 2
+    if single:
+        M = M[None]
+    assert M.ndim == 3 and M.shape[1] == M.shape[2] and M.shape[1] % 2 == 0, M.shape
+    n = M.shape[1] // 2
+    assert 1 <= n <= 16, n
+    return M, single, n
+
+
+def xnor_minors(M, nthreads: int = 0) -> np.ndarray:
+    """All 2^n XNOR principal minors of 2n x 2n matrices (Section III.B): out[S]
+    is the determinant of the rows and columns 2i, 2i+1 of every i in S."""
+    M, single, n = _xnor_batch(M)
+    out = np.empty((M.shape[0], 1 << n))
+    _load().oracle_xnor_minors(M.ctypes.data, n, M.shape[0], out.ctypes.data, nthreads)
+    return out[0] if single else out
+
+
+def xnor_scale(M, use_perm: bool | None = None, nthreads: int = 0) -> np.ndarray:
+    """Rounding scale of each XNOR minor: perm(|M[S]|) of the 2|S| x 2|S|
+    submatrix (n <= 8 by default), else prod_r sum_q |M_rq| over it."""
+    M, single, n = _xnor_batch(M)
+    if use_perm is None:
+        use_perm = n <= 8
+    out = np.empty((M.shape[0], 1 << n))
+    _load().oracle_xnor_scale(M.ctypes.data, n, M.shape[0], int(use_perm), out.ctypes.data, nthreads)
     return out[0] if single else out

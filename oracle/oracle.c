@@ -17,7 +17,11 @@
  *                        Moebius formula c[S] = sum_pi (-1)^{|pi|-1}(|pi|-1)!
  *                        prod_{B in pi} a[B];
  *   - Keldysh sums:      the sum over all 2^n Keldysh index assignments of a
- *                        separate complex determinant each (Section V.D).
+ *                        separate complex determinant each (Section V.D);
+ *   - XNOR minors:       for a 2n x 2n matrix of 2 x 2 blocks, the determinant
+ *                        of every submatrix keeping both rows and columns of
+ *                        a subset of the blocks (Section III.B, the minors of
+ *                        the Nambu CDet of Section V.B), one elimination each.
  *
  * Subsets are bit masks: element k (0-based) <-> bit k (Section II, the
  * subset labelling S_i by the binary digits of i). Matrices are row-major.
@@ -357,5 +361,81 @@ void oracle_keldysh_scale(const double *Mt, int n, int64_t batch, int use_perm, 
             }
         }
         scale[b] = acc;
+    }
+}
+
+/* All 2^n XNOR principal minors of each 2n x 2n matrix M (Section III.B): for
+ * every vertex subset S, the determinant of the submatrix that keeps both rows
+ * and both columns 2i, 2i+1 of each vertex i in S and none of the others, each
+ * by its own partial-pivot elimination; minors[0] = 1. n <= 16. */
+void oracle_xnor_minors(const double *M, int n, int64_t batch, double *minors, int nthreads) {
+    const int m = 2 * n;
+    const int64_t N = (int64_t)1 << n;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(threads_for(nthreads))
+    for (int64_t b = 0; b < batch; ++b) {
+        const double *Mb = M + b * (int64_t)m * m;
+        double *out = minors + b * N;
+        double sub[32 * 32];
+        int idx[32];
+        for (int64_t S = 0; S < N; ++S) {
+            int k = 0;
+            for (int v = 0; v < n; ++v)
+                if ((S >> v) & 1) {
+                    idx[k++] = 2 * v;
+                    idx[k++] = 2 * v + 1;
+                }
+            for (int r = 0; r < k; ++r)
+                for (int q = 0; q < k; ++q) sub[r * k + q] = Mb[idx[r] * m + idx[q]];
+            out[S] = det_partial_pivot(sub, k);
+        }
+    }
+}
+
+/* Rounding scale of each XNOR minor: perm(|M[S]|) of its 2|S| x 2|S| submatrix
+ * (the sum of the absolute values of all Leibniz terms, by Ryser on the
+ * absolute values) when use_perm != 0, else the bound prod_r sum_q |M_rq| over
+ * the submatrix. scale[0] = 1. */
+void oracle_xnor_scale(const double *M, int n, int64_t batch, int use_perm, double *scale, int nthreads) {
+    const int m = 2 * n;
+    const int64_t N = (int64_t)1 << n;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(threads_for(nthreads))
+    for (int64_t b = 0; b < batch; ++b) {
+        const double *Mb = M + b * (int64_t)m * m;
+        double *out = scale + b * N;
+        double sub[32 * 32];
+        int idx[32];
+        for (int64_t S = 0; S < N; ++S) {
+            int k = 0;
+            for (int v = 0; v < n; ++v)
+                if ((S >> v) & 1) {
+                    idx[k++] = 2 * v;
+                    idx[k++] = 2 * v + 1;
+                }
+            for (int r = 0; r < k; ++r)
+                for (int q = 0; q < k; ++q) sub[r * k + q] = fabs(Mb[idx[r] * m + idx[q]]);
+            double acc;
+            if (use_perm) {
+                double total = 0.0;
+                for (int64_t T = 0; T < ((int64_t)1 << k); ++T) {
+                    double prod = 1.0;
+                    for (int r = 0; r < k; ++r) {
+                        double rs = 0.0;
+                        for (int q = 0; q < k; ++q)
+                            if ((T >> q) & 1) rs += sub[r * k + q];
+                        prod *= rs;
+                    }
+                    total += (popcount_u32((uint32_t)T) & 1) ? -prod : prod;
+                }
+                acc = (k & 1) ? -total : total;
+            } else {
+                acc = 1.0;
+                for (int r = 0; r < k; ++r) {
+                    double rs = 0.0;
+                    for (int q = 0; q < k; ++q) rs += sub[r * k + q];
+                    acc *= rs;
+                }
+            }
+            out[S] = acc;
+        }
     }
 }

@@ -253,3 +253,73 @@ def keldysh_varlen(orders: np.ndarray, seed: int = 3):
         for k, b in enumerate(sel):
             flat[off[b]:off[b + 1]] = M[k].ravel()
     return flat, off[:-1].copy()
+
+
+# --- Nambu (BCS) matrices for the XNOR minors / Nambu CDet -------------------
+NAMBU_DELTA = 0.3
+NAMBU_MTAU = 1 << 12
+
+
+def nambu_g0_table(t: float = HUB_T, mu: float = HUB_MU, beta: float = HUB_BETA, delta: float = NAMBU_DELTA,
+                   nk: int = HUB_NK, win: int = HUB_WIN, mtau: int = NAMBU_MTAU):
+    """Bare Nambu propagator of the 2D square-lattice attractive Hubbard model at
+    the BCS mean field, for |rx|,|ry| < win and tau = d*beta/mtau.
+
+    Nambu spinor psi_k = (c_k,up, c^+_-k,down), h_k = [[xi, delta], [delta, -xi]],
+    E = sqrt(xi^2 + delta^2), projectors P+- = (1 +- h/E)/2. With
+    G(k,tau) = -<T psi_k(tau) psi_k^+(0)>:
+      0 < tau < beta : G = -(P+ e^{-E tau} + P- e^{-E(beta-tau)}) / (1 + e^{-beta E})
+     -beta < tau < 0 : G(k,tau) = -G(k,tau+beta)
+      tau = 0        : the 0^- limit, G = n_F(h_k).
+    Real space: G(r,tau) = (1/N) sum_k cos(k.r) G(k,tau) (real). Every
+    exponential has a non-positive argument. Returns (win, win, 2*mtau-1, 2, 2).
+    """
+    half = np.arange(nk // 2 + 1)
+    w1 = np.where((half == 0) | (half == nk // 2), 1.0, 2.0)
+    k1 = 2.0 * np.pi * half / nk
+    kx, ky = np.meshgrid(k1, k1, indexing="ij")
+    wk = np.outer(w1, w1).ravel()
+    xi = (-2.0 * t * (np.cos(kx) + np.cos(ky)) - mu).ravel()
+    E = np.sqrt(xi * xi + delta * delta)
+    r = np.arange(win)
+    cosx = np.cos(np.outer(r, k1))
+    W = (cosx[:, None, :, None] * cosx[None, :, None, :]).reshape(win * win, -1)
+    W = W * wk[None, :] / float(nk * nk)                                # (win^2, K)
+    d = np.arange(-(mtau - 1), mtau)
+    tau = d * (beta / mtau)
+    # s in (0, beta]: tau > 0 -> s = tau with sign -1; tau <= 0 -> s = tau + beta with sign +1
+    # (tau = 0 is the 0^- limit: s = beta)
+    s = np.where(tau > 0, tau, tau + beta)[None, :]
+    sgn = np.where(tau > 0, -1.0, 1.0)[None, :]
+    Ec = E[:, None]
+    den = 1.0 + np.exp(-beta * Ec)
+    ep = np.exp(-Ec * s) / den                  # weight of P+
+    em = np.exp(-Ec * (beta - s)) / den         # weight of P-
+    u2 = (0.5 * (1.0 + xi / E))[:, None]
+    v2 = (0.5 * (1.0 - xi / E))[:, None]
+    g = (0.5 * delta / E)[:, None]
+    G = np.empty((win * win, d.size, 2, 2))
+    G[:, :, 0, 0] = sgn * (W @ (u2 * ep + v2 * em))
+    G[:, :, 1, 1] = sgn * (W @ (v2 * ep + u2 * em))
+    G[:, :, 0, 1] = sgn * (W @ (g * (ep - em)))
+    G[:, :, 1, 0] = G[:, :, 0, 1]
+    return G.reshape(win, win, d.size, 2, 2)
+
+
+def nambu_matrices_from_vertices(x, y, m, mtau: int = NAMBU_MTAU) -> np.ndarray:
+    """2n x 2n matrices of 2 x 2 blocks: block (i, j) at rows 2i, 2i+1 and
+    columns 2j, 2j+1 is G(r_i - r_j, tau_i - tau_j); diagonal blocks G(0, 0^-)."""
+    G = nambu_g0_table(mtau=mtau)
+    b, n = x.shape
+    dx = np.abs(x[:, :, None] - x[:, None, :])
+    dy = np.abs(y[:, :, None] - y[:, None, :])
+    dt = m[:, :, None] - m[:, None, :] + (mtau - 1)
+    blocks = G[dx, dy, dt]                                              # (b, n, n, 2, 2)
+    return np.ascontiguousarray(blocks.transpose(0, 1, 3, 2, 4).reshape(b, 2 * n, 2 * n))
+
+
+def nambu_batch(batch: int = 65536, n: int = 12, seed: int = 6) -> np.ndarray:
+    """Nambu G0 matrices, shape (batch, 2n, 2n), float64 (vertices as for the
+    Hubbard batches: sites on the 8 x 8 window, distinct times on the grid)."""
+    x, y, m = hubbard_vertices(batch, n, seed, mtau=NAMBU_MTAU)
+    return nambu_matrices_from_vertices(x, y, m)

@@ -378,3 +378,90 @@ def test_inputs_shapes_and_conventions():
     assert P.shape == (3, 14, 14) and np.all(P >= 0) and np.allclose(P != 0, (P != 0).transpose(0, 2, 1))
     M = I.keldysh_batch(2, 5)
     assert M.shape == (2, 10, 10) and M.dtype == np.complex128
+
+
+# --- XNOR minors (Section III.B) and the Nambu CDet weights (Section V.B) ----
+
+def _xnor_idx(S, n):
+    return [2 * v + e for v in range(n) if (S >> v) & 1 for e in (0, 1)]
+
+
+def test_xnor_minors_match_numpy_determinants():
+    """Each XNOR minor is the determinant of the rows and columns 2i, 2i+1 of
+    the vertices in S (numpy's LAPACK determinant as the independent check)."""
+    rng = np.random.default_rng(2001)
+    for n in (1, 3, 5):
+        M = rng.standard_normal((3, 2 * n, 2 * n)) + 1.5 * np.eye(2 * n)
+        x = oracle.xnor_minors(M)
+        for b in range(3):
+            assert x[b, 0] == 1.0
+            for S in range(1, 1 << n):
+                idx = _xnor_idx(S, n)
+                ref = np.linalg.det(M[b][np.ix_(idx, idx)])
+                assert abs(x[b, S] - ref) <= 1e-12 * max(1.0, abs(ref)), (n, S)
+
+
+def test_xnor_block_diagonal_closed_form():
+    """Only diagonal 2 x 2 blocks: every XNOR minor is the product of the block
+    determinants of its vertices."""
+    rng = np.random.default_rng(2002)
+    n = 6
+    B = rng.standard_normal((n, 2, 2))
+    M = np.zeros((2 * n, 2 * n))
+    for i in range(n):
+        M[2 * i:2 * i + 2, 2 * i:2 * i + 2] = B[i]
+    d = B[:, 0, 0] * B[:, 1, 1] - B[:, 0, 1] * B[:, 1, 0]
+    x = oracle.xnor_minors(M)
+    for S in range(1 << n):
+        ref = np.prod([d[v] for v in range(n) if (S >> v) & 1])
+        assert abs(x[S] - ref) <= 1e-13 * max(1.0, abs(ref))
+
+
+def test_xnor_without_pairing_factorises():
+    """Delta = 0: the Nambu matrix has no particle-hole mixing, so the XNOR
+    minor is det G_00[S] * det G_11[S] (the rows and columns of each component
+    reordered together, no sign)."""
+    G = I.nambu_g0_table(delta=0.0)
+    x_, y_, m_ = I.hubbard_vertices(2, 7, seed=2003, mtau=I.NAMBU_MTAU)
+    dx = np.abs(x_[:, :, None] - x_[:, None, :])
+    dy = np.abs(y_[:, :, None] - y_[:, None, :])
+    dt = m_[:, :, None] - m_[:, None, :] + (I.NAMBU_MTAU - 1)
+    blocks = G[dx, dy, dt]
+    assert np.all(blocks[..., 0, 1] == 0.0)
+    M = blocks.transpose(0, 1, 3, 2, 4).reshape(2, 14, 14)
+    x = oracle.xnor_minors(M)
+    for b in range(2):
+        for S in range(1, 1 << 7):
+            idx = [v for v in range(7) if (S >> v) & 1]
+            ref = (np.linalg.det(blocks[b, :, :, 0, 0][np.ix_(idx, idx)])
+                   * np.linalg.det(blocks[b, :, :, 1, 1][np.ix_(idx, idx)]))
+            assert abs(x[b, S] - ref) <= 1e-12 * max(1e-3, abs(ref))
+
+
+def test_xnor_leibniz_order_2():
+    """n = 2: the full 4 x 4 minor as the Leibniz sum over all 24 permutations."""
+    import itertools
+    rng = np.random.default_rng(2004)
+    M = rng.standard_normal((4, 4))
+    total = 0.0
+    for p in itertools.permutations(range(4)):
+        sgn = 1
+        for i in range(4):
+            for j in range(i + 1, 4):
+                if p[i] > p[j]:
+                    sgn = -sgn
+        total += sgn * np.prod([M[i, p[i]] for i in range(4)])
+    x = oracle.xnor_minors(M)
+    assert abs(x[3] - total) <= 1e-13 * max(1.0, abs(total))
+    assert abs(x[1] - (M[0, 0] * M[1, 1] - M[0, 1] * M[1, 0])) <= 1e-15
+
+
+def test_xnor_scale_bounds():
+    rng = np.random.default_rng(2005)
+    M = rng.standard_normal((2, 10, 10))
+    x = oracle.xnor_minors(M)
+    sp = oracle.xnor_scale(M, use_perm=True)
+    sb = oracle.xnor_scale(M, use_perm=False)
+    assert np.all(np.abs(x) <= sp * (1 + 1e-12))
+    assert np.all(sp <= sb * (1 + 1e-12))
+    assert np.all(sp[:, 0] == 1.0)
