@@ -67,6 +67,7 @@ typedef enum {
 #define APM_MAX_N_MINORS   16
 #define APM_MAX_N_KELDYSH  16
 #define APM_MAX_N_PERM     16
+#define APM_MAX_N_XNOR     16
 
 /*
  * Pivot correction (Section II, the paragraph after Eq. minor and Alg. 1): when
@@ -135,6 +136,37 @@ apm_status_t apm_cdet_connected(const double *A_up, const double *A_dn, int n, i
  */
 apm_status_t apm_cdet_from_weights(const double *a, int n, int64_t batch, double *c,
                                    void *workspace, size_t workspace_bytes, apm_stream_t stream);
+
+/*
+ * apm_xnor_minors -- all 2^n XNOR principal minors of 2n x 2n matrices made of
+ * 2 x 2 blocks (Section III.B): minors[S] = det of the submatrix that keeps both
+ * rows and both columns 2i, 2i+1 of every vertex i in S and none of the others;
+ * minors[0] = 1. Binary tree of Schur complements with respect to 2 x 2 pivot
+ * blocks, O(2^n); no pivot correction is possible (Section III.B).
+ *   M        [batch][2n][2n] float64, row-major; block (i, j) at rows 2i, 2i+1
+ *            and columns 2j, 2j+1.
+ *   n        1..APM_MAX_N_XNOR.
+ *   minors   [batch][2^n] float64 output.
+ *   status   [batch] or NULL; APM_ST_ZERO_PIVOT marks a singular or non-finite
+ *            2 x 2 pivot block met on the way, APM_ST_NONFINITE_INPUT a NaN or
+ *            infinity in the input; either makes that matrix's row NaN.
+ *   workspace / workspace_bytes: scratch for the depth-first part of the tree,
+ *            needed for n > 8 (apm_workspace_size with APM_OP_XNOR_MINORS).
+ */
+apm_status_t apm_xnor_minors(const double *M, int n, int64_t batch, double *minors, uint32_t *status,
+                             void *workspace, size_t workspace_bytes, apm_stream_t stream);
+
+/*
+ * apm_nambu_cdet -- the CDet connected sums for expansions around BCS theory
+ * (Section V.B): the weights a[S] are the XNOR minors of the 2n x 2n Nambu
+ * matrix (apm_xnor_minors, written to minors), and c[S] follows from them by
+ * the CDet recursion (Eq. recursion), exactly as apm_cdet_from_weights.
+ *   minors   [batch][2^n] float64 output (the weights), c [batch][2^n] output.
+ *   Other arguments as for apm_xnor_minors; the workspace size is
+ *   apm_workspace_size with APM_OP_NAMBU_CDET (zero for n <= 8).
+ */
+apm_status_t apm_nambu_cdet(const double *M, int n, int64_t batch, double *minors, double *c, uint32_t *status,
+                            void *workspace, size_t workspace_bytes, apm_stream_t stream);
 
 /* flags for apm_keldysh_sum and apm_keldysh_sum_noalloc */
 #define APM_KELDYSH_SIGNED 0x1 /* weight each assignment by (-1)^{number of - indices} */
@@ -212,6 +244,8 @@ apm_status_t apm_perm_minors(const double *A, int n, int64_t batch, double *perm
 #define APM_OP_CDET_VARLEN 5
 #define APM_OP_KELDYSH 6
 #define APM_OP_KELDYSH_VARLEN 7
+#define APM_OP_XNOR_MINORS 8
+#define APM_OP_NAMBU_CDET 9
 
 /*
  * apm_cdet_connected_varlen -- apm_cdet_connected for a batch of matrices of

@@ -25,7 +25,7 @@ ST_PIVOT_CORRECTED, ST_NONFINITE_INPUT, ST_ZERO_PIVOT, ST_CORRECTION_OVERFLOW = 
 CDET_SINGLE_DET = 1
 KELDYSH_SIGNED = 1
 OP_ALL_MINORS, OP_CDET, OP_CDET_FROM_WEIGHTS, OP_PERM_MINORS, OP_CDET_VARLEN, OP_KELDYSH, \
-    OP_KELDYSH_VARLEN = 1, 2, 3, 4, 5, 6, 7
+    OP_KELDYSH_VARLEN, OP_XNOR_MINORS, OP_NAMBU_CDET = 1, 2, 3, 4, 5, 6, 7, 8, 9
 ST_BAD_ORDER = 16
 
 
@@ -65,6 +65,8 @@ def lib():
                 "apm_keldysh_sum_noalloc": [P, i32, i64, i32, P, P, P, P],
                 "apm_cdet_connected_varlen": [P, P, P, P, i64, i32, i32, P, P, P, OPT, P, P, sz, P],
                 "apm_keldysh_sum_varlen": [P, P, P, i64, i32, i32, P, P, P, P, sz, P],
+                "apm_xnor_minors": [P, i32, i64, P, P, P, sz, P],
+                "apm_nambu_cdet": [P, i32, i64, P, P, P, P, sz, P],
                 "apm_cdet_tune_set": [P],
                 "apm_cdet_tune_get": [i32, ctypes.POINTER(ctypes.c_uint64)],
                 "apm_workspace_size": [i32, i32, i64, i32, ctypes.POINTER(sz)],
@@ -220,6 +222,45 @@ def keldysh_sum(Mt: torch.Tensor, signed=False, partial=False, return_status=Fal
     res = [torch.view_as_complex(s)]
     if partial:
         res.append(torch.view_as_complex(p))
+    if return_status:
+        res.append(st)
+    return res[0] if len(res) == 1 else tuple(res)
+
+
+def _nambu_batch(M: torch.Tensor):
+    M = _mat_batch(M, torch.float64, "M")
+    b, n2, _ = M.shape
+    if n2 % 2:
+        raise ValueError("M must be 2n x 2n")
+    return M, b, n2 // 2
+
+
+def xnor_minors(M: torch.Tensor, return_status=False):
+    """All 2^n XNOR principal minors (apm_xnor_minors); M (batch, 2n, 2n) float64."""
+    M, b, n = _nambu_batch(M)
+    dev = M.device
+    out = torch.empty((b, 1 << n), dtype=torch.float64, device=dev)
+    st = torch.zeros(b, dtype=torch.int32, device=dev) if return_status else None
+    ws, nb = _workspace(OP_XNOR_MINORS, n, b, dev)
+    _check(lib().apm_xnor_minors(_ptr(M), n, b, _ptr(out), _ptr(st), _ptr(ws), nb, _stream(M)),
+           "apm_xnor_minors")
+    return (out, st) if return_status else out
+
+
+def nambu_cdet(M: torch.Tensor, return_minors=False, return_status=False):
+    """Connected sums c[S] of the Nambu CDet (apm_nambu_cdet): weights = XNOR
+    minors of M (batch, 2n, 2n) float64, then the CDet recursion."""
+    M, b, n = _nambu_batch(M)
+    dev = M.device
+    minors = torch.empty((b, 1 << n), dtype=torch.float64, device=dev)
+    c = torch.empty((b, 1 << n), dtype=torch.float64, device=dev)
+    st = torch.zeros(b, dtype=torch.int32, device=dev) if return_status else None
+    ws, nb = _workspace(OP_NAMBU_CDET, n, b, dev)
+    _check(lib().apm_nambu_cdet(_ptr(M), n, b, _ptr(minors), _ptr(c), _ptr(st), _ptr(ws), nb, _stream(M)),
+           "apm_nambu_cdet")
+    res = [c]
+    if return_minors:
+        res.append(minors)
     if return_status:
         res.append(st)
     return res[0] if len(res) == 1 else tuple(res)

@@ -8,6 +8,24 @@
 
 namespace apm {
 
+// 1/d. Where d and 1/d are normal numbers (biased exponent of |d| in 3..2044):
+// the hardware approximation (rcp.approx.ftz.f64, relative error far below
+// 2^-14) refined by two Newton-Raphson steps x <- x + x(1 - d x), each of which
+// squares the relative error, so the result is within a few units in the last
+// place. Elsewhere (zero, subnormal, huge, inf, NaN): the IEEE division.
+__device__ __forceinline__ double rcp_nr(double d) {
+    const unsigned ex = (static_cast<unsigned>(__double2hiint(d)) >> 20) & 0x7ffu;
+    if (ex - 3u < 2042u) {
+        double x;
+        asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(x) : "d"(d));
+        double e = fma(-d, x, 1.0);
+        x = fma(x, e, x);
+        e = fma(-d, x, 1.0);
+        return fma(x, e, x);
+    }
+    return 1.0 / d;
+}
+
 // Threads per CTA of the minor / connected-sum kernels.
 constexpr int kCdetThreads = 256;
 // Capacity of the per-matrix pivot-correction log.
@@ -68,6 +86,12 @@ int keldysh_warps_per_block();
 size_t keldysh_stack_entries(int n);
 
 int launch_ppm(const double *A, int n, int64_t batch, double *perms, cudaStream_t s);
+
+// XNOR minors of 2n x 2n block matrices (one warp per matrix).
+int xnor_grid(int64_t batch, int *err);
+size_t xnor_workspace_bytes(int n, int64_t batch, int *err);
+int launch_xnor(const double *M, int n, int64_t batch, double *minors, uint32_t *status, void *workspace,
+                cudaStream_t s);
 
 // uneven batches
 unsigned long long cdet_gsel_packed(int n);

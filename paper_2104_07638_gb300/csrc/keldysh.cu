@@ -106,23 +106,6 @@ __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_doub
 __device__ __forceinline__ double2 cneg_if(double2 a, bool neg) {
     return neg ? make_double2(-a.x, -a.y) : a;
 }
-// 1/d for d >= 0. Where d and 1/d are normal numbers (biased exponent of d in
-// 3..2044): the hardware approximation (rcp.approx.ftz.f64, relative error far
-// below 2^-14) refined by two Newton-Raphson steps x <- x + x(1 - d x), each of
-// which squares the relative error, so the result is within a few units in the
-// last place. Elsewhere (zero, subnormal, huge, inf, NaN): the IEEE division.
-__device__ __forceinline__ double rcp_nr(double d) {
-    const unsigned ex = (static_cast<unsigned>(__double2hiint(d)) >> 20) & 0x7ffu;
-    if (ex - 3u < 2042u) {
-        double x;
-        asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(x) : "d"(d));
-        double e = fma(-d, x, 1.0);
-        x = fma(x, e, x);
-        e = fma(-d, x, 1.0);
-        return fma(x, e, x);
-    }
-    return 1.0 / d;
-}
 // 1/p; flags a zero or non-finite pivot (|p|^2 == 0, inf or NaN), tested on
 // the bits so that no FP64 compare is issued
 __device__ __forceinline__ double2 crcp(double2 p, int &bad) {

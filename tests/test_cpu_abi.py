@@ -77,3 +77,23 @@ def test_tune_tables_host_side(lib):
     bad[4] = 3 << (3 * 2)           # layer k = 2 allows r <= 1
     assert lib.apm_cdet_tune_set(ctypes.cast(bad, P)) == 1
     assert lib.apm_cdet_tune_set(None) == 0
+
+
+def test_xnor_and_nambu_argument_errors(lib):
+    P, i32, i64, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_size_t
+    fake = ctypes.c_void_p(1 << 20)           # never dereferenced: the call must fail first
+    x = lib.apm_xnor_minors
+    x.argtypes = [P, i32, i64, P, P, P, sz, P]
+    x.restype = ctypes.c_int
+    assert x(fake, 0, 1, fake, None, None, 0, None) == 2            # n out of range
+    assert x(fake, 17, 1, fake, None, None, 0, None) == 2
+    assert x(fake, 6, -1, fake, None, None, 0, None) == 1           # negative batch
+    assert x(None, 6, 1, fake, None, None, 0, None) == 1            # null input
+    assert x(fake, 6, 1, ctypes.c_void_p((1 << 20) + 8), None, None, 0, None) == 1  # misaligned output
+    assert x(None, 6, 0, None, None, None, 0, None) == 0            # empty batch: no launch
+    nb = lib.apm_nambu_cdet
+    nb.argtypes = [P, i32, i64, P, P, P, P, sz, P]
+    nb.restype = ctypes.c_int
+    assert nb(fake, 17, 1, fake, fake, None, None, 0, None) == 2
+    assert nb(fake, 6, 1, fake, None, None, None, 0, None) == 1     # null c
+    assert nb(None, 6, 0, None, None, None, None, 0, None) == 0
