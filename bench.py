@@ -89,7 +89,7 @@ def parse():
                     help="skip the per-row measurements of the other hot-path steps")
     ap.add_argument("--mc-steps", type=int, default=100)
     ap.add_argument("--case", default=None,
-                    choices=["cdet_n12", "cdet_n16", "keldysh_n12", "ppm_n14", "cdet_uneven"],
+                    choices=["cdet_n12", "cdet_n16", "keldysh_n12", "ppm_n14", "cdet_uneven", "xnor_n12"],
                     help="run 3 launches of one kernel on a small case (for profiling) and exit")
     return ap.parse_args()
 
@@ -158,6 +158,19 @@ def keldysh_flops(n: int) -> int:
             + 12 * (2 ** (n + 1) - 2) + 2 * 2 ** n)
 
 
+def xnor_flops(n: int) -> int:
+    """Algorithmic flops of all XNOR minors of a 2n x 2n matrix: per tree node with
+    a kept child of size m2 = 2(n-l-1), the Schur update (4 m2^2), the row factors
+    C P^-1 (6 m2) and the pivot determinant, inverse and node product (9)."""
+    return sum((1 << l) * (4 * (2 * (n - l - 1)) ** 2 + 12 * (n - l - 1) + 9) for l in range(n))
+
+
+def sc_flops(n: int) -> int:
+    """Flops of the CDet recursion alone: one FMA per (T, S) pair with the
+    lowest element of S in T, T a proper non-empty subset."""
+    return 2 * ((3 ** n - 1) // 2 - (2 ** n - 1))
+
+
 def perm_flops(n: int) -> int:
     """Algorithmic flops of all permanent minors: one product and one addition
     per (T subset of S) pair, plus the row sums."""
@@ -217,6 +230,19 @@ def measure_rows(args, dev, peak):
         "value": 4096 / (ms * 1e-3), "unit": "perm-minor-sets/s", "ms": ms,
         "tflops": fl / (ms * 1e-3) / 1e12, "frac_fp64_peak": fl / (ms * 1e-3) / 1e12 / peak}
     del P
+    # next (Sections III.B, V.B): Nambu CDet, 65536 BCS Nambu matrices of order 12:
+    # XNOR minors of the 24 x 24 matrices, then the CDet recursion on them
+    M = torch.as_tensor(inputs.nambu_batch(65536, 12, seed=6)).to(dev)
+    ms = _event_ms(lambda: apm.nambu_cdet(M))
+    xm = apm.xnor_minors(M)
+    ms_x = _event_ms(lambda: apm.xnor_minors(M))
+    fl = 65536 * (xnor_flops(12) + sc_flops(12))
+    rows["nambu_cdet_65536_n12"] = {
+        "value": 65536 / (ms * 1e-3), "unit": "minor-sets/s", "ms": ms,
+        "tflops": fl / (ms * 1e-3) / 1e12, "frac_fp64_peak": fl / (ms * 1e-3) / 1e12 / peak,
+        "xnor_minors_ms": ms_x, "xnor_minors_tflops": 65536 * xnor_flops(12) / (ms_x * 1e-3) / 1e12,
+        "launch": "XNOR-minor kernel, then the CDet recursion on the minors"}
+    del M, xm
     # a8: learned proposal vs plain, 16384 walkers at each order 10..14
     G = torch.as_tensor(inputs.hubbard_g0_table()).to(dev)
     W, T = 16384, args.mc_steps
@@ -337,6 +363,9 @@ def profile_case(name: str):
     elif name == "keldysh_n12":
         M = torch.as_tensor(inputs.keldysh_batch(8192, 12, seed=3)).to(dev)
         run = lambda: apm.keldysh_sum(M)
+    elif name == "xnor_n12":
+        M = torch.as_tensor(inputs.nambu_batch(8192, 12, seed=6)).to(dev)
+        run = lambda: apm.xnor_minors(M)
     elif name == "ppm_n14":
         P = torch.as_tensor(inputs.perm_batch(14, 1368, seed=4)).to(dev)
         run = lambda: apm.perm_minors(P)

@@ -151,7 +151,7 @@ apm_status_t apm_cdet_from_weights(const double *a, int n, int64_t batch, double
  *            2 x 2 pivot block met on the way, APM_ST_NONFINITE_INPUT a NaN or
  *            infinity in the input; either makes that matrix's row NaN.
  *   workspace / workspace_bytes: scratch for the depth-first part of the tree,
- *            needed for n > 8 (apm_workspace_size with APM_OP_XNOR_MINORS).
+ *            needed for n > 9 (apm_workspace_size with APM_OP_XNOR_MINORS).
  */
 apm_status_t apm_xnor_minors(const double *M, int n, int64_t batch, double *minors, uint32_t *status,
                              void *workspace, size_t workspace_bytes, apm_stream_t stream);
@@ -163,7 +163,7 @@ apm_status_t apm_xnor_minors(const double *M, int n, int64_t batch, double *mino
  * the CDet recursion (Eq. recursion), exactly as apm_cdet_from_weights.
  *   minors   [batch][2^n] float64 output (the weights), c [batch][2^n] output.
  *   Other arguments as for apm_xnor_minors; the workspace size is
- *   apm_workspace_size with APM_OP_NAMBU_CDET (zero for n <= 8).
+ *   apm_workspace_size with APM_OP_NAMBU_CDET (zero for n <= 9).
  */
 apm_status_t apm_nambu_cdet(const double *M, int n, int64_t batch, double *minors, double *c, uint32_t *status,
                             void *workspace, size_t workspace_bytes, apm_stream_t stream);

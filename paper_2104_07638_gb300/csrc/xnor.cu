@@ -15,13 +15,16 @@
 // Mapping: one warp per matrix. The vertices are eliminated from the last one
 // down, so that every node matrix is the leading block of its vertices and
 // dropping a vertex is only a smaller view of the same rows (no copy). The
-// upper vertices s..n-1 (s = min(n, 7)) are walked depth first (the matrices
+// upper vertices s..n-1 (s = min(n, 8)) are walked depth first (the matrices
 // of kept pivots on a per-warp stack in caller scratch, L2-resident); the last
 // s vertices are expanded breadth first in shared memory, and the 4 x 4 nodes
 // of the last two vertices are finished in closed form, one node per lane,
 // each lane writing the four minors of its node as two 16-byte stores (the
 // tail vertices are the low mask bits, so the writes of a warp are
-// contiguous).
+// contiguous). An FP64 warp instruction costs the same pipe time whatever the
+// number of active lanes, so the tail is sized to share each level's pivot
+// inversions among many nodes: 8 vertices (2 to 32 nodes per level, 21 KB of
+// shared memory per warp) measured 0.77 TFLOP/s at n = 12 against 0.70 for 7.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -29,11 +32,17 @@
 
 namespace apm {
 
-constexpr int kXnTail = 7;   // vertices expanded breadth first
-constexpr int kXnWarps = 4;  // warps per CTA
+// vertices expanded breadth first (S) and warps per CTA
+#ifndef APM_XN_TAIL
+#define APM_XN_TAIL 8
+#endif
+constexpr int kXnTail = APM_XN_TAIL;
+static_assert(kXnTail == 7 || kXnTail == 8, "tail of 7 or 8 vertices");
+constexpr int kXnWarps = kXnTail == 7 ? 4 : 2;
 
 // Tail level J (J = 0..S-2) holds 2^J nodes of size 2(S-J); even levels in
 // bufE, odd levels in bufO. S = 7: bufE 196, 400, 576; bufO 288, 512, 512.
+// S = 8: bufE 256, 576, 1024, 1024; bufO 392, 800, 1152.
 __host__ __device__ constexpr int xn_level_entries(int S, int J) {
     return (1 << J) * (2 * (S - J)) * (2 * (S - J));
 }
@@ -42,23 +51,32 @@ __host__ __device__ constexpr int xn_buf_entries(int S, int parity) {
     for (int J = parity; J <= S - 2; J += 2) b = b > xn_level_entries(S, J) ? b : xn_level_entries(S, J);
     return b;
 }
+// row factors of one level: 2 per row of every kept child (2^J x 2(S-J-1)), or
+// of one depth-first step (at most 2 x 30)
+__host__ __device__ constexpr int xn_fac_entries(int S) {
+    int b = 60;
+    for (int J = 0; J <= S - 3; ++J) b = b > (2 << J) * (2 * (S - J - 1)) ? b : (2 << J) * (2 * (S - J - 1));
+    return b;
+}
 constexpr int kXnBufE = xn_buf_entries(kXnTail, 0);
 constexpr int kXnBufO = xn_buf_entries(kXnTail, 1);
-static_assert(kXnBufE == 576 && kXnBufO == 512, "7-vertex tail");
+constexpr int kXnFac = xn_fac_entries(kXnTail);
+static_assert(kXnTail != 7 || (kXnBufE == 576 && kXnBufO == 512 && kXnFac == 128), "7-vertex tail");
+static_assert(kXnTail != 8 || (kXnBufE == 1024 && kXnBufO == 1152 && kXnFac == 256), "8-vertex tail");
 constexpr int kXnMaxN = 16;
 
 struct XnWarpSmem {
     double bufE[kXnBufE];
     double bufO[kXnBufO];
-    double F[128];        // row factors C P^-1: 2 per row of every kept child at one level (<= 16 x 4 x 2)
-    double pinv[16][4];   // inverse pivot block of every node of one level
-    double nd[2][32];     // node determinants of the current and the next level
+    double F[kXnFac];                  // row factors C P^-1 of one level or depth-first step
+    double pinv[1 << (kXnTail - 3)][4];  // inverse pivot block of every node of one level
+    double nd[2][1 << (kXnTail - 2)];    // node determinants of the current and the next level
     double pdet[kXnMaxN + 1];
     const double *vp[kXnMaxN + 1];  // depth-first views: first element and row stride
     int vs[kXnMaxN + 1];
 };
 
-// stack entries (doubles) for order n: the kept-pivot matrices of depths 1..D-1
+// stack entries (doubles) for order n: the kept-pivot matrices of depths 1..D-1 (D = n - S)
 __host__ __device__ constexpr size_t xn_stack_entries(int n) {
     const int D = n > kXnTail ? n - kXnTail : 0;
     size_t t = 0;
@@ -284,7 +302,10 @@ __device__ __forceinline__ void xn_matrix(const double *A, int n, double *out, u
     __syncwarp();
 }
 
-__global__ void __launch_bounds__(kXnWarps * 32) xnor_kernel(const double *__restrict__ M, int n, int64_t batch,
+// CTAs per SM that the shared memory allows (228 KB per SM, 1 KB reserved per CTA)
+constexpr int kXnMinBlocks = static_cast<int>((228 * 1024) / (kXnWarps * sizeof(XnWarpSmem) + 1024));
+
+__global__ void __launch_bounds__(kXnWarps * 32, kXnMinBlocks) xnor_kernel(const double *__restrict__ M, int n, int64_t batch,
                                                              double *minors, uint32_t *status, double *stack_base,
                                                              size_t stack_per_warp) {
     extern __shared__ __align__(16) unsigned char smem_raw[];

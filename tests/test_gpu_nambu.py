@@ -39,10 +39,10 @@ def check_minors(apm, M):
     return x
 
 
-@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10])
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11])
 def test_random_matrices(apm, n):
-    """Orders on both sides of the 7-vertex tail: breadth first only (n <= 7),
-    one and several depth-first levels (n = 8..10, the stack from n = 9)."""
+    """Orders on both sides of the 8-vertex tail: breadth first only (n <= 8),
+    one and two depth-first levels (n = 9, 10; the stack from n = 10)."""
     rng = np.random.default_rng(3000 + n)
     M = rng.standard_normal((5, 2 * n, 2 * n)) + 1.5 * np.eye(2 * n)
     check_minors(apm, M)
