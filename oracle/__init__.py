@@ -65,6 +65,7 @@ def _load():
                 "oracle_keldysh_scale": [P, i32, i64, i32, P, i32],
                 "oracle_xnor_minors": [P, i32, i64, P, i32],
                 "oracle_xnor_scale": [P, i32, i64, i32, P, i32],
+                "oracle_nand": [P, i32, i64, P, P, P, i32],
             }.items():
                 f = getattr(lib, name)
                 f.argtypes = args
@@ -229,3 +230,23 @@ def xnor_scale(M, use_perm: bool | None = None, nthreads: int = 0) -> np.ndarray
     out = np.empty((M.shape[0], 1 << n))
     _load().oracle_xnor_scale(M.ctypes.data, n, M.shape[0], int(use_perm), out.ctypes.data, nthreads)
     return out[0] if single else out
+
+
+def nand(M, minors: bool = False, nthreads: int = 0):
+    """NAND minors of 2n x 2n matrices (Section III.C). Returns (abar, scale):
+    abar[S] = sum over the 2^|S| type assignments of S of the minor keeping row
+    and column 2i (type 1) or 2i+1 (type 2) of each i in S; scale[S] the sum of
+    the matching row-sum bounds. With minors=True also the 3^n minors, indexed
+    by the base-3 digits (vertex i <-> digit i; 0 none, 1 row 2i, 2 row 2i+1)."""
+    M, single, n = _xnor_batch(M)
+    assert n <= 13, n
+    b = M.shape[0]
+    abar = np.empty((b, 1 << n))
+    scale = np.empty((b, 1 << n))
+    out3 = np.empty((b, 3 ** n)) if minors else None
+    _load().oracle_nand(M.ctypes.data, n, b, None if out3 is None else out3.ctypes.data, abar.ctypes.data,
+                        scale.ctypes.data, nthreads)
+    res = [abar[0] if single else abar, scale[0] if single else scale]
+    if minors:
+        res.append(out3[0] if single else out3)
+    return tuple(res)

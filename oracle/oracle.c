@@ -21,7 +21,10 @@
  *   - XNOR minors:       for a 2n x 2n matrix of 2 x 2 blocks, the determinant
  *                        of every submatrix keeping both rows and columns of
  *                        a subset of the blocks (Section III.B, the minors of
- *                        the Nambu CDet of Section V.B), one elimination each.
+ *                        the Nambu CDet of Section V.B), one elimination each;
+ *   - NAND minors:       the 3^n submatrices keeping one or neither row and
+ *                        column of each block (Section III.C) and their sums
+ *                        over the two types of each kept vertex (Section V.C).
  *
  * Subsets are bit masks: element k (0-based) <-> bit k (Section II, the
  * subset labelling S_i by the binary digits of i). Matrices are row-major.
@@ -436,6 +439,58 @@ void oracle_xnor_scale(const double *M, int n, int64_t batch, int use_perm, doub
                 }
             }
             out[S] = acc;
+        }
+    }
+}
+
+/* NAND principal minors of each 2n x 2n matrix M (Section III.C): for every
+ * ternary assignment sigma (vertex i <-> base-3 digit i of the index: 0 keeps
+ * neither row/column 2i nor 2i+1, 1 keeps row and column 2i, 2 keeps row and
+ * column 2i+1), the determinant of the kept submatrix, each by its own
+ * partial-pivot elimination. With out3 != NULL all 3^n minors are written
+ * (out3[0] = 1); with abar != NULL, abar[S] = the sum of the minors of the
+ * 2^|S| assignments whose kept vertices are exactly S (the weights of the CDet
+ * summed over two vertex types, Section V.C); with scale != NULL, scale[S] =
+ * the sum over the same assignments of prod_r sum_q |sub_rq| (a bound on the
+ * absolute Leibniz terms). n <= 13. */
+void oracle_nand(const double *M, int n, int64_t batch, double *out3, double *abar, double *scale,
+                 int nthreads) {
+    const int m = 2 * n;
+    int64_t N3 = 1;
+    for (int i = 0; i < n; ++i) N3 *= 3;
+    const int64_t N = (int64_t)1 << n;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(threads_for(nthreads))
+    for (int64_t b = 0; b < batch; ++b) {
+        const double *Mb = M + b * (int64_t)m * m;
+        double sub[16 * 16];
+        int idx[16];
+        if (abar)
+            for (int64_t S = 0; S < N; ++S) abar[b * N + S] = 0.0;
+        if (scale)
+            for (int64_t S = 0; S < N; ++S) scale[b * N + S] = 0.0;
+        for (int64_t t = 0; t < N3; ++t) {
+            int k = 0;
+            int64_t S = 0, r3 = t;
+            for (int v = 0; v < n; ++v, r3 /= 3) {
+                const int dgt = (int)(r3 % 3);
+                if (dgt) {
+                    idx[k++] = 2 * v + (dgt - 1);
+                    S |= (int64_t)1 << v;
+                }
+            }
+            double bound = 1.0;
+            for (int r = 0; r < k; ++r) {
+                double rs = 0.0;
+                for (int q = 0; q < k; ++q) {
+                    sub[r * k + q] = Mb[idx[r] * m + idx[q]];
+                    rs += fabs(sub[r * k + q]);
+                }
+                bound *= rs;
+            }
+            const double det = det_partial_pivot(sub, k);
+            if (out3) out3[b * N3 + t] = det;
+            if (abar) abar[b * N + S] += det;
+            if (scale) scale[b * N + S] += bound;
         }
     }
 }

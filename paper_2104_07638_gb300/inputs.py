@@ -323,3 +323,22 @@ def nambu_batch(batch: int = 65536, n: int = 12, seed: int = 6) -> np.ndarray:
     Hubbard batches: sites on the 8 x 8 window, distinct times on the grid)."""
     x, y, m = hubbard_vertices(batch, n, seed, mtau=NAMBU_MTAU)
     return nambu_matrices_from_vertices(x, y, m)
+
+
+# --- two vertex types (NAND minors, Section III.C / V.C) -----------------------
+
+def two_type_batch(batch: int = 4096, n: int = 10, seed: int = 7) -> np.ndarray:
+    """Hubbard G0 matrices for expansions with two vertex types, shape
+    (batch, 2n, 2n): vertex i at (r_i, tau_i) (as hubbard_batch) has its second
+    type at (r_i + e_x, tau_i), a translated copy (the artificial second vertex
+    of Section V.C); row/column 2i is type 1, 2i+1 type 2, entry
+    G0(X_i^a - X_j^b), equal-time entries G0(r, 0^-)."""
+    x, y, m = hubbard_vertices(batch, n, seed)
+    G = hubbard_g0_table(win=HUB_WIN + 1)
+    xs = np.stack([x, x + 1], axis=-1).reshape(batch, 2 * n)
+    ys = np.repeat(y, 2, axis=-1)
+    ms = np.repeat(m, 2, axis=-1)
+    dx = np.abs(xs[:, :, None] - xs[:, None, :])
+    dy = np.abs(ys[:, :, None] - ys[:, None, :])
+    dt = ms[:, :, None] - ms[:, None, :] + (HUB_MTAU - 1)
+    return np.ascontiguousarray(G[dx, dy, dt])

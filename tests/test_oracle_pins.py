@@ -465,3 +465,69 @@ def test_xnor_scale_bounds():
     assert np.all(np.abs(x) <= sp * (1 + 1e-12))
     assert np.all(sp <= sb * (1 + 1e-12))
     assert np.all(sp[:, 0] == 1.0)
+
+
+# --- NAND minors (Section III.C) and two-vertex-type weights (Section V.C) ----
+
+def _tern(t, n):
+    return [(t // 3 ** v) % 3 for v in range(n)]
+
+
+def test_nand_minors_match_numpy_determinants():
+    rng = np.random.default_rng(2101)
+    for n in (1, 2, 4):
+        M = rng.standard_normal((2 * n, 2 * n)) + np.eye(2 * n)
+        ab, sc, m3 = oracle.nand(M, minors=True)
+        assert m3[0] == 1.0 and ab[0] == 1.0
+        for t in range(1, 3 ** n):
+            idx = [2 * v + d - 1 for v, d in enumerate(_tern(t, n)) if d]
+            ref = np.linalg.det(M[np.ix_(idx, idx)])
+            assert abs(m3[t] - ref) <= 1e-12 * max(1.0, abs(ref)), (n, t)
+        assert np.all(np.abs(ab) <= sc * (1 + 1e-12))
+
+
+def test_nand_type_sums_are_real_keldysh_sums():
+    """For every subset S, abar[S] is the sum over the 2^|S| type assignments of
+    the kept minors, i.e. the XOR sum of Section III.D of the block matrix
+    restricted to S: the independent complex route of the Keldysh oracle."""
+    rng = np.random.default_rng(2102)
+    n = 5
+    M = rng.standard_normal((2 * n, 2 * n)) + np.eye(2 * n)
+    ab, _ = oracle.nand(M)
+    for S in (0b11111, 0b10101, 0b00110, 0b01000):
+        vs = [v for v in range(n) if (S >> v) & 1]
+        rows = [2 * v + e for v in vs for e in (0, 1)]
+        ref = oracle.keldysh(M[np.ix_(rows, rows)].astype(np.complex128))
+        assert abs(ab[S] - ref.real) <= 1e-12 * max(1.0, abs(ref)) and abs(ref.imag) == 0.0
+
+
+def test_nand_block_diagonal_and_equal_types():
+    rng = np.random.default_rng(2103)
+    n = 5
+    B = rng.standard_normal((n, 2, 2))
+    M = np.zeros((2 * n, 2 * n))
+    for i in range(n):
+        M[2 * i:2 * i + 2, 2 * i:2 * i + 2] = B[i]
+    ab, _, m3 = oracle.nand(M, minors=True)
+    for t in range(3 ** n):
+        ref = np.prod([B[v, d - 1, d - 1] for v, d in enumerate(_tern(t, n)) if d])
+        assert abs(m3[t] - ref) <= 1e-14 * max(1.0, abs(ref))
+    for S in range(1 << n):
+        ref = np.prod([B[v, 0, 0] + B[v, 1, 1] for v in range(n) if (S >> v) & 1])
+        assert abs(ab[S] - ref) <= 1e-13 * max(1.0, abs(ref))
+    # both types of every vertex identical: each of the 2^|S| minors is det g[S]
+    g = rng.standard_normal((n, n)) + 2 * np.eye(n)
+    ab2, _ = oracle.nand(np.kron(g, np.ones((2, 2))))
+    for S in range(1, 1 << n):
+        vs = [v for v in range(n) if (S >> v) & 1]
+        ref = 2 ** len(vs) * np.linalg.det(g[np.ix_(vs, vs)])
+        assert abs(ab2[S] - ref) <= 1e-12 * max(1.0, abs(ref))
+
+
+def test_two_type_inputs_conventions():
+    M = I.two_type_batch(2, 6, seed=2104)
+    assert M.shape == (2, 12, 12)
+    # type-2 of a vertex is its type-1 copy shifted by one site at the same time
+    G = I.hubbard_g0_table(win=I.HUB_WIN + 1)
+    assert np.allclose(M[:, 0, 1], G[1, 0, I.HUB_MTAU - 1])
+    assert np.allclose(np.diagonal(M, axis1=1, axis2=2), G[0, 0, I.HUB_MTAU - 1])
