@@ -68,6 +68,8 @@ typedef enum {
 #define APM_MAX_N_KELDYSH  16
 #define APM_MAX_N_PERM     16
 #define APM_MAX_N_XNOR     16
+#define APM_MAX_N_NAND_MINORS 13 /* 3^n doubles per matrix */
+#define APM_MAX_N_TWO_TYPE 16
 
 /*
  * Pivot correction (Section II, the paragraph after Eq. minor and Alg. 1): when
@@ -168,6 +170,38 @@ apm_status_t apm_xnor_minors(const double *M, int n, int64_t batch, double *mino
 apm_status_t apm_nambu_cdet(const double *M, int n, int64_t batch, double *minors, double *c, uint32_t *status,
                             void *workspace, size_t workspace_bytes, apm_stream_t stream);
 
+/*
+ * apm_nand_minors -- all 3^n NAND principal minors of 2n x 2n matrices made of
+ * 2 x 2 blocks (Section III.C): for every ternary assignment sigma (vertex i <->
+ * base-3 digit i of the index: 0 keeps neither row/column 2i nor 2i+1, 1 keeps
+ * row and column 2i, 2 keeps row and column 2i+1) the determinant of the kept
+ * submatrix; minors3[0] = 1. Ternary tree of Schur complements with scalar
+ * pivots, O(3^n). Pivot corrections, which the paper allows here, are not
+ * applied: a zero or non-finite pivot is flagged instead.
+ *   M        [batch][2n][2n] float64, row-major.
+ *   n        1..APM_MAX_N_NAND_MINORS.
+ *   minors3  [batch][3^n] float64 output.
+ *   status   [batch] or NULL; APM_ST_ZERO_PIVOT (a zero or non-finite pivot met
+ *            on the way) or APM_ST_NONFINITE_INPUT make that matrix's row NaN.
+ *   workspace / workspace_bytes: scratch for the depth-first part, needed for
+ *            n > 7 (apm_workspace_size with APM_OP_NAND_MINORS).
+ */
+apm_status_t apm_nand_minors(const double *M, int n, int64_t batch, double *minors3, uint32_t *status,
+                             void *workspace, size_t workspace_bytes, apm_stream_t stream);
+
+/*
+ * apm_two_type_cdet -- the CDet summed over two vertex types (Section V.C):
+ * abar[S] = the sum over the 2^|S| type assignments of the vertices of S of the
+ * NAND minors (apm_nand_minors), abar[0] = 1, then c[S] from abar by the CDet
+ * recursion (Eq. recursion; summing over types block by block is exact because
+ * the recursion is a sum over set partitions of products of block weights).
+ *   abar, c  [batch][2^n] float64 outputs.   n  1..APM_MAX_N_TWO_TYPE.
+ *   Other arguments as for apm_nand_minors; workspace: apm_workspace_size with
+ *   APM_OP_TWO_TYPE_CDET (zero for n <= 7).
+ */
+apm_status_t apm_two_type_cdet(const double *M, int n, int64_t batch, double *abar, double *c, uint32_t *status,
+                               void *workspace, size_t workspace_bytes, apm_stream_t stream);
+
 /* flags for apm_keldysh_sum and apm_keldysh_sum_noalloc */
 #define APM_KELDYSH_SIGNED 0x1 /* weight each assignment by (-1)^{number of - indices} */
 
@@ -246,6 +280,8 @@ apm_status_t apm_perm_minors(const double *A, int n, int64_t batch, double *perm
 #define APM_OP_KELDYSH_VARLEN 7
 #define APM_OP_XNOR_MINORS 8
 #define APM_OP_NAMBU_CDET 9
+#define APM_OP_NAND_MINORS 10
+#define APM_OP_TWO_TYPE_CDET 11
 
 /*
  * apm_cdet_connected_varlen -- apm_cdet_connected for a batch of matrices of

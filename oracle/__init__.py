@@ -239,7 +239,7 @@ def nand(M, minors: bool = False, nthreads: int = 0):
     the matching row-sum bounds. With minors=True also the 3^n minors, indexed
     by the base-3 digits (vertex i <-> digit i; 0 none, 1 row 2i, 2 row 2i+1)."""
     M, single, n = _xnor_batch(M)
-    assert n <= 13, n
+    assert n <= (13 if minors else 16), n
     b = M.shape[0]
     abar = np.empty((b, 1 << n))
     scale = np.empty((b, 1 << n))

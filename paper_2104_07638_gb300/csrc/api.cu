@@ -156,6 +156,46 @@ apm_status_t apm_nambu_cdet(const double *M, int n, int64_t batch, double *minor
     return cdet_common(a, workspace, workspace_bytes, s);
 }
 
+apm_status_t apm_nand_minors(const double *M, int n, int64_t batch, double *minors3, uint32_t *status,
+                             void *workspace, size_t workspace_bytes, apm_stream_t stream) {
+    if (n < 1 || n > APM_MAX_N_NAND_MINORS) return APM_ERR_UNSUPPORTED_N;
+    if (batch < 0) return APM_ERR_ARG;
+    apm_status_t st;
+    if ((st = check_ptr(M, batch)) || (st = check_ptr(minors3, batch)) || (st = check_opt_ptr(status))) return st;
+    if (batch == 0) return APM_OK;
+    size_t need = 0;
+    if ((st = apm_workspace_size(APM_OP_NAND_MINORS, n, batch, 0, &need))) return st;
+    if (need > 0 && (!workspace || workspace_bytes < need || !aligned16(workspace))) return APM_ERR_WORKSPACE;
+    const int e = apm::launch_nand(M, n, batch, minors3, false, status, workspace,
+                                   reinterpret_cast<cudaStream_t>(stream));
+    return e ? cuda_fail(e) : APM_OK;
+}
+
+apm_status_t apm_two_type_cdet(const double *M, int n, int64_t batch, double *abar, double *c, uint32_t *status,
+                               void *workspace, size_t workspace_bytes, apm_stream_t stream) {
+    if (n < 1 || n > APM_MAX_N_TWO_TYPE) return APM_ERR_UNSUPPORTED_N;
+    if (batch < 0) return APM_ERR_ARG;
+    apm_status_t st;
+    if ((st = check_ptr(M, batch)) || (st = check_ptr(abar, batch)) || (st = check_ptr(c, batch)) ||
+        (st = check_opt_ptr(status)))
+        return st;
+    if (batch == 0) return APM_OK;
+    size_t need = 0;
+    if ((st = apm_workspace_size(APM_OP_TWO_TYPE_CDET, n, batch, 0, &need))) return st;
+    if (need > 0 && (!workspace || workspace_bytes < need || !aligned16(workspace))) return APM_ERR_WORKSPACE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int e = apm::launch_nand(M, n, batch, abar, true, status, workspace, s);
+    if (e) return cuda_fail(e);
+    // the same scratch serves the recursion: the two launches run in order on s
+    apm::CdetArgs a = {};
+    a.a_in = abar;
+    a.c_out = c;
+    a.batch = batch;
+    a.n = n;
+    a.mode = apm::kModeWeights;
+    return cdet_common(a, workspace, workspace_bytes, s);
+}
+
 apm_status_t apm_keldysh_sum(const double *Mt, int n, int64_t batch, int flags, double *sum,
                              double *partial, uint32_t *status, void *workspace,
                              size_t workspace_bytes, apm_stream_t stream) {
@@ -303,6 +343,23 @@ apm_status_t apm_workspace_size(int op, int n_max, int64_t batch, int two_mats, 
             size_t need = apm::xnor_workspace_bytes(n_max, batch, &err);
             if (err) return cuda_fail(err);
             if (op == APM_OP_NAMBU_CDET && n_max > apm::cdet_smem_max_n(false)) {
+                const int grid = apm::cdet_grid(n_max, batch, false, false, &err);
+                if (err) return cuda_fail(err);
+                const size_t rec = static_cast<size_t>(grid) * apm::cdet_slot_doubles(n_max) * sizeof(double);
+                if (rec > need) need = rec;
+            }
+            *bytes = need;
+            return APM_OK;
+        }
+        case APM_OP_NAND_MINORS:
+        case APM_OP_TWO_TYPE_CDET: {
+            const int nmax = op == APM_OP_NAND_MINORS ? APM_MAX_N_NAND_MINORS : APM_MAX_N_TWO_TYPE;
+            if (n_max < 1 || n_max > nmax) return APM_ERR_UNSUPPORTED_N;
+            if (batch == 0) return APM_OK;
+            int err = 0;
+            size_t need = apm::nand_workspace_bytes(n_max, batch, &err);
+            if (err) return cuda_fail(err);
+            if (op == APM_OP_TWO_TYPE_CDET && n_max > apm::cdet_smem_max_n(false)) {
                 const int grid = apm::cdet_grid(n_max, batch, false, false, &err);
                 if (err) return cuda_fail(err);
                 const size_t rec = static_cast<size_t>(grid) * apm::cdet_slot_doubles(n_max) * sizeof(double);

@@ -93,6 +93,13 @@ size_t xnor_workspace_bytes(int n, int64_t batch, int *err);
 int launch_xnor(const double *M, int n, int64_t batch, double *minors, uint32_t *status, void *workspace,
                 cudaStream_t s);
 
+// NAND minors (type_sums = false: all 3^n per matrix) or their sums over the
+// two vertex types (type_sums = true: 2^n per matrix); one warp per matrix.
+int nand_grid(int64_t batch, int *err);
+size_t nand_workspace_bytes(int n, int64_t batch, int *err);
+int launch_nand(const double *M, int n, int64_t batch, double *out, bool type_sums, uint32_t *status,
+                void *workspace, cudaStream_t s);
+
 // uneven batches
 unsigned long long cdet_gsel_packed(int n);
 void cdet_tune_set(const unsigned long long *table);

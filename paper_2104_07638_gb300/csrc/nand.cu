@@ -1,0 +1,378 @@
+// NAND principal minors of 2n x 2n block matrices, and the weights of the CDet
+// summed over two vertex types.
+//
+// Paper: Section III.C (NAND minors: for a matrix of 2 x 2 blocks, the minors of
+// the submatrices that keep at most one row and column of each block, 3^n of
+// them; a ternary tree whose left branch drops a block and whose two right
+// branches take the Schur complement with respect to the block's first or
+// second diagonal entry, dropping the other; O(3^n)) and Section V.C (summing
+// the CDet over the two types of every vertex needs, for each vertex subset S,
+// the sum over the 2^|S| type assignments of these minors; the recursion that
+// follows is the plain CDet one).
+//
+// Indexing: a ternary assignment sigma (vertex i <-> base-3 digit i: 0 drops
+// the block, 1 keeps row/column 2i, 2 keeps row/column 2i+1) has index
+// sum_i sigma_i 3^i; minors3[0] = 1. The type sums: abar[S] = sum over sigma
+// with {i : sigma_i != 0} = S, abar[0] = 1.
+//
+// Mapping: one warp per matrix, as for the XNOR minors: vertices eliminated
+// from the last one down (a dropped vertex is a smaller view of the same
+// rows), the upper vertices s..n-1 (s = min(n, 6)) depth first in base 3 (the
+// matrices of kept pivots on a per-warp stack in caller scratch), the last s
+// vertices breadth first in shared memory, and the 4 x 4 nodes of the last two
+// vertices in closed form (9 minors per node). For the type sums the 3^s
+// minors of a tail go to shared memory and are reduced vertex by vertex (the
+// two kept types of one vertex added, in a fixed order) to 2^s sums, which the
+// warp adds into the matrix's row.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "apm_internal.cuh"
+
+namespace apm {
+
+constexpr int kNdTail = 6;   // vertices expanded breadth first
+constexpr int kNdWarps = 2;  // warps per CTA
+constexpr int kNdMaxN = 16;
+
+__host__ __device__ constexpr int nd_pow3(int k) {
+    int r = 1;
+    for (int i = 0; i < k; ++i) r *= 3;
+    return r;
+}
+// Tail level J (J = 0..S-2) holds 3^J nodes of size 2(S-J); even levels in
+// bufE, odd in bufO. S = 6: bufE 144, 576, 1296; bufO 300, 972.
+__host__ __device__ constexpr int nd_level_entries(int S, int J) {
+    return nd_pow3(J) * (2 * (S - J)) * (2 * (S - J));
+}
+__host__ __device__ constexpr int nd_buf_entries(int S, int parity) {
+    int b = 0;
+    for (int J = parity; J <= S - 2; J += 2) b = b > nd_level_entries(S, J) ? b : nd_level_entries(S, J);
+    return b;
+}
+constexpr int kNdBufE = nd_buf_entries(kNdTail, 0);
+constexpr int kNdBufO = nd_buf_entries(kNdTail, 1);
+static_assert(kNdBufE == 1296 && kNdBufO == 972, "6-vertex tail");
+static_assert(kNdBufO >= 729 && kNdBufE >= 729, "the 3^6 tail minors fit in either buffer");
+// row factors of one level: 2 kept children per node, m-2 rows each (27 x 2 x 4)
+constexpr int kNdFac = 216;
+
+struct NdWarpSmem {
+    double bufE[kNdBufE];
+    double bufO[kNdBufO];
+    double f[kNdFac];                          // row factors of one level or depth-first step
+    double inv[2 * nd_pow3(kNdTail - 3)];       // reciprocal pivots of one level (2 per node)
+    double nd[2][nd_pow3(kNdTail - 2)];         // node determinants, current and next level
+    double pdet[kNdMaxN + 1];
+    const double *vp[kNdMaxN + 1];  // depth-first views: first element and row stride
+    int vs[kNdMaxN + 1];
+    int smask[kNdMaxN + 1];  // kept upper vertices (bit v) along the depth-first path
+};
+
+// stack entries (doubles) for order n: the kept-pivot matrices of depths 1..D-1 (D = n - S)
+__host__ __device__ constexpr size_t nd_stack_entries(int n) {
+    const int D = n > kNdTail ? n - kNdTail : 0;
+    size_t t = 0;
+    for (int d = 1; d < D; ++d) t += static_cast<size_t>(2 * (n - d)) * (2 * (n - d));
+    return t;
+}
+
+// 1/p for a pivot; flags a zero or non-finite value
+__device__ __forceinline__ double nd_inv(double p, int &bad) {
+    const long long bits = __double_as_longlong(p);
+    if ((bits << 1) == 0 || ((bits >> 52) & 0x7ff) == 0x7ff) bad = 1;
+    return rcp_nr(p);
+}
+
+// One breadth-first level J of a tail over S vertices: the 3^J nodes of size
+// m = 2(S-J) in cur give 3^(J+1) children of size m-2 in nxt. Child 3k drops the
+// node's last vertex (the leading block, copied); child 3k+1+t keeps its row
+// and column m-2+t (t = 0, 1) and drops the other: the rank-1 Schur update
+// (r,q) -= f(r) node(m-2+t, q), f(r) = node(r, m-2+t) / node(m-2+t, m-2+t).
+template <int S, int J>
+__device__ __forceinline__ void nd_tail_level(const double *cur, double *nxt, NdWarpSmem &w, int lane, int &bad) {
+    constexpr int m = 2 * (S - J), m2 = m - 2, mm = m * m, mm2 = m2 * m2, nodes = nd_pow3(J);
+    const double *ndc = w.nd[J & 1];
+    double *ndn = w.nd[(J + 1) & 1];
+    for (int i = lane; i < 2 * nodes; i += 32) {
+        const int k = i >> 1, t = i & 1, pi = m - 2 + t;
+        const double p = cur[k * mm + pi * m + pi];
+        w.inv[i] = nd_inv(p, bad);
+        ndn[3 * k + 1 + t] = ndc[k] * p;
+        if (t == 0) ndn[3 * k] = ndc[k];
+    }
+    __syncwarp();
+    for (int idx = lane; idx < 2 * nodes * m2; idx += 32) {
+        const int kt = idx / m2, r = idx - kt * m2;
+        w.f[idx] = cur[(kt >> 1) * mm + r * m + (m - 2 + (kt & 1))] * w.inv[kt];
+    }
+    __syncwarp();
+    for (int e = lane; e < nodes * mm2; e += 32) {
+        const int k = e / mm2, rem = e - k * mm2, r = rem / m2, q = rem - r * m2;
+        nxt[(3 * k) * mm2 + rem] = cur[k * mm + r * m + q];
+    }
+    for (int e = lane; e < 2 * nodes * mm2; e += 32) {
+        const int kt = e / mm2, rem = e - kt * mm2, r = rem / m2, q = rem - r * m2;
+        const int k = kt >> 1, t = kt & 1;
+        const double *P = cur + k * mm;
+        nxt[(3 * k + 1 + t) * mm2 + rem] = fma(-w.f[kt * m2 + r], P[(m - 2 + t) * m + q], P[r * m + q]);
+    }
+    __syncwarp();
+}
+
+// The last two vertices (0: rows 0,1; 1: rows 2,3) of every 4 x 4 node k in
+// closed form: the 9 minors nd * (1, M00, M11, M22, det{0,2}, det{1,2}, M33,
+// det{0,3}, det{1,3}) at out[9k + sigma_0 + 3 sigma_1].
+template <int S>
+__device__ __forceinline__ void nd_bottom(const double *cur, const double *nd, double *out, int lane) {
+    constexpr int nodes = nd_pow3(S - 2);
+    for (int k = lane; k < nodes; k += 32) {
+        const double *M = cur + 16 * k;
+        const double d = nd[k];
+        double *o = out + 9 * k;
+        o[0] = d;
+        o[1] = d * M[0];
+        o[2] = d * M[5];
+        o[3] = d * M[10];
+        o[4] = d * fma(M[0], M[10], -M[2] * M[8]);
+        o[5] = d * fma(M[5], M[10], -M[6] * M[9]);
+        o[6] = d * M[15];
+        o[7] = d * fma(M[0], M[15], -M[3] * M[12]);
+        o[8] = d * fma(M[5], M[15], -M[7] * M[13]);
+    }
+}
+
+// Type sums of a tail's 3^s minors (in a): vertex by vertex, the entries of its
+// two kept types are added (type 1 + type 2, a fixed order); returns the buffer
+// that holds the 2^s sums (index: bit v <-> vertex v kept).
+__device__ __forceinline__ const double *nd_type_sum(int s, double *a, double *b, int lane) {
+    int rest = nd_pow3(s - 1);
+    for (int v = 0; v < s; ++v, rest /= 3) {
+        const int lowsz = 1 << v, nsz = 2 * lowsz * rest;
+        for (int i = lane; i < nsz; i += 32) {
+            const int low = i & (lowsz - 1), kept = (i >> v) & 1, r = i >> (v + 1);
+            const int base = low + lowsz * 3 * r;
+            b[i] = kept ? a[base + lowsz] + a[base + 2 * lowsz] : a[base];
+        }
+        __syncwarp();
+        double *t = a;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+// Tail over the last S vertices; the root (2S x 2S, dense) is in bufE with
+// determinant det0. kSum = false: the 3^S minors go to gout[0 .. 3^S);
+// kSum = true: their type sums are added to gout[0 .. 2^S).
+template <int S, int J, bool kSum>
+__device__ __forceinline__ void nd_tail_levels(double *cur, double *nxt, double *gout, NdWarpSmem &w, int lane,
+                                               int &bad) {
+    if constexpr (J < S - 2) {
+        nd_tail_level<S, J>(cur, nxt, w, lane, bad);
+        nd_tail_levels<S, J + 1, kSum>(nxt, cur, gout, w, lane, bad);
+    } else if constexpr (!kSum) {
+        nd_bottom<S>(cur, w.nd[J & 1], gout, lane);
+    } else {
+        nd_bottom<S>(cur, w.nd[J & 1], nxt, lane);
+        __syncwarp();
+        const double *T = nd_type_sum(S, nxt, cur, lane);
+        for (int i = lane; i < (1 << S); i += 32) gout[i] += T[i];
+    }
+}
+
+template <int S, bool kSum>
+__device__ __forceinline__ void nd_tail(double det0, double *gout, NdWarpSmem &w, int lane, int &bad) {
+    if constexpr (S == 1) {
+        if (lane == 0) {
+            if constexpr (kSum) {
+                gout[0] += det0;
+                gout[1] += det0 * (w.bufE[0] + w.bufE[3]);
+            } else {
+                gout[0] = det0;
+                gout[1] = det0 * w.bufE[0];
+                gout[2] = det0 * w.bufE[3];
+            }
+        }
+    } else {
+        if (lane == 0) w.nd[0][0] = det0;
+        __syncwarp();
+        nd_tail_levels<S, 0, kSum>(w.bufE, w.bufO, gout, w, lane, bad);
+    }
+    __syncwarp();
+}
+
+// Whole matrix of order n <= S as one tail.
+template <int S, bool kSum>
+__device__ __forceinline__ void nd_tail_order(int n, double *gout, NdWarpSmem &w, int lane, int &bad) {
+    if constexpr (S >= 1) {
+        if (n == S) nd_tail<S, kSum>(1.0, gout, w, lane, bad);
+        else nd_tail_order<S - 1, kSum>(n, gout, w, lane, bad);
+    }
+}
+
+// One matrix of order n (whole warp). kSum = false: all 3^n minors into out;
+// kSum = true: the 2^n type sums. A zero or non-finite pivot, or a non-finite
+// input, sets the status and makes the whole row NaN.
+template <bool kSum>
+__device__ __forceinline__ void nd_matrix(const double *A, int n, double *out, uint32_t *status_out, double *stack,
+                                          NdWarpSmem &w, int lane) {
+    const int s = n < kNdTail ? n : kNdTail;
+    const int D = n - s;
+    const int m0 = 2 * n;
+    const int64_t row = kSum ? (int64_t(1) << n) : static_cast<int64_t>(nd_pow3(n));
+    int bad = 0, nonfin = 0;
+    for (int e = lane; e < m0 * m0; e += 32)
+        if (!isfinite(A[e])) nonfin = 1;
+    nonfin = __any_sync(0xffffffffu, nonfin);
+    if (kSum)
+        for (int64_t e = lane; e < row; e += 32) out[e] = 0.0;
+    __syncwarp();
+    if (!nonfin) {
+        if (D == 0) {
+            for (int e = lane; e < m0 * m0; e += 32) w.bufE[e] = A[e];
+            __syncwarp();
+            nd_tail_order<kNdTail, kSum>(n, out, w, lane, bad);
+        } else {
+            if (lane == 0) {
+                w.vp[0] = A;
+                w.vs[0] = m0;
+                w.pdet[0] = 1.0;
+                w.smask[0] = 0;
+            }
+            __syncwarp();
+            const int64_t T3 = nd_pow3(D), tail3 = nd_pow3(s);
+            for (int64_t t = 0; t < T3; ++t) {
+                // first depth whose digit changed from t-1 to t (vertex n-1 <-> top digit)
+                int d0 = 0;
+                if (t) {
+                    int p = 0;
+                    for (int64_t u = t; u % 3 == 0; u /= 3) ++p;
+                    d0 = D - 1 - p;
+                }
+                for (int d = d0; d < D; ++d) {
+                    const int digit = static_cast<int>((t / nd_pow3(D - 1 - d)) % 3);
+                    const double *P = w.vp[d];
+                    const int st = w.vs[d], m = 2 * (n - d), m2 = m - 2;
+                    if (digit) {
+                        const int pi = m - 2 + (digit - 1);
+                        double *dst = w.bufE;
+                        if (d + 1 < D) {  // stack slot of depth d+1
+                            size_t off = 0;
+                            for (int k = 1; k <= d; ++k) off += static_cast<size_t>(2 * (n - k)) * (2 * (n - k));
+                            dst = stack + off;
+                        }
+                        const double piv = P[pi * st + pi];
+                        const double iv = nd_inv(piv, bad);
+                        for (int r = lane; r < m2; r += 32) w.f[r] = P[r * st + pi] * iv;
+                        __syncwarp();
+                        for (int e = lane; e < m2 * m2; e += 32) {
+                            const int r = e / m2, q = e - r * m2;
+                            dst[e] = fma(-w.f[r], P[pi * st + q], P[r * st + q]);
+                        }
+                        __syncwarp();
+                        if (lane == 0) {
+                            w.vp[d + 1] = dst;
+                            w.vs[d + 1] = m2;
+                            w.pdet[d + 1] = w.pdet[d] * piv;
+                            w.smask[d + 1] = w.smask[d] | (1 << (n - 1 - d));
+                        }
+                    } else {
+                        if (d + 1 == D) {  // the tail root must be dense
+                            for (int e = lane; e < m2 * m2; e += 32) {
+                                const int r = e / m2, q = e - r * m2;
+                                w.bufE[e] = P[r * st + q];
+                            }
+                        }
+                        if (lane == 0) {
+                            w.vp[d + 1] = d + 1 == D ? w.bufE : P;
+                            w.vs[d + 1] = d + 1 == D ? m2 : st;
+                            w.pdet[d + 1] = w.pdet[d];
+                            w.smask[d + 1] = w.smask[d];
+                        }
+                    }
+                    __syncwarp();
+                }
+                double *gout = kSum ? out + w.smask[D] : out + t * tail3;
+                nd_tail<kNdTail, kSum>(w.pdet[D], gout, w, lane, bad);
+            }
+        }
+    }
+    bad = __any_sync(0xffffffffu, bad);
+    if (bad || nonfin) {
+        const double nanv = __longlong_as_double(0x7ff8000000000000ll);
+        for (int64_t e = lane; e < row; e += 32) out[e] = nanv;
+    }
+    if (lane == 0 && status_out)
+        *status_out = (bad ? APM_ST_ZERO_PIVOT : 0u) | (nonfin ? APM_ST_NONFINITE_INPUT : 0u);
+    __syncwarp();
+}
+
+// CTAs per SM that the shared memory allows (228 KB per SM, 1 KB reserved per CTA)
+constexpr int kNdMinBlocks = static_cast<int>((228 * 1024) / (kNdWarps * sizeof(NdWarpSmem) + 1024));
+
+template <bool kSum>
+__global__ void __launch_bounds__(kNdWarps * 32, kNdMinBlocks) nand_kernel(const double *__restrict__ M, int n,
+                                                                         int64_t batch, double *out,
+                                                                         uint32_t *status, double *stack_base,
+                                                                         size_t stack_per_warp) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    NdWarpSmem &w = reinterpret_cast<NdWarpSmem *>(smem_raw)[wid];
+    const int64_t gw = static_cast<int64_t>(blockIdx.x) * kNdWarps + wid;
+    const int64_t nw = static_cast<int64_t>(gridDim.x) * kNdWarps;
+    double *stack = stack_base ? stack_base + gw * stack_per_warp : nullptr;
+    const int64_t m0 = 2 * n;
+    const int64_t row = kSum ? (int64_t(1) << n) : static_cast<int64_t>(nd_pow3(n));
+    for (int64_t b = gw; b < batch; b += nw)
+        nd_matrix<kSum>(M + b * m0 * m0, n, out + b * row, status ? status + b : nullptr, stack, w, lane);
+}
+
+int nand_grid(int64_t batch, int *err) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t smem = kNdWarps * sizeof(NdWarpSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(nand_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(smem));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(nand_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(smem));
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, nand_kernel<true>, kNdWarps * 32, smem);
+    if (e != cudaSuccess || per_sm < 1) {
+        *err = e != cudaSuccess ? static_cast<int>(e) : static_cast<int>(cudaErrorInvalidConfiguration);
+        return 0;
+    }
+    *err = 0;
+    const int64_t need = (batch + kNdWarps - 1) / kNdWarps;
+    int64_t g = static_cast<int64_t>(sms) * per_sm;
+    if (need < g) g = need;
+    return static_cast<int>(g < 1 ? 1 : g);
+}
+
+size_t nand_workspace_bytes(int n, int64_t batch, int *err) {
+    *err = 0;
+    const size_t per = nd_stack_entries(n);
+    if (per == 0 || batch == 0) return 0;
+    const int grid = nand_grid(batch, err);
+    if (*err) return 0;
+    return static_cast<size_t>(grid) * kNdWarps * per * sizeof(double);
+}
+
+int launch_nand(const double *M, int n, int64_t batch, double *out, bool type_sums, uint32_t *status,
+                void *workspace, cudaStream_t s) {
+    int err = 0;
+    const int grid = nand_grid(batch, &err);
+    if (err) return err;
+    const size_t smem = kNdWarps * sizeof(NdWarpSmem);
+    double *stack = static_cast<double *>(workspace);
+    if (type_sums)
+        nand_kernel<true><<<grid, kNdWarps * 32, smem, s>>>(M, n, batch, out, status, stack, nd_stack_entries(n));
+    else
+        nand_kernel<false><<<grid, kNdWarps * 32, smem, s>>>(M, n, batch, out, status, stack, nd_stack_entries(n));
+    return static_cast<int>(cudaGetLastError());
+}
+
+}  // namespace apm
