@@ -20,10 +20,11 @@
 // rows), the upper vertices s..n-1 (s = min(n, 6)) depth first in base 3 (the
 // matrices of kept pivots on a per-warp stack in caller scratch), the last s
 // vertices breadth first in shared memory, and the 4 x 4 nodes of the last two
-// vertices in closed form (9 minors per node). For the type sums the 3^s
-// minors of a tail go to shared memory and are reduced vertex by vertex (the
-// two kept types of one vertex added, in a fixed order) to 2^s sums, which the
-// warp adds into the matrix's row.
+// vertices in closed form (9 minors per node). For the type sums the closed
+// form gives the 4 sums over the types of those two vertices, and the other
+// tail vertices are reduced in shared memory vertex by vertex (the two kept
+// types of one vertex added, in a fixed order) to 2^s sums, which the warp
+// adds into the matrix's row.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -57,7 +58,9 @@ static_assert(kNdBufO >= 729 && kNdBufE >= 729, "the 3^6 tail minors fit in eith
 // row factors of one level: 2 kept children per node, m-2 rows each (27 x 2 x 4)
 constexpr int kNdFac = 216;
 
-struct NdWarpSmem {
+// 16-byte aligned, and a multiple of 16 bytes, so that every warp's buffers
+// take 16-byte (double2) stores
+struct alignas(16) NdWarpSmem {
     double bufE[kNdBufE];
     double bufO[kNdBufO];
     double f[kNdFac];                          // row factors of one level or depth-first step
@@ -68,6 +71,8 @@ struct NdWarpSmem {
     int vs[kNdMaxN + 1];
     int smask[kNdMaxN + 1];  // kept upper vertices (bit v) along the depth-first path
 };
+
+static_assert(sizeof(NdWarpSmem) % 16 == 0, "per-warp blocks stay 16-byte aligned");
 
 // stack entries (doubles) for order n: the kept-pivot matrices of depths 1..D-1 (D = n - S)
 __host__ __device__ constexpr size_t nd_stack_entries(int n) {
@@ -142,17 +147,37 @@ __device__ __forceinline__ void nd_bottom(const double *cur, const double *nd, d
     }
 }
 
-// Type sums of a tail's 3^s minors (in a): vertex by vertex, the entries of its
-// two kept types are added (type 1 + type 2, a fixed order); returns the buffer
-// that holds the 2^s sums (index: bit v <-> vertex v kept).
+// The type sums of the last two vertices of every 4 x 4 node k: out[4k + b],
+// bit 0 of b <-> vertex 0 kept, bit 1 <-> vertex 1 kept: nd * (1, M00 + M11,
+// M22 + M33, the four minors of one row/column of each).
+template <int S>
+__device__ __forceinline__ void nd_bottom_sum(const double *cur, const double *nd, double *out, int lane) {
+    constexpr int nodes = nd_pow3(S - 2);
+    for (int k = lane; k < nodes; k += 32) {
+        const double *M = cur + 16 * k;
+        const double d = nd[k];
+        const double m4 = fma(M[0], M[10], -M[2] * M[8]) + fma(M[5], M[10], -M[6] * M[9]) +
+                          fma(M[0], M[15], -M[3] * M[12]) + fma(M[5], M[15], -M[7] * M[13]);
+        double2 *o = reinterpret_cast<double2 *>(out + 4 * k);
+        o[0] = make_double2(d, d * (M[0] + M[5]));
+        o[1] = make_double2(d * (M[10] + M[15]), d * m4);
+    }
+}
+
+// Type sums over the remaining tail vertices 2..s-1: a holds, for each node,
+// the 4 sums of the last two vertices (index low + 4 * (ternary digits of
+// vertices 2..s-1)); vertex by vertex, the entries of its two kept types are
+// added (type 1 + type 2, a fixed order). Returns the buffer holding the 2^s
+// sums (bit v <-> vertex v kept).
 __device__ __forceinline__ const double *nd_type_sum(int s, double *a, double *b, int lane) {
-    int rest = nd_pow3(s - 1);
-    for (int v = 0; v < s; ++v, rest /= 3) {
-        const int lowsz = 1 << v, nsz = 2 * lowsz * rest;
-        for (int i = lane; i < nsz; i += 32) {
-            const int low = i & (lowsz - 1), kept = (i >> v) & 1, r = i >> (v + 1);
-            const int base = low + lowsz * 3 * r;
-            b[i] = kept ? a[base + lowsz] + a[base + 2 * lowsz] : a[base];
+    int rest = nd_pow3(s - 3);
+    for (int v = 2; v < s; ++v, rest /= 3) {
+        const int lowsz = 1 << v;
+        for (int j = lane; j < lowsz * rest; j += 32) {
+            const int low = j & (lowsz - 1), r = j >> v;
+            const int base = low + lowsz * 3 * r, i0 = low + lowsz * 2 * r;
+            b[i0] = a[base];
+            b[i0 + lowsz] = a[base + lowsz] + a[base + 2 * lowsz];
         }
         __syncwarp();
         double *t = a;
@@ -174,7 +199,7 @@ __device__ __forceinline__ void nd_tail_levels(double *cur, double *nxt, double 
     } else if constexpr (!kSum) {
         nd_bottom<S>(cur, w.nd[J & 1], gout, lane);
     } else {
-        nd_bottom<S>(cur, w.nd[J & 1], nxt, lane);
+        nd_bottom_sum<S>(cur, w.nd[J & 1], nxt, lane);
         __syncwarp();
         const double *T = nd_type_sum(S, nxt, cur, lane);
         for (int i = lane; i < (1 << S); i += 32) gout[i] += T[i];

@@ -65,7 +65,7 @@ static_assert(kXnTail != 7 || (kXnBufE == 576 && kXnBufO == 512 && kXnFac == 128
 static_assert(kXnTail != 8 || (kXnBufE == 1024 && kXnBufO == 1152 && kXnFac == 256), "8-vertex tail");
 constexpr int kXnMaxN = 16;
 
-struct XnWarpSmem {
+struct alignas(16) XnWarpSmem {
     double bufE[kXnBufE];
     double bufO[kXnBufO];
     double F[kXnFac];                  // row factors C P^-1 of one level or depth-first step
@@ -75,6 +75,8 @@ struct XnWarpSmem {
     const double *vp[kXnMaxN + 1];  // depth-first views: first element and row stride
     int vs[kXnMaxN + 1];
 };
+
+static_assert(sizeof(XnWarpSmem) % 16 == 0, "per-warp blocks stay 16-byte aligned");
 
 // stack entries (doubles) for order n: the kept-pivot matrices of depths 1..D-1 (D = n - S)
 __host__ __device__ constexpr size_t xn_stack_entries(int n) {
