@@ -89,7 +89,8 @@ def parse():
                     help="skip the per-row measurements of the other hot-path steps")
     ap.add_argument("--mc-steps", type=int, default=100)
     ap.add_argument("--case", default=None,
-                    choices=["cdet_n12", "cdet_n16", "keldysh_n12", "ppm_n14", "cdet_uneven", "xnor_n12"],
+                    choices=["cdet_n12", "cdet_n16", "keldysh_n12", "ppm_n14", "cdet_uneven", "xnor_n12",
+                             "nand_n10"],
                     help="run 3 launches of one kernel on a small case (for profiling) and exit")
     return ap.parse_args()
 
@@ -163,6 +164,14 @@ def xnor_flops(n: int) -> int:
     a kept child of size m2 = 2(n-l-1), the Schur update (4 m2^2), the row factors
     C P^-1 (6 m2) and the pivot determinant, inverse and node product (9)."""
     return sum((1 << l) * (4 * (2 * (n - l - 1)) ** 2 + 12 * (n - l - 1) + 9) for l in range(n))
+
+
+def nand_flops(n: int) -> int:
+    """Algorithmic flops of all NAND minors of a 2n x 2n matrix (the ternary
+    tree): per node two kept children of size m2 = 2(n-l-1), each the rank-1
+    Schur update (2 m2^2), its row factors (m2) and the pivot reciprocal and
+    node product (3)."""
+    return sum(3 ** l * 2 * (2 * (2 * (n - l - 1)) ** 2 + 2 * (n - l - 1) + 3) for l in range(n))
 
 
 def sc_flops(n: int) -> int:
@@ -243,6 +252,17 @@ def measure_rows(args, dev, peak):
         "xnor_minors_ms": ms_x, "xnor_minors_tflops": 65536 * xnor_flops(12) / (ms_x * 1e-3) / 1e12,
         "launch": "XNOR-minor kernel, then the CDet recursion on the minors"}
     del M, xm
+    # next (Sections III.C, V.C): CDet summed over two vertex types, 16384 Hubbard
+    # matrices of order 10 with a shifted second vertex type: NAND minors summed
+    # over the types of each subset, then the CDet recursion
+    M = torch.as_tensor(inputs.two_type_batch(16384, 10, seed=7)).to(dev)
+    ms = _event_ms(lambda: apm.two_type_cdet(M))
+    fl = 16384 * (nand_flops(10) + sc_flops(10))
+    rows["two_type_cdet_16384_n10"] = {
+        "value": 16384 / (ms * 1e-3), "unit": "minor-sets/s", "ms": ms,
+        "tflops": fl / (ms * 1e-3) / 1e12, "frac_fp64_peak": fl / (ms * 1e-3) / 1e12 / peak,
+        "launch": "NAND-minor kernel (type sums), then the CDet recursion"}
+    del M
     # a8: learned proposal vs plain, 16384 walkers at each order 10..14
     G = torch.as_tensor(inputs.hubbard_g0_table()).to(dev)
     W, T = 16384, args.mc_steps
@@ -366,6 +386,9 @@ def profile_case(name: str):
     elif name == "xnor_n12":
         M = torch.as_tensor(inputs.nambu_batch(8192, 12, seed=6)).to(dev)
         run = lambda: apm.xnor_minors(M)
+    elif name == "nand_n10":
+        M = torch.as_tensor(inputs.two_type_batch(16384, 10, seed=7)).to(dev)
+        run = lambda: apm.two_type_cdet(M)
     elif name == "ppm_n14":
         P = torch.as_tensor(inputs.perm_batch(14, 1368, seed=4)).to(dev)
         run = lambda: apm.perm_minors(P)
