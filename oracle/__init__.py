@@ -66,6 +66,8 @@ def _load():
                 "oracle_xnor_minors": [P, i32, i64, P, i32],
                 "oracle_xnor_scale": [P, i32, i64, i32, P, i32],
                 "oracle_nand": [P, i32, i64, P, P, P, i32],
+                "oracle_keldysh2": [P, P, i32, i64, i32, P, P, i32],
+                "oracle_keldysh2_scale": [P, P, i32, i64, P, i32],
             }.items():
                 f = getattr(lib, name)
                 f.argtypes = args
@@ -250,3 +252,33 @@ def nand(M, minors: bool = False, nthreads: int = 0):
     if minors:
         res.append(out3[0] if single else out3)
     return tuple(res)
+
+
+def keldysh2(Mu, Md, signed: bool = False, partial: bool = False, nthreads: int = 0):
+    """Two-spin Keldysh sum: sum over alpha of det(Mu_alpha) det(Md_alpha);
+    returns the complex sums (batch,) and, if partial, the per-depth sums."""
+    Mu, single = _mat_batch(Mu, np.complex128)
+    Md, _ = _mat_batch(Md, np.complex128)
+    assert Mu.shape == Md.shape
+    b, n2, _ = Mu.shape
+    n = n2 // 2
+    s = np.empty((b, 2))
+    p = np.empty((b, n + 1, 2)) if partial else None
+    _load().oracle_keldysh2(Mu.ctypes.data, Md.ctypes.data, n, b, int(signed), s.ctypes.data,
+                            p.ctypes.data if partial else None, nthreads)
+    s = s[:, 0] + 1j * s[:, 1]
+    if partial:
+        p = p[..., 0] + 1j * p[..., 1]
+        return (s[0], p[0]) if single else (s, p)
+    return s[0] if single else s
+
+
+def keldysh2_scale(Mu, Md, nthreads: int = 0) -> np.ndarray:
+    """Rounding scale of the two-spin sum: sum over alpha of the products of the
+    two row-sum bounds."""
+    Mu, single = _mat_batch(Mu, np.complex128)
+    Md, _ = _mat_batch(Md, np.complex128)
+    b, n2, _ = Mu.shape
+    out = np.empty(b)
+    _load().oracle_keldysh2_scale(Mu.ctypes.data, Md.ctypes.data, n2 // 2, b, out.ctypes.data, nthreads)
+    return out[0] if single else out

@@ -24,7 +24,10 @@
  *                        the Nambu CDet of Section V.B), one elimination each;
  *   - NAND minors:       the 3^n submatrices keeping one or neither row and
  *                        column of each block (Section III.C) and their sums
- *                        over the two types of each kept vertex (Section V.C).
+ *                        over the two types of each kept vertex (Section V.C);
+ *   - two-spin Keldysh:  the sum over the 2^n assignments shared by both spins
+ *                        of the product of the two determinants (Section V.D
+ *                        with the two determinants of Eq. CTINT).
  *
  * Subsets are bit masks: element k (0-based) <-> bit k (Section II, the
  * subset labelling S_i by the binary digits of i). Matrices are row-major.
@@ -492,5 +495,73 @@ void oracle_nand(const double *M, int n, int64_t batch, double *out3, double *ab
             if (abar) abar[b * N + S] += det;
             if (scale) scale[b * N + S] += bound;
         }
+    }
+}
+
+/* Two-spin Keldysh sum (Section V.D with the two determinants of Eq. CTINT):
+ * sum over the 2^n assignments alpha shared by both spins of
+ * det(M_up,alpha) det(M_dn,alpha), each determinant by its own complex
+ * partial-pivot elimination; partial[d] (if not NULL) is the same sum over the
+ * first d vertices only (leading blocks), partial[0] = 1. signed_ weights each
+ * assignment by (-1)^{number of - indices} once. */
+void oracle_keldysh2(const double *Mu, const double *Md, int n, int64_t batch, int signed_, double *sum,
+                     double *partial, int nthreads) {
+#pragma omp parallel for schedule(dynamic, 1) num_threads(threads_for(nthreads))
+    for (int64_t b = 0; b < batch; ++b) {
+        const double complex *U = (const double complex *)Mu + b * (int64_t)(2 * n) * (2 * n);
+        const double complex *Dn = (const double complex *)Md + b * (int64_t)(2 * n) * (2 * n);
+        double complex A[MAXN * MAXN], B[MAXN * MAXN];
+        for (int d = (partial ? 0 : n); d <= n; ++d) {
+            double complex acc = 0.0;
+            for (int64_t al = 0; al < ((int64_t)1 << d); ++al) {
+                for (int i = 0; i < d; ++i)
+                    for (int j = 0; j < d; ++j) {
+                        int ri = 2 * i + (int)((al >> i) & 1);
+                        int cj = 2 * j + (int)((al >> j) & 1);
+                        A[i * d + j] = U[ri * (2 * n) + cj];
+                        B[i * d + j] = Dn[ri * (2 * n) + cj];
+                    }
+                double complex v = cdet_partial_pivot(A, d) * cdet_partial_pivot(B, d);
+                if (signed_ && (popcount_u32((uint32_t)al) & 1)) v = -v;
+                acc += v;
+            }
+            if (partial) {
+                partial[(b * (n + 1) + d) * 2 + 0] = creal(acc);
+                partial[(b * (n + 1) + d) * 2 + 1] = cimag(acc);
+            }
+            if (d == n) {
+                sum[b * 2 + 0] = creal(acc);
+                sum[b * 2 + 1] = cimag(acc);
+            }
+        }
+    }
+}
+
+/* Error scale for the two-spin sum: sum over alpha of the product of the two
+ * row-sum bounds prod_i sum_j |(M_sigma,alpha)_ij| (>= the absolute Leibniz
+ * terms of the product of the two determinants). */
+void oracle_keldysh2_scale(const double *Mu, const double *Md, int n, int64_t batch, double *scale,
+                           int nthreads) {
+#pragma omp parallel for schedule(dynamic, 1) num_threads(threads_for(nthreads))
+    for (int64_t b = 0; b < batch; ++b) {
+        const double complex *U = (const double complex *)Mu + b * (int64_t)(2 * n) * (2 * n);
+        const double complex *Dn = (const double complex *)Md + b * (int64_t)(2 * n) * (2 * n);
+        double acc = 0.0;
+        for (int64_t al = 0; al < ((int64_t)1 << n); ++al) {
+            double pu = 1.0, pd = 1.0;
+            for (int i = 0; i < n; ++i) {
+                double su = 0.0, sd = 0.0;
+                const int ri = 2 * i + (int)((al >> i) & 1);
+                for (int j = 0; j < n; ++j) {
+                    const int cj = 2 * j + (int)((al >> j) & 1);
+                    su += cabs(U[ri * (2 * n) + cj]);
+                    sd += cabs(Dn[ri * (2 * n) + cj]);
+                }
+                pu *= su;
+                pd *= sd;
+            }
+            acc += pu * pd;
+        }
+        scale[b] = acc;
     }
 }

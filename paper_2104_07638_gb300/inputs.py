@@ -179,8 +179,9 @@ KEL_MT = 1 << 14
 
 @functools.lru_cache(maxsize=None)
 def keldysh_g0_tables(beta: float = KEL_BETA, L: int = KEL_L, win: int = KEL_WIN,
-                      tmax: float = KEL_TMAX, mt: int = KEL_MT):
-    """G^<(x,t) and G^>(x,t) of a free 1D chain (eps_k = -2 cos k, mu = 0):
+                      tmax: float = KEL_TMAX, mt: int = KEL_MT, shift: float = 0.0):
+    """G^<(x,t) and G^>(x,t) of a free 1D chain (eps_k = -2 cos k + shift, mu = 0;
+    shift = +-h is a Zeeman field for the two spins):
         G^<(x,t) = +(i/L) sum_k e^{i(kx - eps_k t)} f(eps_k)
         G^>(x,t) = -(i/L) sum_k e^{i(kx - eps_k t)} (1 - f(eps_k))
     for |x| < win and t = d*tmax/mt, d in [-(mt-1), mt-1]. Returns two complex
@@ -188,7 +189,7 @@ def keldysh_g0_tables(beta: float = KEL_BETA, L: int = KEL_L, win: int = KEL_WIN
     half = np.arange(L // 2 + 1)
     wk = np.where((half == 0) | (half == L // 2), 1.0, 2.0)
     k = 2.0 * np.pi * half / L
-    eps = -2.0 * np.cos(k)
+    eps = -2.0 * np.cos(k) + shift
     f = 1.0 / (np.exp(beta * eps) + 1.0)
     x = np.arange(win)
     C = np.cos(np.outer(x, k)) * wk[None, :] / float(L)               # (win, K)
@@ -208,13 +209,13 @@ def keldysh_vertices(batch: int, n: int, seed: int = 3, win: int = KEL_WIN,
     return x, m
 
 
-def keldysh_matrices_from_vertices(x, m, mt: int = KEL_MT) -> np.ndarray:
+def keldysh_matrices_from_vertices(x, m, mt: int = KEL_MT, shift: float = 0.0) -> np.ndarray:
     """2n x 2n complex block matrices; block (i,j) sits at rows 2i,2i+1 (Keldysh
     index +,-) and columns 2j,2j+1:
         [[G^{++}, G^{+-}], [G^{-+}, G^{--}]](x_i - x_j, t_i - t_j),
     G^{++}(t) = theta(t) G^>(t) + theta(-t) G^<(t), G^{--}(t) = theta(t) G^<(t) + theta(-t) G^>(t),
     G^{+-} = G^<, G^{-+} = G^>; at equal times (the diagonal blocks) G^{++} = G^{--} = G^<."""
-    Gl, Gg = keldysh_g0_tables(mt=mt)
+    Gl, Gg = keldysh_g0_tables(mt=mt, shift=shift)
     batch, n = x.shape
     dx = np.abs(x[:, :, None] - x[:, None, :])
     dm = m[:, :, None] - m[:, None, :]
@@ -342,3 +343,15 @@ def two_type_batch(batch: int = 4096, n: int = 10, seed: int = 7) -> np.ndarray:
     dy = np.abs(ys[:, :, None] - ys[:, None, :])
     dt = ms[:, :, None] - ms[:, None, :] + (HUB_MTAU - 1)
     return np.ascontiguousarray(G[dx, dy, dt])
+
+
+# --- two spins under one Keldysh assignment (Section V.D with Eq. CTINT) -------
+KEL_ZEEMAN = 0.5
+
+
+def keldysh2_batch(batch: int, n: int, seed: int = 8, h: float = KEL_ZEEMAN):
+    """Two Keldysh block matrices per vertex set, (up, down), each (batch, 2n, 2n)
+    complex128: the chain of keldysh_batch with the energies shifted by -h (up)
+    and +h (down), the same vertices for both spins."""
+    x, m = keldysh_vertices(batch, n, seed)
+    return keldysh_matrices_from_vertices(x, m, shift=-h), keldysh_matrices_from_vertices(x, m, shift=h)

@@ -531,3 +531,55 @@ def test_two_type_inputs_conventions():
     G = I.hubbard_g0_table(win=I.HUB_WIN + 1)
     assert np.allclose(M[:, 0, 1], G[1, 0, I.HUB_MTAU - 1])
     assert np.allclose(np.diagonal(M, axis1=1, axis2=2), G[0, 0, I.HUB_MTAU - 1])
+
+
+# --- two-spin Keldysh sums (Section V.D with Eq. CTINT) -------------------------
+
+def test_keldysh2_vs_numpy_bruteforce():
+    rng = np.random.default_rng(2201)
+    for n in (1, 3, 5):
+        Mu = rng.standard_normal((2 * n, 2 * n)) + 1j * rng.standard_normal((2 * n, 2 * n))
+        Md = rng.standard_normal((2 * n, 2 * n)) + 1j * rng.standard_normal((2 * n, 2 * n))
+        for signed in (False, True):
+            ref = 0.0
+            for al in itertools.product([0, 1], repeat=n):
+                idx = [2 * i + a for i, a in enumerate(al)]
+                v = np.linalg.det(Mu[np.ix_(idx, idx)]) * np.linalg.det(Md[np.ix_(idx, idx)])
+                ref += -v if (signed and sum(al) % 2) else v
+            got = oracle.keldysh2(Mu, Md, signed=signed)
+            assert abs(got - ref) <= 1e-12 * max(1.0, abs(ref)), (n, signed)
+
+
+def test_keldysh2_identity_partner_is_single_spin_sum():
+    """With the identity as the second matrix every M_dn,alpha is the identity,
+    so the two-spin sum is the (independently pinned) single-spin Keldysh sum."""
+    Mu = I.keldysh_batch(2, 6, seed=2202)
+    Md = np.broadcast_to(np.eye(12, dtype=np.complex128), Mu.shape).copy()
+    for signed in (False, True):
+        a = oracle.keldysh2(Mu, Md, signed=signed)
+        b = oracle.keldysh(Mu, signed=signed)
+        assert np.all(np.abs(a - b) <= 1e-12 * np.maximum(1.0, np.abs(b)))
+
+
+def test_keldysh2_equal_blocks_and_largest_time():
+    rng = np.random.default_rng(2203)
+    n = 6
+    gu = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)) + 3 * np.eye(n)
+    gd = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)) + 3 * np.eye(n)
+    s = oracle.keldysh2(np.kron(gu, np.ones((2, 2))), np.kron(gd, np.ones((2, 2))))
+    ref = 2 ** n * np.linalg.det(gu) * np.linalg.det(gd)
+    assert abs(s - ref) <= 1e-11 * abs(ref)
+    # causal contour: both rows of the latest vertex agree in each spin, so the
+    # sign-weighted sum over the shared assignment vanishes
+    Mu, Md = I.keldysh2_batch(3, 7, seed=2204)
+    sg = oracle.keldysh2(Mu, Md, signed=True)
+    assert np.all(np.abs(sg) <= 1e-12 * oracle.keldysh2_scale(Mu, Md))
+
+
+def test_keldysh2_partial_sums_are_leading_blocks():
+    Mu, Md = I.keldysh2_batch(2, 5, seed=2205)
+    s, p = oracle.keldysh2(Mu, Md, partial=True)
+    assert np.all(p[:, 0] == 1.0) and np.array_equal(p[:, 5], s)
+    for d in range(1, 5):
+        ref = oracle.keldysh2(Mu[:, :2 * d, :2 * d], Md[:, :2 * d, :2 * d])
+        assert np.all(np.abs(p[:, d] - ref) <= 1e-13 * np.maximum(1.0, np.abs(ref)))
