@@ -233,6 +233,27 @@ apm_status_t apm_keldysh_sum(const double *Mt, int n, int64_t batch, int flags, 
                              size_t workspace_bytes, apm_stream_t stream);
 
 /*
+ * apm_keldysh2_sum -- the Keldysh sum for two spins under one shared assignment
+ * (Section V.D with the two determinants per configuration of Eq. CTINT):
+ *   sum[b] = sum over alpha in {+,-}^n of det(Mu_b,alpha) det(Md_b,alpha),
+ * one binary tree of Schur complements walked for both matrices at once.
+ *   Mu, Md   [batch][2n][2n] complex128 each (up and down spin), laid out as
+ *            for apm_keldysh_sum.
+ *   n        1..APM_MAX_N_KELDYSH.     flags  0 or APM_KELDYSH_SIGNED (the
+ *            weight (-1)^{number of -} is applied once per assignment).
+ *   sum      [batch][2] float64 output; partial [batch][n+1][2] or NULL: the same
+ *            sum over the first d vertices (the lower orders), partial[b][0] = 1.
+ *   status   [batch] or NULL; APM_ST_ZERO_PIVOT marks a zero or non-finite pivot
+ *            in either spin, and then that pair's results are NaN.
+ *   workspace / workspace_bytes: scratch for the depth-first part (both spins'
+ *            path matrices), needed for n > 7 (apm_workspace_size with
+ *            APM_OP_KELDYSH2).
+ */
+apm_status_t apm_keldysh2_sum(const double *Mu, const double *Md, int n, int64_t batch, int flags, double *sum,
+                              double *partial, uint32_t *status, void *workspace, size_t workspace_bytes,
+                              apm_stream_t stream);
+
+/*
  * apm_keldysh_sum_noalloc -- the same sum as apm_keldysh_sum, for callers that
  * cannot allocate device memory around the call: programs that hand all device
  * memory to their own pool allocator and forbid cudaMalloc inside their
@@ -282,6 +303,7 @@ apm_status_t apm_perm_minors(const double *A, int n, int64_t batch, double *perm
 #define APM_OP_NAMBU_CDET 9
 #define APM_OP_NAND_MINORS 10
 #define APM_OP_TWO_TYPE_CDET 11
+#define APM_OP_KELDYSH2 12
 
 /*
  * apm_cdet_connected_varlen -- apm_cdet_connected for a batch of matrices of

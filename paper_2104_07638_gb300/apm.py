@@ -25,8 +25,8 @@ ST_PIVOT_CORRECTED, ST_NONFINITE_INPUT, ST_ZERO_PIVOT, ST_CORRECTION_OVERFLOW = 
 CDET_SINGLE_DET = 1
 KELDYSH_SIGNED = 1
 OP_ALL_MINORS, OP_CDET, OP_CDET_FROM_WEIGHTS, OP_PERM_MINORS, OP_CDET_VARLEN, OP_KELDYSH, \
-    OP_KELDYSH_VARLEN, OP_XNOR_MINORS, OP_NAMBU_CDET, OP_NAND_MINORS, OP_TWO_TYPE_CDET = \
-    1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11
+    OP_KELDYSH_VARLEN, OP_XNOR_MINORS, OP_NAMBU_CDET, OP_NAND_MINORS, OP_TWO_TYPE_CDET, OP_KELDYSH2 = \
+    1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12
 ST_BAD_ORDER = 16
 
 
@@ -70,6 +70,7 @@ def lib():
                 "apm_nambu_cdet": [P, i32, i64, P, P, P, P, sz, P],
                 "apm_nand_minors": [P, i32, i64, P, P, P, sz, P],
                 "apm_two_type_cdet": [P, i32, i64, P, P, P, P, sz, P],
+                "apm_keldysh2_sum": [P, P, i32, i64, i32, P, P, P, P, sz, P],
                 "apm_cdet_tune_set": [P],
                 "apm_cdet_tune_get": [i32, ctypes.POINTER(ctypes.c_uint64)],
                 "apm_workspace_size": [i32, i32, i64, i32, ctypes.POINTER(sz)],
@@ -296,6 +297,29 @@ def two_type_cdet(M: torch.Tensor, return_weights=False, return_status=False):
     res = [c]
     if return_weights:
         res.append(abar)
+    if return_status:
+        res.append(st)
+    return res[0] if len(res) == 1 else tuple(res)
+
+
+def keldysh2_sum(Mu: torch.Tensor, Md: torch.Tensor, signed=False, partial=False, return_status=False):
+    """Two-spin Keldysh sum (apm_keldysh2_sum): sum over the shared assignments
+    of det(Mu_alpha) det(Md_alpha); Mu, Md (batch, 2n, 2n) complex128."""
+    Mu = _mat_batch(Mu, torch.complex128, "Mu")
+    Md = _mat_batch(Md, torch.complex128, "Md")
+    if Mu.shape != Md.shape or Mu.shape[1] % 2:
+        raise ValueError("Mu and Md must both be (batch, 2n, 2n)")
+    b, n = Mu.shape[0], Mu.shape[1] // 2
+    dev = Mu.device
+    s = torch.empty((b, 2), dtype=torch.float64, device=dev)
+    p = torch.empty((b, n + 1, 2), dtype=torch.float64, device=dev) if partial else None
+    st = torch.zeros(b, dtype=torch.int32, device=dev) if return_status else None
+    ws, nb = _workspace(OP_KELDYSH2, n, b, dev)
+    _check(lib().apm_keldysh2_sum(_ptr(Mu), _ptr(Md), n, b, KELDYSH_SIGNED if signed else 0, _ptr(s), _ptr(p),
+                                  _ptr(st), _ptr(ws), nb, _stream(Mu)), "apm_keldysh2_sum")
+    res = [torch.view_as_complex(s)]
+    if partial:
+        res.append(torch.view_as_complex(p))
     if return_status:
         res.append(st)
     return res[0] if len(res) == 1 else tuple(res)

@@ -196,6 +196,24 @@ apm_status_t apm_two_type_cdet(const double *M, int n, int64_t batch, double *ab
     return cdet_common(a, workspace, workspace_bytes, s);
 }
 
+apm_status_t apm_keldysh2_sum(const double *Mu, const double *Md, int n, int64_t batch, int flags, double *sum,
+                              double *partial, uint32_t *status, void *workspace, size_t workspace_bytes,
+                              apm_stream_t stream) {
+    if (n < 1 || n > APM_MAX_N_KELDYSH) return APM_ERR_UNSUPPORTED_N;
+    if (batch < 0 || (flags & ~APM_KELDYSH_SIGNED)) return APM_ERR_ARG;
+    apm_status_t st;
+    if ((st = check_ptr(Mu, batch)) || (st = check_ptr(Md, batch)) || (st = check_ptr(sum, batch)) ||
+        (st = check_opt_ptr(partial)) || (st = check_opt_ptr(status)))
+        return st;
+    if (batch == 0) return APM_OK;
+    size_t need = 0;
+    if ((st = apm_workspace_size(APM_OP_KELDYSH2, n, batch, 0, &need))) return st;
+    if (need > 0 && (!workspace || workspace_bytes < need || !aligned16(workspace))) return APM_ERR_WORKSPACE;
+    const int e = apm::launch_keldysh2(Mu, Md, n, batch, (flags & APM_KELDYSH_SIGNED) ? 1 : 0, sum, partial, status,
+                                       workspace, reinterpret_cast<cudaStream_t>(stream));
+    return e ? cuda_fail(e) : APM_OK;
+}
+
 apm_status_t apm_keldysh_sum(const double *Mt, int n, int64_t batch, int flags, double *sum,
                              double *partial, uint32_t *status, void *workspace,
                              size_t workspace_bytes, apm_stream_t stream) {
@@ -367,6 +385,13 @@ apm_status_t apm_workspace_size(int op, int n_max, int64_t batch, int two_mats, 
             }
             *bytes = need;
             return APM_OK;
+        }
+        case APM_OP_KELDYSH2: {
+            if (n_max < 1 || n_max > APM_MAX_N_KELDYSH) return APM_ERR_UNSUPPORTED_N;
+            if (batch == 0) return APM_OK;
+            int err = 0;
+            *bytes = apm::keldysh2_workspace_bytes(n_max, batch, &err);
+            return err ? cuda_fail(err) : APM_OK;
         }
         case APM_OP_PERM_MINORS:
             if (n_max < 1 || n_max > APM_MAX_N_PERM) return APM_ERR_UNSUPPORTED_N;

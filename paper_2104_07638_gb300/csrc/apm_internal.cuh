@@ -93,6 +93,12 @@ size_t xnor_workspace_bytes(int n, int64_t batch, int *err);
 int launch_xnor(const double *M, int n, int64_t batch, double *minors, uint32_t *status, void *workspace,
                 cudaStream_t s);
 
+// Two-spin Keldysh sums (one warp per matrix pair).
+int keldysh2_grid(int64_t batch, int *err);
+size_t keldysh2_workspace_bytes(int n, int64_t batch, int *err);
+int launch_keldysh2(const double *Mu, const double *Md, int n, int64_t batch, int sgn, double *sum,
+                    double *partial, uint32_t *status, void *workspace, cudaStream_t s);
+
 // NAND minors (type_sums = false: all 3^n per matrix) or their sums over the
 // two vertex types (type_sums = true: 2^n per matrix); one warp per matrix.
 int nand_grid(int64_t batch, int *err);

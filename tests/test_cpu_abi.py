@@ -115,3 +115,15 @@ def test_nand_and_two_type_argument_errors(lib):
     assert g(fake, 17, 1, fake, fake, None, None, 0, None) == 2
     assert g(fake, 16, -1, fake, fake, None, None, 0, None) == 1
     assert g(fake, 6, 1, fake, None, None, None, 0, None) == 1
+
+
+def test_keldysh2_argument_errors(lib):
+    P, i32, i64, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_size_t
+    fake = ctypes.c_void_p(1 << 20)
+    f = lib.apm_keldysh2_sum
+    f.argtypes = [P, P, i32, i64, i32, P, P, P, P, sz, P]
+    f.restype = ctypes.c_int
+    assert f(fake, fake, 17, 1, 0, fake, None, None, None, 0, None) == 2
+    assert f(fake, None, 6, 1, 0, fake, None, None, None, 0, None) == 1      # missing second spin
+    assert f(fake, fake, 6, 1, 2, fake, None, None, None, 0, None) == 1      # unknown flag
+    assert f(None, None, 6, 0, 0, None, None, None, None, 0, None) == 0
