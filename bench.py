@@ -90,7 +90,7 @@ def parse():
     ap.add_argument("--mc-steps", type=int, default=100)
     ap.add_argument("--case", default=None,
                     choices=["cdet_n12", "cdet_n16", "keldysh_n12", "ppm_n14", "cdet_uneven", "xnor_n12",
-                             "nand_n10"],
+                             "nand_n10", "keldysh2_n12"],
                     help="run 3 launches of one kernel on a small case (for profiling) and exit")
     return ap.parse_args()
 
@@ -164,6 +164,12 @@ def xnor_flops(n: int) -> int:
     a kept child of size m2 = 2(n-l-1), the Schur update (4 m2^2), the row factors
     C P^-1 (6 m2) and the pivot determinant, inverse and node product (9)."""
     return sum((1 << l) * (4 * (2 * (n - l - 1)) ** 2 + 12 * (n - l - 1) + 9) for l in range(n))
+
+
+def keldysh2_flops(n: int) -> int:
+    """Algorithmic flops of one two-spin Keldysh sum: both spins' XOR trees
+    (2 keldysh_flops) plus the extra complex product per node and per leaf."""
+    return 2 * keldysh_flops(n) + 6 * (2 ** (n + 1) - 2) + 8 * 2 ** n
 
 
 def nand_flops(n: int) -> int:
@@ -252,6 +258,16 @@ def measure_rows(args, dev, peak):
         "xnor_minors_ms": ms_x, "xnor_minors_tflops": 65536 * xnor_flops(12) / (ms_x * 1e-3) / 1e12,
         "launch": "XNOR-minor kernel, then the CDet recursion on the minors"}
     del M, xm
+    # next (Section V.D with Eq. CTINT): two-spin Keldysh sums of 16384 chain pairs
+    # of order 12 (Zeeman-split spins, one shared assignment)
+    Mu, Md = inputs.keldysh2_batch(16384, 12, seed=8)
+    Mu, Md = torch.as_tensor(Mu).to(dev), torch.as_tensor(Md).to(dev)
+    ms = _event_ms(lambda: apm.keldysh2_sum(Mu, Md))
+    fl = 16384 * keldysh2_flops(12)
+    rows["keldysh2_16384_n12"] = {
+        "value": 16384 / (ms * 1e-3), "unit": "sums/s", "ms": ms,
+        "tflops": fl / (ms * 1e-3) / 1e12, "frac_fp64_peak": fl / (ms * 1e-3) / 1e12 / peak}
+    del Mu, Md
     # next (Sections III.C, V.C): CDet summed over two vertex types, 16384 Hubbard
     # matrices of order 10 with a shifted second vertex type: NAND minors summed
     # over the types of each subset, then the CDet recursion
@@ -386,6 +402,10 @@ def profile_case(name: str):
     elif name == "xnor_n12":
         M = torch.as_tensor(inputs.nambu_batch(8192, 12, seed=6)).to(dev)
         run = lambda: apm.xnor_minors(M)
+    elif name == "keldysh2_n12":
+        Mu, Md = inputs.keldysh2_batch(8192, 12, seed=8)
+        Mu, Md = torch.as_tensor(Mu).to(dev), torch.as_tensor(Md).to(dev)
+        run = lambda: apm.keldysh2_sum(Mu, Md)
     elif name == "nand_n10":
         M = torch.as_tensor(inputs.two_type_batch(16384, 10, seed=7)).to(dev)
         run = lambda: apm.two_type_cdet(M)
