@@ -406,8 +406,8 @@ apm_status_t apm_mc_accept(int32_t *X, const int32_t *Xp, double *weight, double
                            const float *u2, int n, int32_t *accepted, apm_stream_t stream);
 
 /* Surrogate network: in 64 -> 256 -> 256 -> 256 -> 1 with ReLU, BF16 weights
- * and activations, FP32 accumulation (mma.sync BF16 tensor-core tiles), FP32
- * master weights and Adam moments. Parameter layout (APM_MLP_PARAMS floats):
+ * and activations, FP32 accumulation (tcgen05 tensor-core GEMMs fed by TMA),
+ * FP32 master weights and Adam moments. Parameter layout (APM_MLP_PARAMS floats):
  * W1 [256][64], b1 [256], W2 [256][256], b2, W3 [256][256], b3, w4 [256], b4 [1],
  * 7 floats padding; weight matrices stored [out][in]. All buffers device memory
  * owned by the caller. */
@@ -422,8 +422,25 @@ typedef struct {
     float *adam_v;         /* [APM_MLP_PARAMS] */
 } apm_mlp;
 
-/* scratch for a batch of batch_padded rows (a multiple of 64) */
+/* scratch for a batch of batch_padded rows (a multiple of 64). Its first four
+ * bytes are a status word that the GEMMs OR flags into: zero them before the
+ * first use (apm_mlp_status reads and clears them). */
 apm_status_t apm_mlp_workspace_size(int batch_padded, size_t *bytes);
+/* Synchronises `stream`, stores the workspace's status word in *flags (host,
+ * nullable) and clears it. Bit 0: a bounded wait inside a tensor-core GEMM gave
+ * up after one second (its tile was not written); returns APM_ERR_TIMEOUT then,
+ * else APM_OK. */
+apm_status_t apm_mlp_status(void *workspace, size_t workspace_bytes, uint32_t *flags, apm_stream_t stream);
+/* The network's GEMM on its own: C[M][N] = A[M][K] * Bt[N][K]^T (+ bias[N])
+ * (ReLU if relu), BF16 operands (K contiguous in both), FP32 accumulation;
+ * writes C32 (FP32) and/or Cb (BF16) when not NULL. N and K multiples of 64,
+ * M >= 1, every pointer 16-byte aligned device memory; the workspace is one
+ * sized for any batch (its status word and split-K partials are used).
+ * A product with a plain FP32 result and a long K may split K: its slices are
+ * added in a fixed order (same result on every call). */
+apm_status_t apm_mlp_gemm_tn(const uint16_t *A, const uint16_t *Bt, const float *bias, float *C32, uint16_t *Cb,
+                             int M, int N, int K, int relu, void *workspace, size_t workspace_bytes,
+                             apm_stream_t stream);
 /* refresh param_bf16 from param (after the caller initialises param) */
 apm_status_t apm_mlp_sync_bf16(const apm_mlp *net, apm_stream_t stream);
 /* y[b] (FP32) = network(X[b]) for b < batch_padded; X [batch_padded][64] BF16 */

@@ -139,9 +139,17 @@ struct MlpParams {
     const float *b1, *b2, *b3, *b4;
 };
 struct MlpWork {
+    uint32_t *err;  // bit 0: a bounded wait of the tensor-core GEMM gave up
+    float *part;    // split-K partial tiles
     __nv_bfloat16 *h1, *h2, *h3, *dzb, *t1, *t2, *wt;
     float *y, *dy, *dz32, *dh32;
 };
+// C = A * Bt^T (+ bias) (ReLU) on the tensor cores; part (part_floats) holds
+// split-K partials when K is long next to M x N
+size_t tc_gemm_split_floats();
+int launch_tc_gemm_tn(const __nv_bfloat16 *A, const __nv_bfloat16 *Bt, const float *bias, float *C32,
+                      __nv_bfloat16 *Cb, int M, int N, int K, int relu, float *part, size_t part_floats,
+                      uint32_t *err, cudaStream_t s);
 size_t mlp_workspace_bytes(int Bp);
 void mlp_bind(const apm_mlp *net, MlpParams &P);
 void mlp_work(void *ws, int Bp, MlpWork &w);

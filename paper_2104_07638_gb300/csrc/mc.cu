@@ -246,4 +246,33 @@ apm_status_t apm_mlp_train_step(const apm_mlp *net, const uint16_t *X, const flo
                : APM_OK;
 }
 
+apm_status_t apm_mlp_status(void *workspace, size_t workspace_bytes, uint32_t *flags, apm_stream_t stream) {
+    if (!workspace || workspace_bytes < mlp_workspace_bytes(0)) return APM_ERR_WORKSPACE;
+    uint32_t v = 0;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaMemcpyAsync(&v, workspace, sizeof(v), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemsetAsync(workspace, 0, sizeof(v), s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+        return APM_ERR_CUDA;
+    if (flags) *flags = v;
+    return v ? APM_ERR_TIMEOUT : APM_OK;
+}
+
+apm_status_t apm_mlp_gemm_tn(const uint16_t *A, const uint16_t *Bt, const float *bias, float *C32, uint16_t *Cb,
+                             int M, int N, int K, int relu, void *workspace, size_t workspace_bytes,
+                             apm_stream_t stream) {
+    if (!A || !Bt || (!C32 && !Cb) || M < 1 || N < 64 || K < 64 || N % 64 || K % 64) return APM_ERR_ARG;
+    if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(Bt) |
+         reinterpret_cast<uintptr_t>(C32) | reinterpret_cast<uintptr_t>(Cb)) &
+        15)
+        return APM_ERR_ARG;
+    if (!workspace || workspace_bytes < mlp_workspace_bytes(0)) return APM_ERR_WORKSPACE;
+    MlpWork w;
+    mlp_work(workspace, 0, w);
+    return launch_tc_gemm_tn(reinterpret_cast<const __nv_bfloat16 *>(A), reinterpret_cast<const __nv_bfloat16 *>(Bt),
+                             bias, C32, reinterpret_cast<__nv_bfloat16 *>(Cb), M, N, K, relu, w.part,
+                             tc_gemm_split_floats(), w.err, reinterpret_cast<cudaStream_t>(stream))
+               ? APM_ERR_CUDA
+               : APM_OK;
+}
+
 }  // extern "C"

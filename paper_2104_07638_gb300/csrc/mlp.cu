@@ -2,11 +2,10 @@
 // (in 64 -> 256 -> 256 -> 256 -> 1, ReLU) with BF16 weights and activations,
 // FP32 accumulation and FP32 master weights trained by Adam.
 //
-// GEMMs are "TN": C[M x N] = A[M x K] * Bt[N x K]^T (both operands K-contiguous
-// BF16), computed with warp-level mma.sync m16n8k16 BF16 -> FP32 on 64x64 CTA
-// tiles (4 warps, 32x32 each), K staged through shared memory in steps of 32.
-// M, N multiples of 64, K a multiple of 32. The network is tiny next to the
-// FP64 minor kernels; these kernels only need to be correct and cheap.
+// GEMMs are "TN": C[M x N] = A[M x K] * Bt[N x K]^T with both operands
+// K-contiguous BF16, on the tensor cores (tcgen05, tc_gemm.cu); the forms that
+// need a transposed operand get it from transpose_bf16_kernel. M a multiple of
+// 64, N of 64, K of 64. The network is tiny next to the FP64 minor kernels.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -14,96 +13,6 @@
 #include "apm_internal.cuh"
 
 namespace apm {
-
-constexpr int kTile = 64;
-constexpr int kKStep = 32;
-constexpr int kPad = 8;  // bf16 padding per shared row (bank-conflict relief)
-
-__device__ __forceinline__ uint32_t ld_pair(const __nv_bfloat16 *p) {
-    return *reinterpret_cast<const uint32_t *>(p);
-}
-
-__device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
-                                         uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-// C = A * Bt^T (+ bias) (ReLU if relu); writes C32 (if not NULL) and Cb (bf16, if not NULL)
-__global__ void __launch_bounds__(128) gemm_tn_kernel(const __nv_bfloat16 *__restrict__ A,
-                                                      const __nv_bfloat16 *__restrict__ Bt,
-                                                      const float *__restrict__ bias, float *C32,
-                                                      __nv_bfloat16 *Cb, int M, int N, int K, int relu) {
-    __shared__ __align__(16) __nv_bfloat16 As[kTile][kKStep + kPad];
-    __shared__ __align__(16) __nv_bfloat16 Bs[kTile][kKStep + kPad];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm = warp >> 1, wn = warp & 1;
-    const int g = lane >> 2, t = lane & 3;
-    const int m0 = blockIdx.y * kTile, n0 = blockIdx.x * kTile;
-    float acc[2][4][4] = {};
-    for (int k0 = 0; k0 < K; k0 += kKStep) {
-        // 64 rows x 32 bf16 = 256 chunks of 8 bf16 (16 B) per operand; 2 per thread
-        for (int c = tid; c < 256; c += 128) {
-            const int r = c >> 2, q = (c & 3) * 8;
-            *reinterpret_cast<uint4 *>(&As[r][q]) =
-                *reinterpret_cast<const uint4 *>(A + static_cast<size_t>(m0 + r) * K + k0 + q);
-            *reinterpret_cast<uint4 *>(&Bs[r][q]) =
-                *reinterpret_cast<const uint4 *>(Bt + static_cast<size_t>(n0 + r) * K + k0 + q);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < kKStep; kk += 16) {
-            uint32_t af[2][4], bfr[4][2];
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
-                const int r = wm * 32 + mt * 16 + g;
-                af[mt][0] = ld_pair(&As[r][kk + 2 * t]);
-                af[mt][1] = ld_pair(&As[r + 8][kk + 2 * t]);
-                af[mt][2] = ld_pair(&As[r][kk + 2 * t + 8]);
-                af[mt][3] = ld_pair(&As[r + 8][kk + 2 * t + 8]);
-            }
-#pragma unroll
-            for (int nt = 0; nt < 4; ++nt) {
-                const int r = wn * 32 + nt * 8 + g;
-                bfr[nt][0] = ld_pair(&Bs[r][kk + 2 * t]);
-                bfr[nt][1] = ld_pair(&Bs[r][kk + 2 * t + 8]);
-            }
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-                for (int nt = 0; nt < 4; ++nt)
-                    mma_bf16(acc[mt][nt], af[mt][0], af[mt][1], af[mt][2], af[mt][3], bfr[nt][0], bfr[nt][1]);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int row = m0 + wm * 32 + mt * 16 + g + 8 * h;
-                const int col = n0 + wn * 32 + nt * 8 + 2 * t;
-                float v0 = acc[mt][nt][2 * h], v1 = acc[mt][nt][2 * h + 1];
-                if (bias) {
-                    v0 += bias[col];
-                    v1 += bias[col + 1];
-                }
-                if (relu) {
-                    v0 = fmaxf(v0, 0.f);
-                    v1 = fmaxf(v1, 0.f);
-                }
-                const size_t o = static_cast<size_t>(row) * N + col;
-                if (C32) {
-                    C32[o] = v0;
-                    C32[o + 1] = v1;
-                }
-                if (Cb) *reinterpret_cast<__nv_bfloat162 *>(Cb + o) = __floats2bfloat162_rn(v0, v1);
-            }
-}
 
 // bf16 transpose: out[c][r] = in[r][c], in is R x C
 __global__ void transpose_bf16_kernel(const __nv_bfloat16 *__restrict__ in, __nv_bfloat16 *out, int R, int C) {
@@ -215,9 +124,10 @@ __global__ void f32_to_bf16_kernel(const float *in, __nv_bfloat16 *out, int coun
 
 static size_t al(size_t x) { return (x + 255) & ~size_t(255); }
 
+// layout: status word (offset 0), split-K partials, activations and gradients
 size_t mlp_workspace_bytes(int Bp) {
     const size_t act = static_cast<size_t>(Bp) * kMlpH;
-    return 3 * al(act * 2) + 2 * al(static_cast<size_t>(Bp) * 4) + 2 * al(act * 4) + al(act * 2) +
+    return al(sizeof(uint32_t)) + al(tc_gemm_split_floats() * 4) + 3 * al(act * 2) + 2 * al(static_cast<size_t>(Bp) * 4) + 2 * al(act * 4) + al(act * 2) +
            2 * al(act * 2) + al(static_cast<size_t>(kMlpH) * kMlpH * 2);
 }
 
@@ -229,6 +139,8 @@ void mlp_work(void *ws, int Bp, MlpWork &w) {
         p += al(bytes);
         return q;
     };
+    w.err = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t)));
+    w.part = reinterpret_cast<float *>(take(tc_gemm_split_floats() * 4));
     w.h1 = reinterpret_cast<__nv_bfloat16 *>(take(act * 2));
     w.h2 = reinterpret_cast<__nv_bfloat16 *>(take(act * 2));
     w.h3 = reinterpret_cast<__nv_bfloat16 *>(take(act * 2));
@@ -259,10 +171,8 @@ void mlp_bind(const apm_mlp *net, MlpParams &P) {
 }
 
 static int gemm_tn(const __nv_bfloat16 *A, const __nv_bfloat16 *Bt, const float *bias, float *C32,
-                   __nv_bfloat16 *Cb, int M, int N, int K, int relu, cudaStream_t s) {
-    dim3 grid(N / kTile, M / kTile);
-    gemm_tn_kernel<<<grid, 128, 0, s>>>(A, Bt, bias, C32, Cb, M, N, K, relu);
-    return static_cast<int>(cudaGetLastError());
+                   __nv_bfloat16 *Cb, int M, int N, int K, int relu, MlpWork &w, cudaStream_t s) {
+    return launch_tc_gemm_tn(A, Bt, bias, C32, Cb, M, N, K, relu, w.part, tc_gemm_split_floats(), w.err, s);
 }
 
 static int transpose(const __nv_bfloat16 *in, __nv_bfloat16 *out, int R, int C, cudaStream_t s) {
@@ -273,9 +183,9 @@ static int transpose(const __nv_bfloat16 *in, __nv_bfloat16 *out, int R, int C, 
 
 int mlp_forward(const MlpParams &P, const __nv_bfloat16 *X, int Bp, float *y, MlpWork &w, cudaStream_t s) {
     int e;
-    if ((e = gemm_tn(X, P.w1b, P.b1, nullptr, w.h1, Bp, kMlpH, kMlpIn, 1, s))) return e;
-    if ((e = gemm_tn(w.h1, P.w2b, P.b2, nullptr, w.h2, Bp, kMlpH, kMlpH, 1, s))) return e;
-    if ((e = gemm_tn(w.h2, P.w3b, P.b3, nullptr, w.h3, Bp, kMlpH, kMlpH, 1, s))) return e;
+    if ((e = gemm_tn(X, P.w1b, P.b1, nullptr, w.h1, Bp, kMlpH, kMlpIn, 1, w, s))) return e;
+    if ((e = gemm_tn(w.h1, P.w2b, P.b2, nullptr, w.h2, Bp, kMlpH, kMlpH, 1, w, s))) return e;
+    if ((e = gemm_tn(w.h2, P.w3b, P.b3, nullptr, w.h3, Bp, kMlpH, kMlpH, 1, w, s))) return e;
     head_forward_kernel<<<(Bp + 7) / 8, 256, 0, s>>>(w.h3, P.w4b, P.b4, y, Bp, kMlpH);
     return static_cast<int>(cudaGetLastError());
 }
@@ -296,21 +206,21 @@ int mlp_train_step(MlpParams &P, const __nv_bfloat16 *X, const float *target, in
     // layer 3: dW3 = dZ3^T H2 ; dH2 = dZ3 W3
     if ((e = transpose(w.dzb, w.t1, Bp, kMlpH, s))) return e;  // dZ3^T [256 x Bp]
     if ((e = transpose(w.h2, w.t2, Bp, kMlpH, s))) return e;   // H2^T  [256 x Bp]
-    if ((e = gemm_tn(w.t1, w.t2, nullptr, gw3, nullptr, kMlpH, kMlpH, Bp, 0, s))) return e;
+    if ((e = gemm_tn(w.t1, w.t2, nullptr, gw3, nullptr, kMlpH, kMlpH, Bp, 0, w, s))) return e;
     if ((e = transpose(P.w3b, w.wt, kMlpH, kMlpH, s))) return e;  // W3 stored [out x in] -> [in x out]
-    if ((e = gemm_tn(w.dzb, w.wt, nullptr, w.dh32, nullptr, Bp, kMlpH, kMlpH, 0, s))) return e;
+    if ((e = gemm_tn(w.dzb, w.wt, nullptr, w.dh32, nullptr, Bp, kMlpH, kMlpH, 0, w, s))) return e;
     // layer 2
     relu_backward_kernel<<<(Bp + rpb - 1) / rpb, kMlpH, 0, s>>>(w.dh32, w.h2, w.dz32, w.dzb, gb2, Bp, kMlpH, rpb);
     if ((e = transpose(w.dzb, w.t1, Bp, kMlpH, s))) return e;  // dZ2^T
     if ((e = transpose(w.h1, w.t2, Bp, kMlpH, s))) return e;   // H1^T
-    if ((e = gemm_tn(w.t1, w.t2, nullptr, gw2, nullptr, kMlpH, kMlpH, Bp, 0, s))) return e;
+    if ((e = gemm_tn(w.t1, w.t2, nullptr, gw2, nullptr, kMlpH, kMlpH, Bp, 0, w, s))) return e;
     if ((e = transpose(P.w2b, w.wt, kMlpH, kMlpH, s))) return e;
-    if ((e = gemm_tn(w.dzb, w.wt, nullptr, w.dh32, nullptr, Bp, kMlpH, kMlpH, 0, s))) return e;
+    if ((e = gemm_tn(w.dzb, w.wt, nullptr, w.dh32, nullptr, Bp, kMlpH, kMlpH, 0, w, s))) return e;
     // layer 1
     relu_backward_kernel<<<(Bp + rpb - 1) / rpb, kMlpH, 0, s>>>(w.dh32, w.h1, w.dz32, w.dzb, gb1, Bp, kMlpH, rpb);
     if ((e = transpose(w.dzb, w.t1, Bp, kMlpH, s))) return e;  // dZ1^T [256 x Bp]
     if ((e = transpose(X, w.t2, Bp, kMlpIn, s))) return e;     // X^T   [64 x Bp]
-    if ((e = gemm_tn(w.t1, w.t2, nullptr, gw1, nullptr, kMlpH, kMlpIn, Bp, 0, s))) return e;
+    if ((e = gemm_tn(w.t1, w.t2, nullptr, gw1, nullptr, kMlpH, kMlpIn, Bp, 0, w, s))) return e;
     // Adam
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
     const float c1 = 1.f - powf(b1, static_cast<float>(step)), c2 = 1.f - powf(b2, static_cast<float>(step));

@@ -46,6 +46,8 @@ def _sig(L):
         "apm_mlp_sync_bf16": [ctypes.POINTER(ApmMlp), P],
         "apm_mlp_forward": [ctypes.POINTER(ApmMlp), P, i32, P, P, sz, P],
         "apm_mlp_train_step": [ctypes.POINTER(ApmMlp), P, P, i32, i32, ctypes.c_float, i32, P, P, sz, P],
+        "apm_mlp_status": [P, sz, ctypes.POINTER(ctypes.c_uint32), P],
+        "apm_mlp_gemm_tn": [P, P, P, P, P, i32, i32, i32, i32, P, sz, P],
     }.items():
         f = getattr(L, name)
         if f.argtypes is None:
@@ -91,7 +93,7 @@ class Surrogate:
         self.max_batch = pad64(max_batch)
         nb = ctypes.c_size_t(0)
         apm._check(lib().apm_mlp_workspace_size(self.max_batch, ctypes.byref(nb)), "apm_mlp_workspace_size")
-        self.ws = torch.empty(nb.value, dtype=torch.uint8, device=device)
+        self.ws = torch.zeros(nb.value, dtype=torch.uint8, device=device)  # status word starts clear
         self.loss_acc = torch.zeros(1, dtype=torch.float32, device=device)
         self.step = 0
         self.y_mean, self.y_std = 0.0, 1.0
@@ -102,6 +104,12 @@ class Surrogate:
         assert Bp % 64 == 0 and Bp <= self.max_batch
         apm._check(lib().apm_mlp_forward(ctypes.byref(self.net), _p(F), Bp, _p(y), _p(self.ws), self.ws.numel(),
                                          _s(F)), "apm_mlp_forward")
+
+    def check(self):
+        """Synchronise and raise if a tensor-core GEMM reported a timed-out wait."""
+        flags = ctypes.c_uint32(0)
+        apm._check(lib().apm_mlp_status(_p(self.ws), self.ws.numel(), ctypes.byref(flags), _s(self.ws)),
+                   "apm_mlp_status")
 
     def log_weight(self, F: torch.Tensor, y: torch.Tensor):
         """y <- predicted log|c| (de-normalised)."""
@@ -130,6 +138,7 @@ class Surrogate:
                                                     self.ws.numel(), _s(Fb)), "apm_mlp_train_step")
                 losses.append(self.loss_acc)
                 self.loss_acc = torch.zeros(1, dtype=torch.float32, device=F_all.device)
+        self.check()
         return torch.cat(losses).cpu().numpy() if losses else np.zeros(0)
 
 

@@ -127,3 +127,25 @@ def test_keldysh2_argument_errors(lib):
     assert f(fake, None, 6, 1, 0, fake, None, None, None, 0, None) == 1      # missing second spin
     assert f(fake, fake, 6, 1, 2, fake, None, None, None, 0, None) == 1      # unknown flag
     assert f(None, None, 6, 0, 0, None, None, None, None, 0, None) == 0
+
+
+def test_mlp_gemm_and_status_argument_errors(lib):
+    P, i32, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+    fake = ctypes.c_void_p(1 << 20)
+    ws = ctypes.c_size_t(0)
+    lib.apm_mlp_workspace_size.argtypes = [i32, ctypes.POINTER(sz)]
+    assert lib.apm_mlp_workspace_size(0, ctypes.byref(ws)) == 0 and ws.value > 0
+    f = lib.apm_mlp_gemm_tn
+    f.argtypes = [P, P, P, P, P, i32, i32, i32, i32, P, sz, P]
+    f.restype = ctypes.c_int
+    assert f(fake, fake, None, fake, None, 128, 96, 64, 0, fake, ws.value, None) == 1     # N not a multiple of 64
+    assert f(fake, fake, None, fake, None, 128, 64, 80, 0, fake, ws.value, None) == 1     # K not a multiple of 64
+    assert f(fake, fake, None, fake, None, 0, 64, 64, 0, fake, ws.value, None) == 1       # empty M
+    assert f(fake, fake, None, None, None, 128, 64, 64, 0, fake, ws.value, None) == 1     # no output
+    assert f(ctypes.c_void_p((1 << 20) + 8), fake, None, fake, None, 128, 64, 64, 0, fake, ws.value, None) == 1
+    assert f(fake, fake, None, fake, None, 128, 64, 64, 0, None, 0, None) == 6            # no workspace
+    assert f(fake, fake, None, fake, None, 128, 64, 64, 0, fake, ws.value - 1, None) == 6
+    g = lib.apm_mlp_status
+    g.argtypes = [P, sz, ctypes.POINTER(ctypes.c_uint32), P]
+    g.restype = ctypes.c_int
+    assert g(None, 0, None, None) == 6
