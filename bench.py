@@ -90,7 +90,7 @@ def parse():
     ap.add_argument("--mc-steps", type=int, default=100)
     ap.add_argument("--case", default=None,
                     choices=["cdet_n12", "cdet_n16", "keldysh_n12", "ppm_n14", "cdet_uneven", "xnor_n12",
-                             "nand_n10", "keldysh2_n12"],
+                             "nand_n10", "keldysh2_n12", "mlp_gemm"],
                     help="run 3 launches of one kernel on a small case (for profiling) and exit")
     return ap.parse_args()
 
@@ -190,6 +190,15 @@ def perm_flops(n: int) -> int:
     """Algorithmic flops of all permanent minors: one product and one addition
     per (T subset of S) pair, plus the row sums."""
     return 2 * 3 ** n + n * 2 ** n
+
+
+def _measured_peaks() -> dict:
+    """Measured HBM and BF16 peaks of this GPU type, when the file is present."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
 
 
 def _event_ms(fn, reps=3):
@@ -294,6 +303,32 @@ def measure_rows(args, dev, peak):
     net = mc.Surrogate(seed=7, max_batch=W)
     losses, t_train = mc.timed(lambda: net.train(torch.cat(feats), torch.cat(targs), epochs=1, batch=8192,
                                                  lr=3e-3))
+    net.check()
+    # the surrogate's tensor-core GEMMs at the walkers' batch (context: not the
+    # FP64 roofline): the forward pass (three GEMMs and the head), and the
+    # 16384 x 256 x 256 hidden-layer GEMM alone, against the measured BF16 peak
+    gen = torch.Generator(device="cpu").manual_seed(17)
+    Fq = (torch.randn((W, 64), generator=gen) * 0.5).to(torch.bfloat16).view(torch.int16).to(dev)
+    yq = torch.empty(W, dtype=torch.float32, device=dev)
+    ms_fwd = _event_ms(lambda: net.forward_raw(Fq, yq), reps=20)
+    Ag = torch.randn((W, 256), generator=gen).to(torch.bfloat16).to(dev)
+    Bg = torch.randn((256, 256), generator=gen).to(torch.bfloat16).to(dev)
+    Cg = torch.empty((W, 256), dtype=torch.bfloat16, device=dev)
+
+    def hidden_gemm():
+        apm._check(mc.lib().apm_mlp_gemm_tn(mc._p(Ag), mc._p(Bg), None, None, mc._p(Cg), W, 256, 256, 1,
+                                            mc._p(net.ws), net.ws.numel(), mc._s(Ag)), "apm_mlp_gemm_tn")
+    ms_gemm = _event_ms(hidden_gemm, reps=50)
+    net.check()
+    bf16_peak = _measured_peaks().get("bf16_tflops")
+    fwd_tf = 2 * W * (64 * 256 + 2 * 256 * 256) / (ms_fwd * 1e-3) / 1e12
+    gemm_tf = 2 * W * 256 * 256 / (ms_gemm * 1e-3) / 1e12
+    surrogate = {"forward_us": ms_fwd * 1e3, "forward_gemm_tflops": fwd_tf,
+                 "hidden_gemm_16384x256x256_us": ms_gemm * 1e3, "hidden_gemm_tflops": gemm_tf,
+                 "bf16_peak_tflops": bf16_peak,
+                 "hidden_gemm_frac_bf16_peak": gemm_tf / bf16_peak if bf16_peak else None,
+                 "train_step_8192_us": t_train / max(len(losses), 1) * 1e6,
+                 "kernel": "tcgen05.mma kind::f16, TMA loads, TMEM accumulator (one 128 x 128 tile per CTA)"}
     per_n = {}
     tot = {"plain_ess": 0.0, "plain_s": 0.0, "learned_ess": 0.0, "learned_s": 0.0}
     for n, wk in walkers.items():
@@ -328,7 +363,7 @@ def measure_rows(args, dev, peak):
         "gain_incl_training": (tot["learned_ess"] / (tot["learned_s"] + t_net)) /
                               (tot["plain_ess"] / tot["plain_s"]),
         "steps_per_chain": T, "train_s": t_train, "collect_s": t_collect,
-        "final_train_loss": float(np.mean(losses[-5:])), "per_order": per_n}
+        "final_train_loss": float(np.mean(losses[-5:])), "per_order": per_n, "surrogate": surrogate}
     return rows
 
 
@@ -412,6 +447,22 @@ def profile_case(name: str):
     elif name == "ppm_n14":
         P = torch.as_tensor(inputs.perm_batch(14, 1368, seed=4)).to(dev)
         run = lambda: apm.perm_minors(P)
+    elif name == "mlp_gemm":
+        # the surrogate's hidden-layer GEMM at the walkers' batch (16384 x 256 x 256,
+        # BF16 out with bias and ReLU); operands fit in L2 at this size
+        from paper_2104_07638_gb300 import mc
+        gen = torch.Generator(device="cpu").manual_seed(17)
+        Ag = torch.randn((16384, 256), generator=gen).to(torch.bfloat16).to(dev)
+        Bg = torch.randn((256, 256), generator=gen).to(torch.bfloat16).to(dev)
+        bias = torch.zeros(256, dtype=torch.float32, device=dev)
+        Cg = torch.empty((16384, 256), dtype=torch.bfloat16, device=dev)
+        import ctypes
+        nb = ctypes.c_size_t(0)
+        apm._check(mc.lib().apm_mlp_workspace_size(0, ctypes.byref(nb)), "apm_mlp_workspace_size")
+        ws = torch.zeros(nb.value, dtype=torch.uint8, device=dev)
+        run = lambda: apm._check(mc.lib().apm_mlp_gemm_tn(mc._p(Ag), mc._p(Bg), mc._p(bias), None, mc._p(Cg), 16384,
+                                                          256, 256, 1, mc._p(ws), ws.numel(), mc._s(Ag)),
+                                 "apm_mlp_gemm_tn")
     else:
         orders = inputs.varlen_orders(16384, 4, 16, seed=3)
         flat, off = inputs.hubbard_varlen(orders, seed=3)
