@@ -90,7 +90,7 @@ def parse():
     ap.add_argument("--mc-steps", type=int, default=100)
     ap.add_argument("--case", default=None,
                     choices=["cdet_n12", "cdet_n16", "keldysh_n12", "ppm_n14", "cdet_uneven", "xnor_n12",
-                             "nand_n10", "keldysh2_n12", "mlp_gemm"],
+                             "nand_n10", "keldysh2_n12", "mlp_gemm", "fsc_n16"],
                     help="run 3 launches of one kernel on a small case (for profiling) and exit")
     return ap.parse_args()
 
@@ -184,6 +184,14 @@ def sc_flops(n: int) -> int:
     """Flops of the CDet recursion alone: one FMA per (T, S) pair with the
     lowest element of S in T, T a proper non-empty subset."""
     return 2 * ((3 ** n - 1) // 2 - (2 ** n - 1))
+
+
+def fsc_flops(n: int) -> int:
+    """Flops of the connected sums by the fast subset convolution: ranked zeta
+    and Mobius transforms (n ranks x n elements x 2^(n-1) additions each) and,
+    per mask, the power-series logarithm (k-1 FMAs and a multiply-add and a
+    scaling for each of the n coefficients)."""
+    return 2 * n * n * 2 ** (n - 1) + 2 ** n * (n * (n - 1) + 3 * n)
 
 
 def perm_flops(n: int) -> int:
@@ -288,6 +296,23 @@ def measure_rows(args, dev, peak):
         "tflops": fl / (ms * 1e-3) / 1e12, "frac_fp64_peak": fl / (ms * 1e-3) / 1e12 / peak,
         "launch": "NAND-minor kernel (type sums), then the CDet recursion"}
     del M
+    # next (Section V.A): the connected sums by the fast subset convolution against
+    # the direct recursion, from the same weights (det^2 of Hubbard matrices)
+    fsc = {}
+    for n, B in ((12, 16384), (13, 8192), (14, 2048), (15, 1024), (16, 456)):
+        A = torch.as_tensor(inputs.hubbard_batch(B, n, seed=9)).to(dev)
+        m = apm.all_minors(A)
+        a = m * m
+        del A, m
+        ms_d = _event_ms(lambda: apm.cdet_from_weights(a))
+        ms_f = _event_ms(lambda: apm.cdet_from_weights_fsc(a))
+        fsc[str(n)] = {"batch": B, "recursion_ms": ms_d, "fsc_ms": ms_f, "fsc_over_recursion": ms_f / ms_d,
+                       "recursion_tflops": B * sc_flops(n) / (ms_d * 1e-3) / 1e12,
+                       "fsc_tflops_of_unpruned_count": B * fsc_flops(n) / (ms_f * 1e-3) / 1e12,
+                       "fsc_over_recursion_flops": fsc_flops(n) / sc_flops(n)}
+        del a
+        torch.cuda.empty_cache()
+    rows["cdet_fsc_vs_recursion_n12to16"] = fsc
     # a8: learned proposal vs plain, 16384 walkers at each order 10..14
     G = torch.as_tensor(inputs.hubbard_g0_table()).to(dev)
     W, T = 16384, args.mc_steps
@@ -447,6 +472,12 @@ def profile_case(name: str):
     elif name == "ppm_n14":
         P = torch.as_tensor(inputs.perm_batch(14, 1368, seed=4)).to(dev)
         run = lambda: apm.perm_minors(P)
+    elif name == "fsc_n16":
+        # connected sums by the fast subset convolution, 152 weight rows of order 16
+        A = torch.as_tensor(inputs.hubbard_batch(152, 16, seed=9)).to(dev)
+        m = apm.all_minors(A)
+        a = m * m
+        run = lambda: apm.cdet_from_weights_fsc(a)
     elif name == "mlp_gemm":
         # the surrogate's hidden-layer GEMM at the walkers' batch (16384 x 256 x 256,
         # BF16 out with bias and ReLU); operands fit in L2 at this size

@@ -140,6 +140,21 @@ apm_status_t apm_cdet_from_weights(const double *a, int n, int64_t batch, double
                                    void *workspace, size_t workspace_bytes, apm_stream_t stream);
 
 /*
+ * apm_cdet_from_weights_fsc -- the same connected sums as apm_cdet_from_weights,
+ * by the fast subset convolution the paper mentions for Eq. recursion
+ * (Section V.A, O(n^2 2^n) instead of O(3^n)): ranked zeta transform of a
+ * (a[0] taken as 1), logarithm of the power series in the rank variable at
+ * every mask, ranked Mobius transform, c[S] read at rank |S|. Results agree
+ * with the recursion up to rounding (a different order of operations).
+ *   a  [batch][2^n] float64 input (a[0] is ignored).   c  [batch][2^n] output.
+ *   n  1..APM_MAX_N_MINORS.
+ *   workspace  apm_workspace_size(APM_OP_CDET_FSC, n, batch): the ranked arrays
+ *              (n 2^n doubles per resident CTA) for n > 9, none below.
+ */
+apm_status_t apm_cdet_from_weights_fsc(const double *a, int n, int64_t batch, double *c, void *workspace,
+                                       size_t workspace_bytes, apm_stream_t stream);
+
+/*
  * apm_xnor_minors -- all 2^n XNOR principal minors of 2n x 2n matrices made of
  * 2 x 2 blocks (Section III.B): minors[S] = det of the submatrix that keeps both
  * rows and both columns 2i, 2i+1 of every vertex i in S and none of the others;
@@ -304,6 +319,7 @@ apm_status_t apm_perm_minors(const double *A, int n, int64_t batch, double *perm
 #define APM_OP_NAND_MINORS 10
 #define APM_OP_TWO_TYPE_CDET 11
 #define APM_OP_KELDYSH2 12
+#define APM_OP_CDET_FSC 13
 
 /*
  * apm_cdet_connected_varlen -- apm_cdet_connected for a batch of matrices of

@@ -25,8 +25,8 @@ ST_PIVOT_CORRECTED, ST_NONFINITE_INPUT, ST_ZERO_PIVOT, ST_CORRECTION_OVERFLOW = 
 CDET_SINGLE_DET = 1
 KELDYSH_SIGNED = 1
 OP_ALL_MINORS, OP_CDET, OP_CDET_FROM_WEIGHTS, OP_PERM_MINORS, OP_CDET_VARLEN, OP_KELDYSH, \
-    OP_KELDYSH_VARLEN, OP_XNOR_MINORS, OP_NAMBU_CDET, OP_NAND_MINORS, OP_TWO_TYPE_CDET, OP_KELDYSH2 = \
-    1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12
+    OP_KELDYSH_VARLEN, OP_XNOR_MINORS, OP_NAMBU_CDET, OP_NAND_MINORS, OP_TWO_TYPE_CDET, OP_KELDYSH2, \
+    OP_CDET_FSC = 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13
 ST_BAD_ORDER = 16
 
 
@@ -61,6 +61,7 @@ def lib():
                 "apm_all_minors": [P, i32, i64, P, OPT, P, P, sz, P],
                 "apm_cdet_connected": [P, P, i32, i64, i32, P, P, OPT, P, P, sz, P],
                 "apm_cdet_from_weights": [P, i32, i64, P, P, sz, P],
+                "apm_cdet_from_weights_fsc": [P, i32, i64, P, P, sz, P],
                 "apm_keldysh_sum": [P, i32, i64, i32, P, P, P, P, sz, P],
                 "apm_perm_minors": [P, i32, i64, P, P, sz, P],
                 "apm_keldysh_sum_noalloc": [P, i32, i64, i32, P, P, P, P],
@@ -206,6 +207,24 @@ def cdet_from_weights(a: torch.Tensor):
     ws, nb = _workspace(OP_CDET_FROM_WEIGHTS, n, b, a.device)
     _check(lib().apm_cdet_from_weights(_ptr(a), n, b, _ptr(c), _ptr(ws), nb, _stream(a)),
            "apm_cdet_from_weights")
+    return c
+
+
+def cdet_from_weights_fsc(a: torch.Tensor):
+    """The connected sums of cdet_from_weights by the fast subset convolution."""
+    if not a.is_cuda or a.dtype != torch.float64:
+        raise TypeError("a must be a CUDA float64 tensor")
+    if a.dim() == 1:
+        a = a.unsqueeze(0)
+    a = a.contiguous()
+    b, N = a.shape
+    n = N.bit_length() - 1
+    if 1 << n != N:
+        raise ValueError("last dimension must be 2^n")
+    c = torch.empty_like(a)
+    ws, nb = _workspace(OP_CDET_FSC, n, b, a.device)
+    _check(lib().apm_cdet_from_weights_fsc(_ptr(a), n, b, _ptr(c), _ptr(ws), nb, _stream(a)),
+           "apm_cdet_from_weights_fsc")
     return c
 
 

@@ -117,6 +117,20 @@ apm_status_t apm_cdet_from_weights(const double *a_in, int n, int64_t batch, dou
     return cdet_common(a, workspace, workspace_bytes, reinterpret_cast<cudaStream_t>(stream));
 }
 
+apm_status_t apm_cdet_from_weights_fsc(const double *a, int n, int64_t batch, double *c, void *workspace,
+                                       size_t workspace_bytes, apm_stream_t stream) {
+    if (n < 1 || n > APM_MAX_N_MINORS) return APM_ERR_UNSUPPORTED_N;
+    if (batch < 0) return APM_ERR_ARG;
+    apm_status_t st;
+    if ((st = check_ptr(a, batch)) || (st = check_ptr(c, batch))) return st;
+    if (batch == 0) return APM_OK;
+    size_t need = 0;
+    if ((st = apm_workspace_size(APM_OP_CDET_FSC, n, batch, 0, &need))) return st;
+    if (need > 0 && (!workspace || workspace_bytes < need || !aligned16(workspace))) return APM_ERR_WORKSPACE;
+    const int e = apm::launch_fsc(a, n, batch, c, workspace, reinterpret_cast<cudaStream_t>(stream));
+    return e ? cuda_fail(e) : APM_OK;
+}
+
 apm_status_t apm_xnor_minors(const double *M, int n, int64_t batch, double *minors, uint32_t *status,
                              void *workspace, size_t workspace_bytes, apm_stream_t stream) {
     if (n < 1 || n > APM_MAX_N_XNOR) return APM_ERR_UNSUPPORTED_N;
@@ -391,6 +405,13 @@ apm_status_t apm_workspace_size(int op, int n_max, int64_t batch, int two_mats, 
             if (batch == 0) return APM_OK;
             int err = 0;
             *bytes = apm::keldysh2_workspace_bytes(n_max, batch, &err);
+            return err ? cuda_fail(err) : APM_OK;
+        }
+        case APM_OP_CDET_FSC: {
+            if (n_max < 1 || n_max > APM_MAX_N_MINORS) return APM_ERR_UNSUPPORTED_N;
+            if (batch == 0) return APM_OK;
+            int err = 0;
+            *bytes = apm::fsc_workspace_bytes(n_max, batch, &err);
             return err ? cuda_fail(err) : APM_OK;
         }
         case APM_OP_PERM_MINORS:

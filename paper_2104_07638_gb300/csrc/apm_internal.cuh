@@ -106,6 +106,11 @@ size_t nand_workspace_bytes(int n, int64_t batch, int *err);
 int launch_nand(const double *M, int n, int64_t batch, double *out, bool type_sums, uint32_t *status,
                 void *workspace, cudaStream_t s);
 
+// connected sums by the fast subset convolution (from weights)
+int fsc_grid(int n, int64_t batch, int *err);
+size_t fsc_workspace_bytes(int n, int64_t batch, int *err);
+int launch_fsc(const double *a, int n, int64_t batch, double *c, void *workspace, cudaStream_t s);
+
 // uneven batches
 unsigned long long cdet_gsel_packed(int n);
 void cdet_tune_set(const unsigned long long *table);

@@ -1,0 +1,247 @@
+// Connected sums by the fast subset convolution, O(n^2 2^n) (FP64).
+//
+// Paper: Section V.A notes that the CDet recursion (Eq. recursion) is a subset
+// convolution and can also be evaluated in O(n^2 2^n) with the fast subset
+// convolution of Bjorklund, Husfeldt, Kaski and Koivisto. With a[{}] = 1 the
+// recursion states a[S] = sum over the set partitions of S of the products of
+// c over the blocks, i.e. a = exp(c) in the ring of set functions under subset
+// convolution. The ranked zeta transform
+//     Z_k(X) = sum_{S subset of X, |S| = k} a[S]          (Z_0 = 1)
+// turns subset convolution into products of polynomials in one variable t per
+// mask X (exact on the coefficient of t^|S| after the Mobius transform), so
+//     L(X; t) = log Z(X; t)   (power series to degree n),
+//     c[S] = sum_{X subset of S} (-1)^{|S \ X|} L_{|S|}(X).
+// The logarithm comes from k Z_k = sum_{j=1..k} j L_j Z_{k-j}: with M_k = k L_k,
+//     M_k = k Z_k - sum_{m=1..k-1} Z_m M_{k-m}.
+//
+// One CTA (256 threads) per matrix, persistent over the batch; the ranked
+// arrays R[k][X] (k = 1..n) are transformed in tiles of 512 masks in shared
+// memory. n <= 9 is one tile (init, zeta, logarithm, Mobius, read-out, all in
+// shared memory). Above, the low 9 elements are handled inside a tile and the
+// high h = n - 9 across tiles, through the CTA's slot of the workspace:
+//   pass A  per high pattern X_H: rank init and zeta over the low elements,
+//           only for the ranks |X_H| .. |X_H| + 9 (no other rank can be
+//           nonzero after a zeta over 9 elements); the other ranks are zero;
+//   pass B  per group of 512 / 2^h low patterns (all high patterns): zeta over
+//           the high elements, the logarithm of every mask, Mobius over the
+//           high elements;
+//   pass C  per X_H: Mobius over the low elements for the ranks |X_H| ..
+//           |X_H| + 9 (the only ones read out) and c[X] = L_{|X|}(X).
+// Butterflies run one element at a time with the lanes on consecutive pairs
+// (no bank conflicts). The transforms act on M_k = k L_k (linear), and the
+// read-out divides by |S|. The logarithm keeps Z and M of one mask in
+// registers and skips the terms Z_m = 0 (m > |X|) when every lane of the warp
+// has |X| <= 9: in pass B the masks of a tile are visited in order of
+// popcount (|X| = popcount of the tile index + that of the group), so that
+// the warps are mostly uniform in |X|.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "apm_internal.cuh"
+
+namespace apm {
+
+constexpr int kFscThreads = 256;
+constexpr int kFscTileBits = 9;
+constexpr int kFscTile = 1 << kFscTileBits;
+constexpr int kFscMaxN = 16;
+
+// C(m, k) for m <= 9
+__device__ __forceinline__ int binom_small(int m, int k) {
+    if (k < 0 || k > m) return 0;
+    int r = 1;
+    for (int i = 1; i <= k; ++i) r = r * (m - k + i) / i;
+    return r;
+}
+
+// zeta (sum over subsets) or Mobius (its inverse) over the tile bits [d0, d1)
+// of the rank rows 0..nr-1 of T (rows kFscTile apart, 2^bits masks each)
+__device__ __forceinline__ void fsc_butterfly(double *T, int bits, int d0, int d1, int nr, bool mobius) {
+    const int half = 1 << (bits - 1);
+    for (int d = d0; d < d1; ++d) {
+        for (int q = threadIdx.x; q < half * nr; q += kFscThreads) {
+            const int r = q >> (bits - 1), p = q & (half - 1);
+            const int lo = ((p >> d) << (d + 1)) | (p & ((1 << d) - 1));
+            double *row = T + r * kFscTile;
+            const double v = row[lo];
+            row[lo | (1 << d)] = mobius ? row[lo | (1 << d)] - v : row[lo | (1 << d)] + v;
+        }
+        __syncthreads();
+    }
+}
+
+// M_1..M_n (M_k = k L_k, L = log Z) of tile entry t in place of Z_1..Z_n,
+// for a mask with at most X elements (Z_m = 0 for m > X; X <= n)
+template <int X>
+__device__ __forceinline__ void fsc_log_entry(double *T, int t, int n) {
+    double Z[X + 1], M[kFscMaxN + 1];
+#pragma unroll
+    for (int m = 1; m <= X; ++m) Z[m] = m <= n ? T[(m - 1) * kFscTile + t] : 0.0;  // no mask has more than n
+#pragma unroll
+    for (int k = 1; k <= kFscMaxN; ++k) {
+        if (k <= n) {
+            double s = 0.0;
+            if (k <= X) s = static_cast<double>(k) * Z[k];
+#pragma unroll
+            for (int m = 1; m < kFscMaxN; ++m)
+                if (m < k && m <= X) s = fma(-Z[m], M[k - m], s);
+            M[k] = s;
+            T[(k - 1) * kFscTile + t] = s;
+        }
+    }
+}
+
+// the logarithm for the tile entries order[i] (i < nx; identity when order is
+// NULL), whose masks have popcount(entry) + xoff elements
+__device__ __forceinline__ void fsc_log(double *T, int nx, int n, const uint16_t *order, int xoff) {
+    for (int base = 0; base < nx; base += kFscThreads) {
+        const int i = base + threadIdx.x;
+        const bool act = i < nx;
+        const int t = act ? (order ? order[i] : i) : 0;
+        const int x = act ? __popc(t) + xoff : 0;
+        const int xm = __reduce_max_sync(0xffffffffu, static_cast<unsigned>(x));
+        if (!act) continue;
+        // two specialisations: more would not fit the registers of three CTAs per SM
+        if (xm <= 9)
+            fsc_log_entry<9>(T, t, n);
+        else
+            fsc_log_entry<kFscMaxN>(T, t, n);
+    }
+}
+
+__global__ void __launch_bounds__(kFscThreads, 3) fsc_kernel(const double *__restrict__ a, int n, int64_t batch,
+                                                              double *c, double *ws) {
+    extern __shared__ __align__(16) double T[];
+    __shared__ uint16_t s_order[kFscTile];  // tile entries by (popcount, value)
+    __shared__ double s_inv[kFscMaxN + 1];  // 1/k
+    const int tid = threadIdx.x;
+    const int N = 1 << n;
+    if (tid <= kFscMaxN) s_inv[tid] = tid ? 1.0 / tid : 0.0;
+    for (int t = tid; t < kFscTile; t += kFscThreads) {
+        // position of t: the classes of fewer elements first, then the rank of t
+        // among the masks of its popcount (combinatorial number system)
+        const int p = __popc(t);
+        int pos = 0;
+        for (int c = 0; c < p; ++c) pos += binom_small(kFscTileBits, c);
+        int i = 0;
+        for (int r = t; r; r &= r - 1) pos += binom_small(__ffs(r) - 1, ++i);
+        s_order[pos] = static_cast<uint16_t>(t);
+    }
+    __syncthreads();
+    if (n <= kFscTileBits) {
+        for (int64_t b = blockIdx.x; b < batch; b += gridDim.x) {
+            const double *ab = a + b * N;
+            for (int q = tid; q < n * N; q += kFscThreads) {
+                const int r = q >> n, x = q & (N - 1);
+                T[r * kFscTile + x] = __popc(x) == r + 1 ? ab[x] : 0.0;
+            }
+            __syncthreads();
+            fsc_butterfly(T, n, 0, n, n, false);
+            fsc_log(T, N, n, nullptr, 0);
+            __syncthreads();
+            fsc_butterfly(T, n, 0, n, n, true);
+            double *cb = c + b * N;
+            for (int x = tid; x < N; x += kFscThreads)
+                cb[x] = x ? T[(__popc(x) - 1) * kFscTile + x] * s_inv[__popc(x)] : 0.0;
+            __syncthreads();
+        }
+        return;
+    }
+    const int h = n - kFscTileBits, NH = 1 << h, lg = kFscTileBits - h;  // G = 2^lg low patterns per group
+    double *R = ws + static_cast<size_t>(blockIdx.x) * n * N;           // [n][N]
+    for (int64_t b = blockIdx.x; b < batch; b += gridDim.x) {
+        const double *ab = a + b * N;
+        // pass A: partial zeta over the low elements
+        for (int XH = 0; XH < NH; ++XH) {
+            const int p = __popc(XH), k0 = p > 1 ? p : 1, k1 = p + kFscTileBits < n ? p + kFscTileBits : n;
+            const int nr = k1 - k0 + 1;
+            const size_t base = static_cast<size_t>(XH) << kFscTileBits;
+            for (int q = tid; q < nr * kFscTile; q += kFscThreads) {
+                const int r = q >> kFscTileBits, x = q & (kFscTile - 1);
+                T[q] = __popc(x) + p == k0 + r ? ab[base + x] : 0.0;
+            }
+            __syncthreads();
+            fsc_butterfly(T, kFscTileBits, 0, kFscTileBits, nr, false);
+            for (int q = tid; q < n * kFscTile; q += kFscThreads) {
+                const int k = (q >> kFscTileBits) + 1, x = q & (kFscTile - 1);
+                R[static_cast<size_t>(k - 1) * N + base + x] =
+                    k >= k0 && k <= k1 ? T[(k - k0) * kFscTile + x] : 0.0;
+            }
+            __syncthreads();
+        }
+        // pass B: zeta over the high elements, logarithm, Mobius over the high elements
+        for (int g = 0; g < NH; ++g) {
+            for (int q = tid; q < n * kFscTile; q += kFscThreads) {
+                const int r = q >> kFscTileBits, t = q & (kFscTile - 1);
+                const int XH = t >> lg, j = t & ((1 << lg) - 1);
+                T[q] = R[static_cast<size_t>(r) * N + (static_cast<size_t>(XH) << kFscTileBits) + (g << lg) + j];
+            }
+            __syncthreads();
+            fsc_butterfly(T, kFscTileBits, lg, kFscTileBits, n, false);
+            fsc_log(T, kFscTile, n, s_order, __popc(g));
+            __syncthreads();
+            fsc_butterfly(T, kFscTileBits, lg, kFscTileBits, n, true);
+            for (int q = tid; q < n * kFscTile; q += kFscThreads) {
+                const int r = q >> kFscTileBits, t = q & (kFscTile - 1);
+                const int XH = t >> lg, j = t & ((1 << lg) - 1);
+                R[static_cast<size_t>(r) * N + (static_cast<size_t>(XH) << kFscTileBits) + (g << lg) + j] = T[q];
+            }
+            __syncthreads();
+        }
+        // pass C: Mobius over the low elements and the read-out c[X] = L_|X|(X)
+        double *cb = c + b * N;
+        for (int XH = 0; XH < NH; ++XH) {
+            const int p = __popc(XH), k0 = p > 1 ? p : 1, k1 = p + kFscTileBits < n ? p + kFscTileBits : n;
+            const int nr = k1 - k0 + 1;
+            const size_t base = static_cast<size_t>(XH) << kFscTileBits;
+            for (int q = tid; q < nr * kFscTile; q += kFscThreads) {
+                const int r = q >> kFscTileBits, x = q & (kFscTile - 1);
+                T[q] = R[static_cast<size_t>(k0 + r - 1) * N + base + x];
+            }
+            __syncthreads();
+            fsc_butterfly(T, kFscTileBits, 0, kFscTileBits, nr, true);
+            for (int x = tid; x < kFscTile; x += kFscThreads)
+                cb[base + x] = (XH | x) ? T[(__popc(x) + p - k0) * kFscTile + x] * s_inv[__popc(x) + p] : 0.0;
+            __syncthreads();
+        }
+    }
+}
+
+static size_t fsc_smem(int n) { return static_cast<size_t>(n) * kFscTile * sizeof(double); }
+
+int fsc_grid(int n, int64_t batch, int *err) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t smem = fsc_smem(n);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(fsc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(fsc_smem(kFscMaxN)));
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fsc_kernel, kFscThreads, smem);
+    if (e != cudaSuccess || per_sm < 1) {
+        *err = e != cudaSuccess ? static_cast<int>(e) : static_cast<int>(cudaErrorInvalidConfiguration);
+        return 0;
+    }
+    *err = 0;
+    int64_t g = static_cast<int64_t>(sms) * per_sm;
+    if (batch < g) g = batch;
+    return static_cast<int>(g < 1 ? 1 : g);
+}
+
+size_t fsc_workspace_bytes(int n, int64_t batch, int *err) {
+    *err = 0;
+    if (n <= kFscTileBits || batch == 0) return 0;
+    const int grid = fsc_grid(n, batch, err);
+    if (*err) return 0;
+    return static_cast<size_t>(grid) * n * (static_cast<size_t>(1) << n) * sizeof(double);
+}
+
+int launch_fsc(const double *a, int n, int64_t batch, double *c, void *workspace, cudaStream_t s) {
+    int err = 0;
+    const int grid = fsc_grid(n, batch, &err);
+    if (err) return err;
+    fsc_kernel<<<grid, kFscThreads, fsc_smem(n), s>>>(a, n, batch, c, static_cast<double *>(workspace));
+    return static_cast<int>(cudaGetLastError());
+}
+
+}  // namespace apm
