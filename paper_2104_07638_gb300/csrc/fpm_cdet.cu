@@ -240,25 +240,23 @@ __device__ __forceinline__ void fpm_tree(const double *__restrict__ Ag, int n, d
     }
     if (tid == 0) MA[0] = 1.0;
     __syncthreads();
-    if (L > 0 && tid == 0) {
-        double v = W0[0];
-        node_pivot(0, 0, v, MA, thr, shift, h);
-        W0[0] = v;
-    }
-    __syncthreads();
     for (int l = 0; l < L; ++l) {
         const int s = n - l, s1 = s - 1, ss = s * s, ss1 = s1 * s1, P = 1 << l;
         double *Wl = APM_BUF(l);
         double *Wn = APM_BUF(l + 1);
-        // pivot row of every node scaled by 1/p (Wl[0] holds 1/p); row 0 is not
-        // part of the left child, so it can be scaled in place
-        for (int t = tid; t < P * s1; t += T) {
-            const int m = t / s1, q = t - m * s1;
-            Wl[m * ss + q + 1] *= Wl[m * ss];
+        // one thread per node: the node's minor and pivot (the division runs
+        // with a lane per node, not one lane of a warp busy with Schur entries),
+        // then its pivot row scaled by 1/p; row 0 is not part of the left child,
+        // so it can be scaled in place (Wl[0] keeps 1/p)
+        for (int m = tid; m < P; m += T) {
+            double *Wm = Wl + m * ss;
+            double v = Wm[0];
+            node_pivot(m, l, v, MA, thr, shift, h);
+            for (int q = 1; q < s; ++q) Wm[q] *= v;
+            Wm[0] = v;
         }
         __syncthreads();
         const int E = 2 * P * ss1;
-        const bool pivot_next = (l + 1) < L;
         for (int e = tid; e < E; e += T) {
             const int x = e / ss1;
             const int rem = e - x * ss1;
@@ -268,7 +266,6 @@ __device__ __forceinline__ void fpm_tree(const double *__restrict__ Ag, int n, d
             double v = Wp[(p + 1) * s + q + 1];
             if (x >> l)  // right child: Schur complement w.r.t. the pivot
                 v = fma(-Wp[(p + 1) * s], Wp[q + 1], v);
-            if (rem == 0 && pivot_next) node_pivot(x, l + 1, v, MA, thr, shift, h);
             Wn[x * ss1 + rem] = v;
         }
         __syncthreads();
@@ -279,8 +276,8 @@ __device__ __forceinline__ void fpm_tree(const double *__restrict__ Ag, int n, d
     for (int m = tid; m < (1 << L); m += T) bottom4(WL + m * 16, MA[m], MA, m, L, s);
     __syncthreads();
     // back-propagation of pivot corrections, deepest level first (the log is in
-    // non-decreasing level order because each level's pivots are logged in the
-    // tree step that precedes it)
+    // non-decreasing level order: each level's pivots are logged in its own
+    // pivot phase, after a barrier that ends the previous level)
     const int nc = h.ncorr;
     if (nc > kCorrCap) {
         for (int t = tid; t < (1 << n); t += T) MA[t] = __longlong_as_double(0x7ff8000000000000ll);
