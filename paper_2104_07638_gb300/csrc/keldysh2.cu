@@ -61,12 +61,15 @@ __device__ __forceinline__ void k2_tail_level(const double2 *cur0, const double2
                                               int &bad, K2Acc &acc) {
     constexpr int m = 2 * (S - J), m2 = m - 2, mm = m * m, mm2 = m2 * m2;
     constexpr int nchild = 2 << J;
+    static_assert(2 * nchild <= 32, "a lane per child and spin");
+    if (lane < 2 * nchild) {  // lanes [0, nchild) spin up, [nchild, 2 nchild) spin down
+        const int sp = lane >= nchild ? 1 : 0, c = lane - sp * nchild, alpha = c & 1;
+        w.inv[sp][c] = crcp((sp ? cur1 : cur0)[(c >> 1) * mm + alpha * m + alpha], bad);
+    }
     if (lane < nchild) {
         const int alpha = lane & 1;
         const double2 p0 = cur0[(lane >> 1) * mm + alpha * m + alpha];
         const double2 p1 = cur1[(lane >> 1) * mm + alpha * m + alpha];
-        w.inv[0][lane] = crcp(p0, bad);
-        w.inv[1][lane] = crcp(p1, bad);
         const double2 nd = cneg_if(cmul(cmul(w.ndet[J & 1][lane >> 1], p0), p1), sgn && alpha);
         w.ndet[(J + 1) & 1][lane] = nd;
         if (want_part) acc.v[S - 1 - J] = cadd(acc.v[S - 1 - J], nd);
@@ -200,7 +203,11 @@ __device__ __forceinline__ void k2_schur(const double2 *s0, const double2 *s1, i
                                          int &bad) {
     p0 = s0[alpha * m + alpha];
     p1 = s1[alpha * m + alpha];
-    const double2 iv0 = crcp(p0, bad), iv1 = crcp(p1, bad);
+    // one reciprocal per lane (even lanes spin up, odd lanes spin down), then
+    // exchanged: a warp instruction costs the FP64 pipe the same for 1 or 32 lanes
+    const double2 ivl = crcp((lane & 1) ? p1 : p0, bad);
+    const double2 ivo = make_double2(__shfl_xor_sync(0xffffffffu, ivl.x, 1), __shfl_xor_sync(0xffffffffu, ivl.y, 1));
+    const double2 iv0 = (lane & 1) ? ivo : ivl, iv1 = (lane & 1) ? ivl : ivo;
     const int m2 = m - 2;
     for (int idx = lane; idx < 2 * m2; idx += 32) {
         const int sp = idx >= m2, r = idx - sp * m2;
