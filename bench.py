@@ -299,7 +299,9 @@ def measure_rows(args, dev, peak):
     # next (Section V.A): the connected sums by the fast subset convolution against
     # the direct recursion, from the same weights (det^2 of Hubbard matrices)
     fsc = {}
-    for n, B in ((12, 16384), (13, 8192), (14, 2048), (15, 1024), (16, 456)):
+    # batches are multiples of 456 at the larger orders (3 resident CTAs on each of
+    # 152 SMs for both kernels), so that no launch ends with a part-empty round
+    for n, B in ((12, 16416), (13, 8208), (14, 2280), (15, 1368), (16, 456)):
         A = torch.as_tensor(inputs.hubbard_batch(B, n, seed=9)).to(dev)
         m = apm.all_minors(A)
         a = m * m
