@@ -11,7 +11,7 @@ Prints ONE JSON line (rank 0):
   value      minor-sets/s over all ranks, device-timed (inputs resident in HBM)
   e2e        the same metric through the public API from pinned host buffers,
              host->device copy of the inputs and device->host copy of minors and
-             c inside the timed region (chunked over 3 streams)
+             c inside the timed region (32 chunks over 4 streams)
   roofline   FP64-ALU bound of the fused kernel (bound "alu")
   cpu_baseline  the CPU oracle (per-minor LU + plain recursion) on a bounded
              sample of the same workload, all host cores
@@ -577,25 +577,27 @@ def main():
     ms_per_step = 1000.0 * dev_s / args.steps
 
     # ---- end to end through the public API from pinned host memory ----
-    chunks = 8
+    # 32 chunks over 4 streams: the copies of one chunk overlap the kernels of
+    # the others, and only the last chunk's device->host copy is left exposed
+    chunks, nstreams = 32, 4
     cb = B // chunks
     A_host = torch.as_tensor(A_np).pin_memory()
     c_host = torch.empty((B, N), dtype=torch.float64).pin_memory()
     m_host = torch.empty((B, N), dtype=torch.float64).pin_memory()
-    streams = [torch.cuda.Stream(dev) for _ in range(3)]
-    A_d = [torch.empty((cb, n, n), dtype=torch.float64, device=dev) for _ in range(3)]
-    c_d = [torch.empty((cb, N), dtype=torch.float64, device=dev) for _ in range(3)]
-    m_d = [torch.empty((cb, N), dtype=torch.float64, device=dev) for _ in range(3)]
+    streams = [torch.cuda.Stream(dev) for _ in range(nstreams)]
+    A_d = [torch.empty((cb, n, n), dtype=torch.float64, device=dev) for _ in range(nstreams)]
+    c_d = [torch.empty((cb, N), dtype=torch.float64, device=dev) for _ in range(nstreams)]
+    m_d = [torch.empty((cb, N), dtype=torch.float64, device=dev) for _ in range(nstreams)]
 
     def e2e_step():
         for k in range(chunks):
-            s = streams[k % 3]
+            q = k % nstreams
             sl = slice(k * cb, (k + 1) * cb)
-            with torch.cuda.stream(s):
-                A_d[k % 3].copy_(A_host[sl], non_blocking=True)
-                apm.cdet_connected(A_d[k % 3], out_c=c_d[k % 3], out_minors=m_d[k % 3])
-                c_host[sl].copy_(c_d[k % 3], non_blocking=True)
-                m_host[sl].copy_(m_d[k % 3], non_blocking=True)
+            with torch.cuda.stream(streams[q]):
+                A_d[q].copy_(A_host[sl], non_blocking=True)
+                apm.cdet_connected(A_d[q], out_c=c_d[q], out_minors=m_d[q])
+                c_host[sl].copy_(c_d[q], non_blocking=True)
+                m_host[sl].copy_(m_d[q], non_blocking=True)
         for s in streams:
             s.synchronize()
 
