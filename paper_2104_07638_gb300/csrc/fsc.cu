@@ -27,8 +27,11 @@
 //           high elements;
 //   pass C  per X_H: Mobius over the low elements for the ranks |X_H| ..
 //           |X_H| + 9 (the only ones read out) and c[X] = L_{|X|}(X).
-// Butterflies run one element at a time with the lanes on consecutive pairs
-// (no bank conflicts). The transforms act on M_k = k L_k (linear), and the
+// Butterflies run one element at a time, and a warp skips a step when all its
+// pairs are known no-ops (zero sources in a zeta, targets that are never read
+// out in a Mobius): about a third of the transforms at n = 16 (the butterfly
+// loops are kept rolled, which keeps the kernel within the registers of three
+// CTAs per SM). The transforms act on M_k = k L_k (linear), and the
 // read-out divides by |S|. The logarithm keeps Z and M of one mask in
 // registers and skips the terms Z_m = 0 (m > |X|) when every lane of the warp
 // has |X| <= 9: in pass B the masks of a tile are visited in order of
@@ -54,17 +57,75 @@ __device__ __forceinline__ int binom_small(int m, int k) {
     return r;
 }
 
-// zeta (sum over subsets) or Mobius (its inverse) over the tile bits [d0, d1)
-// of the rank rows 0..nr-1 of T (rows kFscTile apart, 2^bits masks each)
-__device__ __forceinline__ void fsc_butterfly(double *T, int bits, int d0, int d1, int nr, bool mobius) {
+// zeta (sum over subsets) or Mobius (its inverse) over all 2^bits tile masks
+// (the low elements) of the rank rows 0..nr-1 of T (rows kFscTile apart). Row r
+// holds the rank whose low part has c = c0 + r elements (zeta: the nonzero
+// inputs; Mobius: the masks read out). With a full tile (bits = 9, every warp
+// busy for nr rounds) a warp skips a step when every lane's pair is known to
+// be a no-op: zeta, the source still sums over no mask with c elements (after
+// the elements below d, it sums over the masks between its part above d and
+// itself); Mobius, no mask with c elements is reached from the target by
+// adding elements above d (its value is never read out).
+__device__ __forceinline__ void fsc_butterfly_low(double *T, int bits, int nr, int c0, bool mobius) {
     const int half = 1 << (bits - 1);
-    for (int d = d0; d < d1; ++d) {
+    const bool prune = bits == kFscTileBits;
+#pragma unroll 1
+    for (int d = 0; d < bits; ++d) {
+#pragma unroll 1
         for (int q = threadIdx.x; q < half * nr; q += kFscThreads) {
             const int r = q >> (bits - 1), p = q & (half - 1);
-            const int lo = ((p >> d) << (d + 1)) | (p & ((1 << d) - 1));
+            const int lo = ((p >> d) << (d + 1)) | (p & ((1 << d) - 1)), hi = lo | (1 << d);
+            if (prune) {
+                const int c = c0 + r;
+                bool skip;
+                if (!mobius) {
+                    skip = __popc(lo) < c || __popc(lo >> d) > c;
+                } else {
+                    const int ph = __popc(hi), free_above = (bits - 1 - d) - __popc(lo >> (d + 1));
+                    skip = ph > c || ph + free_above < c;
+                }
+                if (__all_sync(0xffffffffu, skip)) continue;
+            }
             double *row = T + r * kFscTile;
             const double v = row[lo];
-            row[lo | (1 << d)] = mobius ? row[lo | (1 << d)] - v : row[lo | (1 << d)] + v;
+            row[hi] = mobius ? row[hi] - v : row[hi] + v;
+        }
+        __syncthreads();
+    }
+}
+
+// pass B: zeta or Mobius over the high tile bits [lg, 9) (the h = 9 - lg high
+// elements) of the rank rows 0..n-1 (rank k = row + 1), the pairs of a step
+// visited in popcount order of their high part (ordh: the masks of h - 1 bits
+// by popcount) so that warps skip together: zeta, the source holds zeros (after
+// pass A only high parts with k - 9 .. k elements are nonzero, and after the
+// high elements below d the source sums over the high parts between its part
+// above d and itself); Mobius, no high part with k - 9 .. k elements (the only
+// ones pass C reads at rank k) is reached from the target by adding elements
+// above d.
+__device__ __forceinline__ void fsc_butterfly_high(double *T, int lg, int n, bool mobius, const uint8_t *ordh) {
+    const int h = kFscTileBits - lg;
+#pragma unroll 1
+    for (int dh = 0; dh < h; ++dh) {
+        const int d = lg + dh;
+#pragma unroll 1
+        for (int q = threadIdx.x; q < (kFscTile / 2) * n; q += kFscThreads) {
+            const int r = q >> (kFscTileBits - 1), pq = q & (kFscTile / 2 - 1);
+            const int xr = ordh[pq >> lg];                                             // h - 1 bits
+            const int xlo = ((xr >> dh) << (dh + 1)) | (xr & ((1 << dh) - 1));         // bit dh clear
+            const int lo = (xlo << lg) | (pq & ((1 << lg) - 1)), hi = lo | (1 << d);
+            const int k = r + 1, pl = __popc(xlo);
+            bool skip;
+            if (!mobius) {
+                skip = pl < k - kFscTileBits || __popc(xlo >> dh) > k;
+            } else {
+                const int free_above = (h - 1 - dh) - __popc(xlo >> (dh + 1));
+                skip = pl + 1 > k || pl + 1 + free_above < k - kFscTileBits;
+            }
+            if (__all_sync(0xffffffffu, skip)) continue;
+            double *row = T + r * kFscTile;
+            const double v = row[lo];
+            row[hi] = mobius ? row[hi] - v : row[hi] + v;
         }
         __syncthreads();
     }
@@ -114,6 +175,7 @@ __global__ void __launch_bounds__(kFscThreads, 3) fsc_kernel(const double *__res
     extern __shared__ __align__(16) double T[];
     __shared__ uint16_t s_order[kFscTile];  // tile entries by (popcount, value)
     __shared__ double s_inv[kFscMaxN + 1];  // 1/k
+    __shared__ uint8_t s_ordh[1 << (kFscMaxN - kFscTileBits - 1)];  // masks of h - 1 bits by popcount
     const int tid = threadIdx.x;
     const int N = 1 << n;
     if (tid <= kFscMaxN) s_inv[tid] = tid ? 1.0 / tid : 0.0;
@@ -127,6 +189,15 @@ __global__ void __launch_bounds__(kFscThreads, 3) fsc_kernel(const double *__res
         for (int r = t; r; r &= r - 1) pos += binom_small(__ffs(r) - 1, ++i);
         s_order[pos] = static_cast<uint16_t>(t);
     }
+    const int hb = n > kFscTileBits ? n - kFscTileBits - 1 : 0;  // bits of the high part minus one
+    for (int t = tid; t < (1 << hb); t += kFscThreads) {
+        const int p = __popc(t);
+        int pos = 0;
+        for (int c = 0; c < p; ++c) pos += binom_small(hb, c);
+        int i = 0;
+        for (int r = t; r; r &= r - 1) pos += binom_small(__ffs(r) - 1, ++i);
+        s_ordh[pos] = static_cast<uint8_t>(t);
+    }
     __syncthreads();
     if (n <= kFscTileBits) {
         for (int64_t b = blockIdx.x; b < batch; b += gridDim.x) {
@@ -136,10 +207,10 @@ __global__ void __launch_bounds__(kFscThreads, 3) fsc_kernel(const double *__res
                 T[r * kFscTile + x] = __popc(x) == r + 1 ? ab[x] : 0.0;
             }
             __syncthreads();
-            fsc_butterfly(T, n, 0, n, n, false);
+            fsc_butterfly_low(T, n, n, 1, false);
             fsc_log(T, N, n, nullptr, 0);
             __syncthreads();
-            fsc_butterfly(T, n, 0, n, n, true);
+            fsc_butterfly_low(T, n, n, 1, true);
             double *cb = c + b * N;
             for (int x = tid; x < N; x += kFscThreads)
                 cb[x] = x ? T[(__popc(x) - 1) * kFscTile + x] * s_inv[__popc(x)] : 0.0;
@@ -161,7 +232,7 @@ __global__ void __launch_bounds__(kFscThreads, 3) fsc_kernel(const double *__res
                 T[q] = __popc(x) + p == k0 + r ? ab[base + x] : 0.0;
             }
             __syncthreads();
-            fsc_butterfly(T, kFscTileBits, 0, kFscTileBits, nr, false);
+            fsc_butterfly_low(T, kFscTileBits, nr, k0 - p, false);
             for (int q = tid; q < n * kFscTile; q += kFscThreads) {
                 const int k = (q >> kFscTileBits) + 1, x = q & (kFscTile - 1);
                 R[static_cast<size_t>(k - 1) * N + base + x] =
@@ -177,10 +248,10 @@ __global__ void __launch_bounds__(kFscThreads, 3) fsc_kernel(const double *__res
                 T[q] = R[static_cast<size_t>(r) * N + (static_cast<size_t>(XH) << kFscTileBits) + (g << lg) + j];
             }
             __syncthreads();
-            fsc_butterfly(T, kFscTileBits, lg, kFscTileBits, n, false);
+            fsc_butterfly_high(T, lg, n, false, s_ordh);
             fsc_log(T, kFscTile, n, s_order, __popc(g));
             __syncthreads();
-            fsc_butterfly(T, kFscTileBits, lg, kFscTileBits, n, true);
+            fsc_butterfly_high(T, lg, n, true, s_ordh);
             for (int q = tid; q < n * kFscTile; q += kFscThreads) {
                 const int r = q >> kFscTileBits, t = q & (kFscTile - 1);
                 const int XH = t >> lg, j = t & ((1 << lg) - 1);
@@ -199,7 +270,7 @@ __global__ void __launch_bounds__(kFscThreads, 3) fsc_kernel(const double *__res
                 T[q] = R[static_cast<size_t>(k0 + r - 1) * N + base + x];
             }
             __syncthreads();
-            fsc_butterfly(T, kFscTileBits, 0, kFscTileBits, nr, true);
+            fsc_butterfly_low(T, kFscTileBits, nr, k0 - p, true);
             for (int x = tid; x < kFscTile; x += kFscThreads)
                 cb[base + x] = (XH | x) ? T[(__popc(x) + p - k0) * kFscTile + x] * s_inv[__popc(x) + p] : 0.0;
             __syncthreads();

@@ -77,3 +77,22 @@ def test_a_empty_is_ignored_and_batch_deterministic(apm):
 def test_empty_batch(apm):
     c = apm.cdet_from_weights_fsc(torch.zeros((0, 256), dtype=torch.float64, device="cuda"))
     assert c.shape == (0, 256)
+
+
+def test_bench_size_sampled(apm):
+    """The launch the benchmark row times at the largest order (456 weight rows
+    of order 16, every resident CTA busy): sampled rows against the oracle, and
+    the direct recursion on the same weights within the tolerance."""
+    A = I.hubbard_batch(456, 16, seed=9)
+    ah = oracle.minors_lu(A) ** 2
+    a = torch.as_tensor(ah).cuda()
+    c = apm.cdet_from_weights_fsc(a)
+    assert torch.equal(c, apm.cdet_from_weights_fsc(a))
+    idx = [0, 455]
+    cref = oracle.cdet_recursion(ah[idx])
+    bound = oracle.minors_rowsum_bound(A[idx]) ** 2
+    scale = np.maximum(oracle.cdet_scale(bound), 1e-300)
+    assert np.all(np.abs(c[idx].cpu().numpy() - cref) <= TOL * scale)
+    cd = apm.cdet_from_weights(a)
+    full_scale = np.maximum(oracle.cdet_scale(oracle.minors_rowsum_bound(A) ** 2), 1e-300)
+    assert np.all(np.abs(c.cpu().numpy() - cd.cpu().numpy()) <= TOL * full_scale)
