@@ -39,8 +39,8 @@ METRIC = "minor-sets/sec at n=12 FP64 (% of roofline)"
 # DRAM bytes (read + write) per matrix of the fused kernel from one ncu capture
 # of 4096 matrices (211.3 MB), valid only for the kernel source it was taken on
 # (sha256 prefix below).
-TRAFFIC_PER_SET = 211.30e6 / 4096
-TRAFFIC_SRC_SHA = "c6a0b22863adcd84"
+TRAFFIC_PER_SET = 210.89e6 / 4096
+TRAFFIC_SRC_SHA = "a204edccd590c297"
 UNIT = "minor-sets/s"
 
 
@@ -186,6 +186,17 @@ def sc_flops(n: int) -> int:
     return 2 * ((3 ** n - 1) // 2 - (2 ** n - 1))
 
 
+FSC_FROM_N = 16  # orders whose connected sums the library takes through the fast subset convolution
+
+
+def cdet_path_flops(n: int) -> int:
+    """Algorithmic flops of one minor set as the library computes it: the
+    recursion's count below FSC_FROM_N, the fast subset convolution's from there."""
+    if n < FSC_FROM_N:
+        return flops_per_set(n)
+    return flops_per_set(n) - sc_flops(n) + fsc_flops(n)
+
+
 def fsc_flops(n: int) -> int:
     """Flops of the connected sums by the fast subset convolution: ranked zeta
     and Mobius transforms (n ranks x n elements x 2^(n-1) additions each) and,
@@ -237,11 +248,13 @@ def measure_rows(args, dev, peak):
     n_t = torch.as_tensor(orders).to(dev)
     g = CdetVarlenGraph(A, a_off, n_t)
     ms = _event_ms(g.replay)
-    fl = sum(flops_per_set(int(k)) for k in orders)
+    fl = sum(cdet_path_flops(int(k)) for k in orders)
     rows["a7_cdet_uneven_131072_n4to16"] = {
         "value": orders.size / (ms * 1e-3), "unit": "minor-sets/s", "ms": ms,
         "tflops": fl / (ms * 1e-3) / 1e12, "frac_fp64_peak": fl / (ms * 1e-3) / 1e12 / peak,
-        "launch": "CUDA graph: counting sort by order + one persistent longest-first kernel"}
+        "launch": "CUDA graph: counting sort by order + one persistent longest-first kernel "
+                  "+ the fast subset convolution of the order-16 rows",
+        "flops": "recursion count below n = 16, fast-subset-convolution count at n = 16"}
     del g, A
     # a5 on the same uneven orders: Keldysh sums of 1D-chain real-time G0
     kflat, koff = inputs.keldysh_varlen(orders, seed=3)

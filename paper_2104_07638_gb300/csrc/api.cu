@@ -45,7 +45,12 @@ apm_status_t cdet_common(apm::CdetArgs &a, void *workspace, size_t workspace_byt
         int err = 0;
         const int grid = apm::cdet_grid(a.n, a.batch, two, false, &err);
         if (err) return cuda_fail(err);
-        const size_t need = static_cast<size_t>(grid) * apm::cdet_slot_doubles(a.n) * sizeof(double);
+        size_t need = static_cast<size_t>(grid) * apm::cdet_slot_doubles(a.n) * sizeof(double);
+        if (a.mode == apm::kModeCdet && a.n >= apm::kFscFromN) {
+            const size_t f = apm::fsc_workspace_bytes(a.n, a.batch, &err);
+            if (err) return cuda_fail(err);
+            if (f > need) need = f;
+        }
         if (!workspace || workspace_bytes < need || !aligned16(workspace)) return APM_ERR_WORKSPACE;
         a.gscratch = static_cast<double *>(workspace);
     }
@@ -356,6 +361,11 @@ apm_status_t apm_workspace_size(int op, int n_max, int64_t batch, int two_mats, 
             const int grid = apm::cdet_grid(n_max, batch, two, false, &err);
             if (err) return cuda_fail(err);
             *bytes = static_cast<size_t>(grid) * apm::cdet_slot_doubles(n_max) * sizeof(double);
+            if (op == APM_OP_CDET && n_max >= apm::kFscFromN) {  // then the ranked arrays
+                const size_t f = apm::fsc_workspace_bytes(n_max, batch, &err);
+                if (err) return cuda_fail(err);
+                if (f > *bytes) *bytes = f;
+            }
             return APM_OK;
         }
         case APM_OP_KELDYSH: {

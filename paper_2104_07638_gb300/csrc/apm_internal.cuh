@@ -60,7 +60,12 @@ struct CdetArgs {
     int two_mats;
     double piv_thr;
     double piv_shift;
+    int fsc_from_n;  // orders >= this (0: none) leave the weights a[] in c for the fast subset convolution
 };
+
+// Orders whose connected sums apm_cdet_connected and its uneven-batch form take
+// through the fast subset convolution (faster than the recursion from here on).
+constexpr int kFscFromN = 16;
 
 // Launches the fused minors / connected-sum kernel. Returns a cudaError_t.
 int launch_fpm_cdet(const CdetArgs &a, cudaStream_t s);
@@ -110,6 +115,10 @@ int launch_nand(const double *M, int n, int64_t batch, double *out, bool type_su
 int fsc_grid(int n, int64_t batch, int *err);
 size_t fsc_workspace_bytes(int n, int64_t batch, int *err);
 int launch_fsc(const double *a, int n, int64_t batch, double *c, void *workspace, cudaStream_t s);
+// in place on the rows c + c_off[order[i]] (2^n doubles: weights in, connected
+// sums out) for i < *count (a device counter, at most max_items)
+int launch_fsc_items(double *c, const int64_t *c_off, const int *order, const unsigned *count, int64_t max_items,
+                     int n, void *workspace, cudaStream_t s);
 
 // uneven batches
 unsigned long long cdet_gsel_packed(int n);

@@ -486,6 +486,10 @@ __device__ __forceinline__ void cdet_item(const CdetArgs &p, int n, const double
     if (in_smem) {
         cdet_layers(MA, MA, MC, n, gsel);
         if (tid == 0) bulk_store(co, MC, N * 8u);
+    } else if (p.fsc_from_n && n >= p.fsc_from_n) {
+        // the weights go to the output row; the fast subset convolution that
+        // follows in its own launch turns them into the connected sums in place
+        for (int t = tid; t < N; t += blockDim.x) co[t] = MA[t];
     } else {
         cdet_blocked(MA, co, n, blk, gsel_b);
     }
@@ -579,7 +583,12 @@ __global__ void __launch_bounds__(1024) varlen_order_kernel(const int *__restric
             start[n] = pos;
             pos += hist[n];
         }
-        *ctr = 0u;
+        ctr[0] = 0u;
+        // items of the orders that take the fast subset convolution: the first
+        // ones of the longest-first order
+        int nf = 0;
+        for (int n = kFscFromN; n <= 16; ++n) nf += hist[n];
+        ctr[1] = static_cast<unsigned>(nf);
     }
     __syncthreads();
     for (int64_t b = threadIdx.x; b < batch; b += blockDim.x) {
@@ -724,11 +733,16 @@ int launch_fpm_cdet(const CdetArgs &a, cudaStream_t s) {
     const int grid = cdet_grid(a.n, a.batch, a.two_mats != 0, smem_arrays, &err);
     if (err) return err;
     const size_t smem = cdet_smem_bytes(a.n, a.two_mats != 0, smem_arrays);
+    const bool fsc = a.mode == kModeCdet && a.n >= kFscFromN;
+    P.a.fsc_from_n = fsc ? kFscFromN : 0;
     if (smem_arrays)
         fpm_cdet_kernel<true><<<grid, kCdetThreads, smem, s>>>(P);
     else
         fpm_cdet_kernel<false><<<grid, kCdetThreads, smem, s>>>(P);
-    return static_cast<int>(cudaGetLastError());
+    err = static_cast<int>(cudaGetLastError());
+    if (err || !fsc) return err;
+    // the workspace holds the fused kernel's slots, then the ranked arrays
+    return launch_fsc(a.c_out, a.n, a.batch, a.c_out, a.gscratch, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -763,7 +777,13 @@ size_t cdet_varlen_workspace(int n_max, int64_t batch, bool two_mats, int *err) 
     if (n_max > kVarlenSmemMaxN) {
         const int grid = cdet_varlen_grid(two_mats, err);
         if (*err) return 0;
-        bytes += static_cast<size_t>(grid) * slot_doubles(n_max) * sizeof(double);
+        size_t slots = static_cast<size_t>(grid) * slot_doubles(n_max) * sizeof(double);
+        if (n_max >= kFscFromN) {  // the same region then holds the ranked arrays
+            const size_t f = fsc_workspace_bytes(n_max, batch, err);
+            if (*err) return 0;
+            if (f > slots) slots = f;
+        }
+        bytes += slots;
     } else {
         *err = 0;
     }
@@ -799,9 +819,16 @@ int launch_cdet_varlen(const CdetArgs &a, const int64_t *a_off, const int *n_arr
     V.smem_max_n = kVarlenSmemMaxN;
     V.n_max = n_max;
     for (int n = 0; n <= 16; ++n) V.gsel[n] = cdet_gsel_packed(n);
+    static_assert(kFscFromN == 16, "the item launch below takes the one order 16");
+    const bool fsc = a.mode == kModeCdet && n_max >= kFscFromN;
+    V.a.fsc_from_n = fsc ? kFscFromN : 0;
     const int64_t g = a.batch < grid ? a.batch : grid;
     fpm_cdet_varlen_kernel<<<static_cast<int>(g), kCdetThreads, cdet_smem_bytes(kVarlenSmemMaxN, two, true), s>>>(V);
-    return static_cast<int>(cudaGetLastError());
+    err = static_cast<int>(cudaGetLastError());
+    if (err || !fsc) return err;
+    // the longest-first prefix of n >= kFscFromN items (counted by the order
+    // kernel), in place on their output rows
+    return launch_fsc_items(a.c_out, c_off, order, ctr + 1, a.batch, kFscFromN, slots, s);
 }
 
 }  // namespace apm

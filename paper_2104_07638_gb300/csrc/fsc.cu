@@ -170,8 +170,12 @@ __device__ __forceinline__ void fsc_log(double *T, int nx, int n, const uint16_t
     }
 }
 
-__global__ void __launch_bounds__(kFscThreads, 3) fsc_kernel(const double *__restrict__ a, int n, int64_t batch,
-                                                              double *c, double *ws) {
+// Rows: a + b 2^n -> c + b 2^n for b < batch, or, with `order`, in place on the
+// rows c + c_off[order[i]] for i < *count (a may equal c: every row is read in
+// pass A before pass C writes it).
+__global__ void __launch_bounds__(kFscThreads, 3) fsc_kernel(const double *a, int n, int64_t batch, double *c,
+                                                              double *ws, const int *order, const int64_t *c_off,
+                                                              const unsigned *count) {
     extern __shared__ __align__(16) double T[];
     __shared__ uint16_t s_order[kFscTile];  // tile entries by (popcount, value)
     __shared__ double s_inv[kFscMaxN + 1];  // 1/k
@@ -199,9 +203,12 @@ __global__ void __launch_bounds__(kFscThreads, 3) fsc_kernel(const double *__res
         s_ordh[pos] = static_cast<uint8_t>(t);
     }
     __syncthreads();
+    const int64_t items = order ? static_cast<int64_t>(*count) : batch;
+    auto row_in = [&](int64_t i) { return order ? c + c_off[order[i]] : a + i * N; };
+    auto row_out = [&](int64_t i) { return order ? c + c_off[order[i]] : c + i * N; };
     if (n <= kFscTileBits) {
-        for (int64_t b = blockIdx.x; b < batch; b += gridDim.x) {
-            const double *ab = a + b * N;
+        for (int64_t b = blockIdx.x; b < items; b += gridDim.x) {
+            const double *ab = row_in(b);
             for (int q = tid; q < n * N; q += kFscThreads) {
                 const int r = q >> n, x = q & (N - 1);
                 T[r * kFscTile + x] = __popc(x) == r + 1 ? ab[x] : 0.0;
@@ -211,7 +218,7 @@ __global__ void __launch_bounds__(kFscThreads, 3) fsc_kernel(const double *__res
             fsc_log(T, N, n, nullptr, 0);
             __syncthreads();
             fsc_butterfly_low(T, n, n, 1, true);
-            double *cb = c + b * N;
+            double *cb = row_out(b);
             for (int x = tid; x < N; x += kFscThreads)
                 cb[x] = x ? T[(__popc(x) - 1) * kFscTile + x] * s_inv[__popc(x)] : 0.0;
             __syncthreads();
@@ -220,8 +227,8 @@ __global__ void __launch_bounds__(kFscThreads, 3) fsc_kernel(const double *__res
     }
     const int h = n - kFscTileBits, NH = 1 << h, lg = kFscTileBits - h;  // G = 2^lg low patterns per group
     double *R = ws + static_cast<size_t>(blockIdx.x) * n * N;           // [n][N]
-    for (int64_t b = blockIdx.x; b < batch; b += gridDim.x) {
-        const double *ab = a + b * N;
+    for (int64_t b = blockIdx.x; b < items; b += gridDim.x) {
+        const double *ab = row_in(b);
         // pass A: partial zeta over the low elements
         for (int XH = 0; XH < NH; ++XH) {
             const int p = __popc(XH), k0 = p > 1 ? p : 1, k1 = p + kFscTileBits < n ? p + kFscTileBits : n;
@@ -260,7 +267,7 @@ __global__ void __launch_bounds__(kFscThreads, 3) fsc_kernel(const double *__res
             __syncthreads();
         }
         // pass C: Mobius over the low elements and the read-out c[X] = L_|X|(X)
-        double *cb = c + b * N;
+        double *cb = row_out(b);
         for (int XH = 0; XH < NH; ++XH) {
             const int p = __popc(XH), k0 = p > 1 ? p : 1, k1 = p + kFscTileBits < n ? p + kFscTileBits : n;
             const int nr = k1 - k0 + 1;
@@ -311,7 +318,18 @@ int launch_fsc(const double *a, int n, int64_t batch, double *c, void *workspace
     int err = 0;
     const int grid = fsc_grid(n, batch, &err);
     if (err) return err;
-    fsc_kernel<<<grid, kFscThreads, fsc_smem(n), s>>>(a, n, batch, c, static_cast<double *>(workspace));
+    fsc_kernel<<<grid, kFscThreads, fsc_smem(n), s>>>(a, n, batch, c, static_cast<double *>(workspace), nullptr,
+                                                      nullptr, nullptr);
+    return static_cast<int>(cudaGetLastError());
+}
+
+int launch_fsc_items(double *c, const int64_t *c_off, const int *order, const unsigned *count, int64_t max_items,
+                     int n, void *workspace, cudaStream_t s) {
+    int err = 0;
+    const int grid = fsc_grid(n, max_items, &err);
+    if (err) return err;
+    fsc_kernel<<<grid, kFscThreads, fsc_smem(n), s>>>(c, n, max_items, c, static_cast<double *>(workspace), order,
+                                                      c_off, count);
     return static_cast<int>(cudaGetLastError());
 }
 

@@ -86,6 +86,23 @@ def test_order_14_global_scratch_variant(apm):
     check_cdet(apm, A)
 
 
+@pytest.mark.parametrize("n", [15, 16])
+def test_orders_15_16_hubbard(apm, n):
+    """The largest orders: the blocked recursion (n = 15) and the fast subset
+    convolution that apm_cdet_connected takes at n = 16, for det^2, det and
+    two-matrix weights."""
+    A = I.hubbard_batch(2, n, seed=600 + n)
+    check_minors(apm, A)
+    check_cdet(apm, A)
+    check_cdet(apm, A, single_det=True)
+    B = I.hubbard_batch(2, n, seed=650 + n)
+    c = apm.cdet_connected(dev(A), dev(B)).cpu().numpy()
+    mu, md = oracle.minors_lu(A), oracle.minors_lu(B)
+    su, sd = oracle.minors_scale(A), oracle.minors_scale(B)
+    err = scaled_err(c, oracle.cdet_recursion(mu * md), oracle.cdet_scale(su * sd))
+    assert err <= TOL, err
+
+
 @pytest.mark.parametrize("n", [6, 10, 12])
 def test_zero_diagonal_forces_pivot_correction(apm, n):
     rng = np.random.default_rng(200 + n)
