@@ -123,7 +123,13 @@ apm_status_t apm_all_minors(const double *A, int n, int64_t batch, double *minor
  *   c          [batch][2^n] float64 output.
  *   minors_out [batch][2^n] float64 (minors of A_up) or NULL; when A_dn is given,
  *              [batch][2][2^n] (minors of A_up, then of A_dn).
- *   opt, status, workspace: as for apm_all_minors.
+ *   opt, status, workspace: as for apm_all_minors (for n = 16 the workspace
+ *              also holds the ranked arrays below: apm_workspace_size with
+ *              APM_OP_CDET).
+ * At n = 16 the connected sums come from the same weights by the fast subset
+ * convolution of apm_cdet_from_weights_fsc (a second launch on `stream`, in
+ * place on c), which is faster there; the results agree with the recursion up
+ * to rounding.
  */
 apm_status_t apm_cdet_connected(const double *A_up, const double *A_dn, int n, int64_t batch,
                                 int flags, double *c, double *minors_out,
@@ -339,6 +345,9 @@ apm_status_t apm_perm_minors(const double *A, int n, int64_t batch, double *perm
  * from a global counter (an atomic increment, no waiting). Orders up to 12 keep
  * a[] and c[] in shared memory, larger ones in the CTA's slot of the workspace.
  * The lane-group mapping per order is the one installed by apm_cdet_tune_set.
+ * Order-16 matrices (the first ones of that order, counted by the sort) leave
+ * their weights in c and a third launch finishes them in place by the fast
+ * subset convolution, as apm_cdet_connected does at n = 16.
  * A matrix whose n[b] is outside 1..n_max is skipped with APM_ST_BAD_ORDER.
  * The call allocates nothing and does not synchronise: it can be captured in a
  * CUDA graph once the first (non-captured) call on the device has run.
