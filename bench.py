@@ -360,6 +360,8 @@ def measure_rows(args, dev, peak):
                                             mc._p(net.ws), net.ws.numel(), mc._s(Ag)), "apm_mlp_gemm_tn")
     ms_gemm = _event_ms(hidden_gemm, reps=50)
     net.check()
+    # the same product by the vendor library (torch.matmul -> cuBLAS), for context only
+    ms_lib = _event_ms(lambda: torch.relu(torch.matmul(Ag, Bg.t())), reps=50)
     bf16_peak = _measured_peaks().get("bf16_tflops")
     fwd_tf = 2 * W * (64 * 256 + 2 * 256 * 256) / (ms_fwd * 1e-3) / 1e12
     gemm_tf = 2 * W * 256 * 256 / (ms_gemm * 1e-3) / 1e12
@@ -367,6 +369,7 @@ def measure_rows(args, dev, peak):
                  "hidden_gemm_16384x256x256_us": ms_gemm * 1e3, "hidden_gemm_tflops": gemm_tf,
                  "bf16_peak_tflops": bf16_peak,
                  "hidden_gemm_frac_bf16_peak": gemm_tf / bf16_peak if bf16_peak else None,
+                 "hidden_gemm_cublas_us_context": ms_lib * 1e3,
                  "train_step_8192_us": t_train / max(len(losses), 1) * 1e6,
                  "kernel": "tcgen05.mma kind::f16, TMA loads, TMEM accumulator (one 128 x 128 tile per CTA)"}
     per_n = {}
