@@ -34,8 +34,9 @@
 //    stream-interleaved so that a lane reads its two as one 16-byte word, and
 //    the terms inside each run ordered so that the alpha gathers of a
 //    half-warp mostly hit distinct banks. A stream writes the sum of each run
-//    of terms of one S_L to a result slot; cut sets add their slots in a fixed
-//    order, and the warp adds the 2^l sums into perm[S_H u S_L] in the output
+//    of terms of one S_L to a result slot; the runs of a cut set are added
+//    pairwise in rounds of one addition per lane (a fixed tree), and the warp
+//    adds the 2^l sums into perm[S_H u S_L] in the output
 //    row (no two warps touch one S within a step and steps are separated by
 //    barriers: no atomics, deterministic).
 #include <cuda_runtime.h>
@@ -59,8 +60,10 @@ constexpr int kPpmSchedInts = 60000;
 // Schedules for l = 1..7, packed into one int array on the device.
 struct PpmSched {
     int term;     // [maxlen][64] term words: T_L | 0x80 on the last term of a run | slot << 8; -1 past the end
-    int comb;     // [2^l + 1] CSR offsets of the result slots of each S_L
-    int combidx;  // slot ids per S_L (the slot of the run that comes first in S_L's submask order first)
+    int first;    // [2^l] result slot that ends up holding the sum of S_L (its first run's)
+    int rnd;      // [nrounds + 1] CSR offsets of the rounds of slot additions
+    int pairs;    // slot additions (dst | src << 16): the runs of a cut set added pairwise, a tree
+    int nrounds;
     int tl;       // [kPpmWarps + 1] CSR offsets of the T_L owned by each warp
     int tllist;   // [2^l] owned T_L, warp by warp
     int blvl;     // [kPpmWarps][l + 2] B entries of each warp, level by level
@@ -255,12 +258,24 @@ static void build_schedules(std::vector<int> &buf) {
             }
             blvl[static_cast<size_t>(w) * (l + 2) + l + 1] = static_cast<int>(ent.size() / 2);
         }
-        std::vector<int> comb(NL + 1), combidx;
-        for (int S = 0; S < NL; ++S) {
-            comb[S] = static_cast<int>(combidx.size());
-            combidx.insert(combidx.end(), slots_of[S].begin(), slots_of[S].end());
+        // the runs of every cut set are added pairwise (stride 1, 2, 4, ...) into the
+        // slot of its first run; round r holds the additions of stride 2^r, at most
+        // one per slot, so a warp does a round with one addition per lane
+        std::vector<int> first(NL), rnd(1, 0), pairs;
+        for (int S = 0; S < NL; ++S) first[S] = slots_of[S][0];
+        for (int st = 1;; st *= 2) {
+            bool any = false;
+            for (int S = 0; S < NL; ++S) {
+                const std::vector<int> &sl = slots_of[S];
+                for (size_t i = 0; i + st < sl.size(); i += 2 * st) {
+                    pairs.push_back(sl[i] | (sl[i + st] << 16));
+                    any = true;
+                }
+            }
+            if (!any) break;
+            rnd.push_back(static_cast<int>(pairs.size()));
         }
-        comb[NL] = static_cast<int>(combidx.size());
+        s.nrounds = static_cast<int>(rnd.size()) - 1;
         auto put = [&buf](const std::vector<int> &v) {
             const int at = static_cast<int>(buf.size());
             buf.insert(buf.end(), v.begin(), v.end());
@@ -277,8 +292,9 @@ static void build_schedules(std::vector<int> &buf) {
         if (buf.size() & 1) buf.push_back(0);  // the term words are read in pairs (int2)
         s.term = put(term);
         s.len = put(len);
-        s.comb = put(comb);
-        s.combidx = put(combidx);
+        s.first = put(first);
+        s.rnd = put(rnd);
+        s.pairs = put(pairs);
         s.tl = put(tl);
         s.tllist = put(tllist);
         s.blvl = put(blvl);
@@ -299,6 +315,8 @@ static bool schedules_fit(const std::vector<int> &buf) {
                 const int *lv = buf.data() + s.blvl + w * (l + 2);
                 if (lv[d + 1] - lv[d] > 4 * 32) return false;
             }
+        for (int r = 0; r < s.nrounds; ++r)  // one slot addition per lane and round
+            if (buf[s.rnd + r + 1] - buf[s.rnd + r] > 32) return false;
     }
     return true;
 }
@@ -378,8 +396,9 @@ __global__ void __launch_bounds__(kPpmWarps * 32, 3) ppm_kernel(const double *__
     const int l = n < kPpmMaxL ? n : kPpmMaxL, h = n - l, NL = 1 << l;
     const int N = 1 << n;
     const int *term = g_ppm_sched + sc.term;
-    const int *comb = g_ppm_sched + sc.comb;
-    const int *combidx = g_ppm_sched + sc.combidx;
+    const int *first = g_ppm_sched + sc.first;
+    const int *rnd = g_ppm_sched + sc.rnd;
+    const int *pairs = g_ppm_sched + sc.pairs;
     const int *tllist = g_ppm_sched + sc.tllist + g_ppm_sched[sc.tl + warp];
     const int ntl = g_ppm_sched[sc.tl + warp + 1] - g_ppm_sched[sc.tl + warp];
     const int *blvl = g_ppm_sched + sc.blvl + warp * (l + 2);
@@ -540,10 +559,16 @@ __global__ void __launch_bounds__(kPpmWarps * 32, 3) ppm_kernel(const double *__
                     ppm_terms(term2, alpha, Bp2, res, lenA, lane);
                     __syncwarp();
                     const int SH = TH | Rw | pdep_dev(j, highmask);
+                    for (int r = 0; r < sc.nrounds; ++r) {  // cut sets: their runs' sums, pairwise
+                        const int i = rnd[r] + lane;
+                        if (i < rnd[r + 1]) {
+                            const int pw = pairs[i];
+                            res[pw & 0xffff] += res[pw >> 16];
+                        }
+                        __syncwarp();
+                    }
                     for (int S = lane; S < NL; S += 32) {
-                        const int q0 = comb[S], q1 = comb[S + 1];
-                        double tot = res[combidx[q0]];
-                        for (int q = q0 + 1; q < q1; ++q) tot += res[combidx[q]];
+                        const double tot = res[first[S]];
                         // the output row streams through L2 only, so that L1 keeps the schedule
                         double *o = perm + ((SH << l) | S);
                         __stcg(o, __ldcg(o) + tot);
