@@ -96,6 +96,26 @@ def test_graph_replay_matches_direct_call(apm):
     assert not torch.equal(c1, c2)
 
 
+def test_graph_replay_with_order_16(apm):
+    """Orders up to 16: the captured graph holds the sort, the persistent kernel
+    and the fast subset convolution of the order-16 rows."""
+    from paper_2104_07638_gb300.batch import CdetVarlenGraph
+    orders = np.concatenate([[16, 16, 16], I.varlen_orders(200, 4, 15, seed=1306)]).astype(np.int32)
+    A, a_off, n, flat, off = packed_hubbard(orders, seed=1307)
+    g = CdetVarlenGraph(A, a_off, n)
+    direct = apm.cdet_connected_varlen(A, a_off, n)
+    assert torch.equal(g.replay().clone(), direct)
+    c_off = apm.varlen_out_offsets(n).cpu().numpy()
+    c = direct.cpu().numpy()
+    for b in range(3):                # the order-16 rows against the oracle
+        M = flat[off[b]:off[b] + 256].reshape(1, 16, 16)
+        mref = oracle.minors_lu(M)
+        bound = oracle.minors_rowsum_bound(M) ** 2
+        cref = oracle.cdet_recursion(mref * mref)[0]
+        scale = np.maximum(oracle.cdet_scale(bound)[0], 1e-300)
+        assert np.all(np.abs(c[c_off[b]:c_off[b] + (1 << 16)] - cref) <= TOL * scale)
+
+
 def test_tuned_tables_keep_bitwise_agreement(apm):
     from paper_2104_07638_gb300.batch import _shift_table
     table = [_shift_table(apm.tune_get(m), m, -1) for m in range(17)]
