@@ -8,7 +8,7 @@
  * Every routine is the direct definition of what it computes, written for
  * obviousness rather than speed:
  *   - principal minors:  one Gaussian elimination with partial pivoting per
- *                        subset (the "trivial" O(n^3 2^n) method of Section II);
+ *                        subset (the naive O(n^3 2^n) method that Section II improves on);
  *   - permanents:        Ryser's inclusion-exclusion formula (Eq. ryser,
  *                        Section IV) applied to each principal submatrix, with
  *                        the global sign (-1)^|S| that makes it the permanent;
