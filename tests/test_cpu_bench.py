@@ -1,8 +1,6 @@
 """Host-side arithmetic of the benchmark: the algorithmic work counts behind
 every roofline figure, checked by enumerating the operations they count on
 small orders (no GPU)."""
-import itertools
-
 import bench
 
 
