@@ -4,10 +4,6 @@ small orders (no GPU)."""
 import bench
 
 
-def popc(x):
-    return bin(x).count("1")
-
-
 def test_recursion_pairs_by_enumeration():
     """One FMA per (T, S) pair of Eq. recursion: T a proper nonempty subset of S
     holding S's lowest element."""
