@@ -1,6 +1,6 @@
 """Parity of the CUDA minors / connected-sum path with the CPU oracle.
 
-Tolerance (fixed by the benchmark spec for this path): |gpu - oracle| <= 1e-10
+Tolerance: |gpu - oracle| <= 1e-10
 times the sum of the absolute values of the terms: perm(|A[S]|) for a minor,
 and for c[S] the recursion run on those scales with all signs positive.
 """
