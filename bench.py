@@ -175,9 +175,12 @@ def keldysh2_flops(n: int) -> int:
 def nand_flops(n: int) -> int:
     """Algorithmic flops of all NAND minors of a 2n x 2n matrix (the ternary
     tree): per node two kept children of size m2 = 2(n-l-1), each the rank-1
-    Schur update (2 m2^2), its row factors (m2) and the pivot reciprocal and
-    node product (3)."""
-    return sum(3 ** l * 2 * (2 * (2 * (n - l - 1)) ** 2 + 2 * (n - l - 1) + 3) for l in range(n))
+    Schur update of the m2 (m2 - 1) entries a minor can read (a minor keeps at
+    most one row and column of a 2 x 2 block, so the blocks' off-diagonal
+    entries are never read: 2 m2 (m2 - 1)), its row factors (m2) and the pivot
+    reciprocal and node product (3)."""
+    return sum(3 ** l * 2 * (2 * (2 * (n - l - 1)) * (2 * (n - l - 1) - 1) + 2 * (n - l - 1) + 3)
+               for l in range(n))
 
 
 def sc_flops(n: int) -> int:

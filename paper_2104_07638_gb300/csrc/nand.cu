@@ -41,10 +41,17 @@ __host__ __device__ constexpr int nd_pow3(int k) {
     for (int i = 0; i < k; ++i) r *= 3;
     return r;
 }
-// Tail level J (J = 0..S-2) holds 3^J nodes of size 2(S-J); even levels in
-// bufE, odd in bufO. S = 6: bufE 144, 576, 1296; bufO 300, 972.
+// Tail nodes are stored without the two off-diagonal entries of each 2 x 2
+// diagonal block: a minor keeps at most one row and column of a block, and a
+// Schur update of entry (r, q) reads only (r, q), (r, p), (p, q) and (p, p)
+// with the pivot p in another block, so entries (2i, 2i+1) and (2i+1, 2i) are
+// never read. Row r of a node of size m holds its m - 1 columns q != r ^ 1 in
+// order (compact column c <-> q = c + (c >= (r ^ 1))); a column of another
+// block has the same compact index in a node and in its children.
+// Tail level J (J = 0..S-2) holds 3^J nodes of size m = 2(S-J), m(m-1) entries
+// each; even levels in bufE, odd in bufO. S = 6: bufE 132, 504, 972; bufO 270, 810.
 __host__ __device__ constexpr int nd_level_entries(int S, int J) {
-    return nd_pow3(J) * (2 * (S - J)) * (2 * (S - J));
+    return nd_pow3(J) * (2 * (S - J)) * (2 * (S - J) - 1);
 }
 __host__ __device__ constexpr int nd_buf_entries(int S, int parity) {
     int b = 0;
@@ -53,7 +60,7 @@ __host__ __device__ constexpr int nd_buf_entries(int S, int parity) {
 }
 constexpr int kNdBufE = nd_buf_entries(kNdTail, 0);
 constexpr int kNdBufO = nd_buf_entries(kNdTail, 1);
-static_assert(kNdBufE == 1296 && kNdBufO == 972, "6-vertex tail");
+static_assert(kNdBufE == 972 && kNdBufO == 810, "6-vertex tail");
 static_assert(kNdBufO >= 729 && kNdBufE >= 729, "the 3^6 tail minors fit in either buffer");
 // row factors of one level: 2 kept children per node, m-2 rows each (27 x 2 x 4)
 constexpr int kNdFac = 216;
@@ -92,16 +99,19 @@ __device__ __forceinline__ double nd_inv(double p, int &bad) {
 // One breadth-first level J of a tail over S vertices: the 3^J nodes of size
 // m = 2(S-J) in cur give 3^(J+1) children of size m-2 in nxt. Child 3k drops the
 // node's last vertex (the leading block, copied); child 3k+1+t keeps its row
-// and column m-2+t (t = 0, 1) and drops the other: the rank-1 Schur update
-// (r,q) -= f(r) node(m-2+t, q), f(r) = node(r, m-2+t) / node(m-2+t, m-2+t).
+// and column p = m-2+t (t = 0, 1) and drops the other: the rank-1 Schur update
+// (r,q) -= f(r) node(p, q), f(r) = node(r, p) / node(p, p). In the compact
+// layout node(p, p) is at column m-2 of row p, node(r, p) at column p-1 of row
+// r, and node(p, q), q < m-2, at column q of row p.
 template <int S, int J>
 __device__ __forceinline__ void nd_tail_level(const double *cur, double *nxt, NdWarpSmem &w, int lane, int &bad) {
-    constexpr int m = 2 * (S - J), m2 = m - 2, mm = m * m, mm2 = m2 * m2, nodes = nd_pow3(J);
+    constexpr int m = 2 * (S - J), m2 = m - 2, rl = m - 1, rl2 = m2 - 1;
+    constexpr int mm = m * rl, mm2 = m2 * rl2, nodes = nd_pow3(J);
     const double *ndc = w.nd[J & 1];
     double *ndn = w.nd[(J + 1) & 1];
     for (int i = lane; i < 2 * nodes; i += 32) {
         const int k = i >> 1, t = i & 1, pi = m - 2 + t;
-        const double p = cur[k * mm + pi * m + pi];
+        const double p = cur[k * mm + pi * rl + (m - 2)];
         w.inv[i] = nd_inv(p, bad);
         ndn[3 * k + 1 + t] = ndc[k] * p;
         if (t == 0) ndn[3 * k] = ndc[k];
@@ -109,58 +119,61 @@ __device__ __forceinline__ void nd_tail_level(const double *cur, double *nxt, Nd
     __syncwarp();
     for (int idx = lane; idx < 2 * nodes * m2; idx += 32) {
         const int kt = idx / m2, r = idx - kt * m2;
-        w.f[idx] = cur[(kt >> 1) * mm + r * m + (m - 2 + (kt & 1))] * w.inv[kt];
+        w.f[idx] = cur[(kt >> 1) * mm + r * rl + (m - 3 + (kt & 1))] * w.inv[kt];
     }
     __syncwarp();
     for (int e = lane; e < nodes * mm2; e += 32) {
-        const int k = e / mm2, rem = e - k * mm2, r = rem / m2, q = rem - r * m2;
-        nxt[(3 * k) * mm2 + rem] = cur[k * mm + r * m + q];
+        const int k = e / mm2, rem = e - k * mm2, r = rem / rl2, c = rem - r * rl2;
+        nxt[(3 * k) * mm2 + rem] = cur[k * mm + r * rl + c];
     }
     for (int e = lane; e < 2 * nodes * mm2; e += 32) {
-        const int kt = e / mm2, rem = e - kt * mm2, r = rem / m2, q = rem - r * m2;
+        const int kt = e / mm2, rem = e - kt * mm2, r = rem / rl2, c = rem - r * rl2;
+        const int q = c + (c >= (r ^ 1));
         const int k = kt >> 1, t = kt & 1;
         const double *P = cur + k * mm;
-        nxt[(3 * k + 1 + t) * mm2 + rem] = fma(-w.f[kt * m2 + r], P[(m - 2 + t) * m + q], P[r * m + q]);
+        nxt[(3 * k + 1 + t) * mm2 + rem] = fma(-w.f[kt * m2 + r], P[(m - 2 + t) * rl + q], P[r * rl + c]);
     }
     __syncwarp();
 }
 
 // The last two vertices (0: rows 0,1; 1: rows 2,3) of every 4 x 4 node k in
 // closed form: the 9 minors nd * (1, M00, M11, M22, det{0,2}, det{1,2}, M33,
-// det{0,3}, det{1,3}) at out[9k + sigma_0 + 3 sigma_1].
+// det{0,3}, det{1,3}) at out[9k + sigma_0 + 3 sigma_1]. A compact 4 x 4 node
+// holds (M00 M02 M03 | M11 M12 M13 | M20 M21 M22 | M30 M31 M33).
 template <int S>
 __device__ __forceinline__ void nd_bottom(const double *cur, const double *nd, double *out, int lane) {
     constexpr int nodes = nd_pow3(S - 2);
     for (int k = lane; k < nodes; k += 32) {
-        const double *M = cur + 16 * k;
+        const double *M = cur + 12 * k;
         const double d = nd[k];
         double *o = out + 9 * k;
         o[0] = d;
         o[1] = d * M[0];
-        o[2] = d * M[5];
-        o[3] = d * M[10];
-        o[4] = d * fma(M[0], M[10], -M[2] * M[8]);
-        o[5] = d * fma(M[5], M[10], -M[6] * M[9]);
-        o[6] = d * M[15];
-        o[7] = d * fma(M[0], M[15], -M[3] * M[12]);
-        o[8] = d * fma(M[5], M[15], -M[7] * M[13]);
+        o[2] = d * M[3];
+        o[3] = d * M[8];
+        o[4] = d * fma(M[0], M[8], -M[1] * M[6]);
+        o[5] = d * fma(M[3], M[8], -M[4] * M[7]);
+        o[6] = d * M[11];
+        o[7] = d * fma(M[0], M[11], -M[2] * M[9]);
+        o[8] = d * fma(M[3], M[11], -M[5] * M[10]);
     }
 }
 
 // The type sums of the last two vertices of every 4 x 4 node k: out[4k + b],
 // bit 0 of b <-> vertex 0 kept, bit 1 <-> vertex 1 kept: nd * (1, M00 + M11,
-// M22 + M33, the four minors of one row/column of each).
+// M22 + M33, the four minors of one row/column of each). The sum of the four
+// 2 x 2 minors is (M00 + M11)(M22 + M33) minus the four off-block products.
 template <int S>
 __device__ __forceinline__ void nd_bottom_sum(const double *cur, const double *nd, double *out, int lane) {
     constexpr int nodes = nd_pow3(S - 2);
     for (int k = lane; k < nodes; k += 32) {
-        const double *M = cur + 16 * k;
+        const double *M = cur + 12 * k;
         const double d = nd[k];
-        const double m4 = fma(M[0], M[10], -M[2] * M[8]) + fma(M[5], M[10], -M[6] * M[9]) +
-                          fma(M[0], M[15], -M[3] * M[12]) + fma(M[5], M[15], -M[7] * M[13]);
+        const double a = M[0] + M[3], b = M[8] + M[11];
+        const double x = fma(M[1], M[6], fma(M[4], M[7], fma(M[2], M[9], M[5] * M[10])));
         double2 *o = reinterpret_cast<double2 *>(out + 4 * k);
-        o[0] = make_double2(d, d * (M[0] + M[5]));
-        o[1] = make_double2(d * (M[10] + M[15]), d * m4);
+        o[0] = make_double2(d, d * a);
+        o[1] = make_double2(d * b, d * fma(a, b, -x));
     }
 }
 
@@ -212,11 +225,11 @@ __device__ __forceinline__ void nd_tail(double det0, double *gout, NdWarpSmem &w
         if (lane == 0) {
             if constexpr (kSum) {
                 gout[0] += det0;
-                gout[1] += det0 * (w.bufE[0] + w.bufE[3]);
+                gout[1] += det0 * (w.bufE[0] + w.bufE[1]);
             } else {
                 gout[0] = det0;
                 gout[1] = det0 * w.bufE[0];
-                gout[2] = det0 * w.bufE[3];
+                gout[2] = det0 * w.bufE[1];
             }
         }
     } else {
@@ -255,7 +268,10 @@ __device__ __forceinline__ void nd_matrix(const double *A, int n, double *out, u
     __syncwarp();
     if (!nonfin) {
         if (D == 0) {
-            for (int e = lane; e < m0 * m0; e += 32) w.bufE[e] = A[e];
+            for (int e = lane; e < m0 * (m0 - 1); e += 32) {  // compact tail root
+                const int r = e / (m0 - 1), c = e - r * (m0 - 1);
+                w.bufE[e] = A[r * m0 + c + (c >= (r ^ 1))];
+            }
             __syncwarp();
             nd_tail_order<kNdTail, kSum>(n, out, w, lane, bad);
         } else {
@@ -291,9 +307,12 @@ __device__ __forceinline__ void nd_matrix(const double *A, int n, double *out, u
                         const double iv = nd_inv(piv, bad);
                         for (int r = lane; r < m2; r += 32) w.f[r] = P[r * st + pi] * iv;
                         __syncwarp();
-                        for (int e = lane; e < m2 * m2; e += 32) {
-                            const int r = e / m2, q = e - r * m2;
-                            dst[e] = fma(-w.f[r], P[pi * st + q], P[r * st + q]);
+                        // the entries a minor can read (no within-block off-diagonals): dense on
+                        // the stack, compact in the tail root
+                        const bool root = d + 1 == D;
+                        for (int e = lane; e < m2 * (m2 - 1); e += 32) {
+                            const int r = e / (m2 - 1), c = e - r * (m2 - 1), q = c + (c >= (r ^ 1));
+                            dst[root ? e : r * m2 + q] = fma(-w.f[r], P[pi * st + q], P[r * st + q]);
                         }
                         __syncwarp();
                         if (lane == 0) {
@@ -303,10 +322,10 @@ __device__ __forceinline__ void nd_matrix(const double *A, int n, double *out, u
                             w.smask[d + 1] = w.smask[d] | (1 << (n - 1 - d));
                         }
                     } else {
-                        if (d + 1 == D) {  // the tail root must be dense
-                            for (int e = lane; e < m2 * m2; e += 32) {
-                                const int r = e / m2, q = e - r * m2;
-                                w.bufE[e] = P[r * st + q];
+                        if (d + 1 == D) {  // the tail root is a compact copy
+                            for (int e = lane; e < m2 * (m2 - 1); e += 32) {
+                                const int r = e / (m2 - 1), c = e - r * (m2 - 1);
+                                w.bufE[e] = P[r * st + c + (c >= (r ^ 1))];
                             }
                         }
                         if (lane == 0) {
