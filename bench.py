@@ -154,8 +154,11 @@ class ClockSampler:
 
 def keldysh_flops(n: int) -> int:
     """Algorithmic flops of one Keldysh sum: complex FMAs of every Schur step of
-    the XOR tree (8 real flops each), pivot reciprocals/products, leaf sums."""
-    return (8 * sum((1 << (l + 1)) * (2 * (n - l - 1)) ** 2 for l in range(n - 1))
+    the XOR tree (8 real flops each) over the m2 (m2 - 1) entries of a child of
+    size m2 that a minor can read (an XOR minor keeps one row and column of a
+    2 x 2 block, so the blocks' off-diagonal entries are never read), pivot
+    reciprocals/products, leaf sums."""
+    return (8 * sum((1 << (l + 1)) * (2 * (n - l - 1)) * (2 * (n - l - 1) - 1) for l in range(n - 1))
             + 12 * (2 ** (n + 1) - 2) + 2 * 2 ** n)
 
 

@@ -41,23 +41,31 @@
 namespace apm {
 
 // Tail size S (vertices expanded breadth first in shared memory) and warps per
-// CTA; S = 7 needs 20 KB of shared memory per warp, so its CTA holds the 11
-// warps that fit on one SM.
+// CTA; S = 7 needs 17.3 KB of shared memory per warp, so its CTA holds the 12
+// warps that fit on one SM (13 would fit the shared memory but not the
+// registers, 168 per thread).
 #ifndef APM_KEL_TAIL
 #define APM_KEL_TAIL 7
 #endif
 constexpr int kKelTail = APM_KEL_TAIL;
 static_assert(kKelTail == 6 || kKelTail == 7, "tail of 6 or 7 vertices");
-constexpr int kKelWarps = kKelTail == 6 ? 4 : 11;
+constexpr int kKelWarps = kKelTail == 6 ? 4 : 12;
+// Tail nodes are stored without the off-diagonal entries of the 2 x 2 blocks:
+// an XOR minor keeps one row and column of a block, and a Schur update of
+// entry (r, q) reads only (r, q), (r, p), (p, q) and (p, p) with the pivot p in
+// another block, so entries (2i, 2i+1) and (2i+1, 2i) are never read. Row r of
+// a node of size m holds its m - 1 columns q != r ^ 1 in order (compact column
+// c <-> q = c + (c >= (r ^ 1))); entry (r+2, q+2) of a node has the compact
+// column of (r, q) in its child, plus 2.
 // Tail of S vertices: the root (2S x 2S) and the outputs of the odd levels sit
 // in bufE, the outputs of the even levels in bufO; level J (J = 0..S-4) makes
-// 2^(J+1) nodes of size 2(S-J-1). S = 6: bufE 144, 256; bufO 200, 288.
-// S = 7: bufE 196, 400, 576; bufO 288, 512.
+// 2^(J+1) nodes of size m = 2(S-J-1), m(m-1) entries each. S = 6: bufE 132,
+// 224; bufO 180, 240. S = 7: bufE 182, 360, 480; bufO 264, 448.
 __host__ __device__ constexpr int kel_level_entries(int S, int J) {
-    return (2 << J) * (2 * (S - J - 1)) * (2 * (S - J - 1));
+    return (2 << J) * (2 * (S - J - 1)) * (2 * (S - J - 1) - 1);
 }
 __host__ __device__ constexpr int kel_buf_entries(int S, int first) {
-    int b = first == 1 ? 4 * S * S : 0;
+    int b = first == 1 ? 2 * S * (2 * S - 1) : 0;
     for (int J = first; J <= S - 4; J += 2) b = b > kel_level_entries(S, J) ? b : kel_level_entries(S, J);
     return b;
 }
@@ -73,8 +81,8 @@ __host__ __device__ constexpr int kel_fac_entries(int S) {
 constexpr int kKelBufE = kel_buf_entries(kKelTail, 1);
 constexpr int kKelBufO = kel_buf_entries(kKelTail, 0);
 constexpr int kKelFac = kel_fac_entries(kKelTail);
-static_assert(kKelTail != 6 || (kKelBufE == 256 && kKelBufO == 288 && kKelFac == 48), "6-vertex tail");
-static_assert(kKelTail != 7 || (kKelBufE == 576 && kKelBufO == 512 && kKelFac == 96), "7-vertex tail");
+static_assert(kKelTail != 6 || (kKelBufE == 224 && kKelBufO == 240 && kKelFac == 48), "6-vertex tail");
+static_assert(kKelTail != 7 || (kKelBufE == 480 && kKelBufO == 448 && kKelFac == 96), "7-vertex tail");
 
 struct KelWarpSmem {
     double2 bufE[kKelBufE];
@@ -100,17 +108,19 @@ __host__ __device__ constexpr size_t kel_stack_entries(int n) {
     return t;
 }
 
-// One Schur step of the depth-first part: src (m x m) -> dst ((m-2) x (m-2)).
-__device__ __forceinline__ void kel_schur(const double2 *src, int m, int alpha, double2 *dst,
+// One Schur step of the depth-first part: src (m x m, dense) -> dst ((m-2) x
+// (m-2)): the entries a minor can read, dense on the stack (the blocks'
+// off-diagonal entries left unwritten) or compact in the tail root.
+__device__ __forceinline__ void kel_schur(const double2 *src, int m, int alpha, double2 *dst, bool root,
                                           KelWarpSmem &w, int lane, double2 &piv, int &bad) {
     piv = src[alpha * m + alpha];
     const double2 iv = crcp(piv, bad);
     const int m2 = m - 2;
     for (int r = lane; r < m2; r += 32) w.fac[r] = cmul(src[(r + 2) * m + alpha], iv);
     __syncwarp();
-    for (int e = lane; e < m2 * m2; e += 32) {
-        const int r = e / m2, q = e - r * m2;
-        dst[e] = cfms(w.fac[r], src[alpha * m + q + 2], src[(r + 2) * m + q + 2]);
+    for (int e = lane; e < m2 * (m2 - 1); e += 32) {
+        const int r = e / (m2 - 1), c = e - r * (m2 - 1), q = c + (c >= (r ^ 1));
+        dst[root ? e : r * m2 + q] = cfms(w.fac[r], src[alpha * m + q + 2], src[(r + 2) * m + q + 2]);
     }
     __syncwarp();
 }
@@ -123,16 +133,18 @@ struct KelAcc {
 };
 
 // One breadth-first level J of a tail over S vertices: the 2^J nodes of size
-// m = 2(S-J) in cur give 2^(J+1) children of size m-2 in nxt.
+// m = 2(S-J) in cur give 2^(J+1) children of size m-2 in nxt (compact layout:
+// the pivot (alpha, alpha) is compact column 0 of row alpha, entry (r+2, alpha)
+// column alpha of row r+2, entry (alpha, q+2) column q+1 of row alpha).
 template <int S, int J>
 __device__ __forceinline__ void kel_tail_level(const double2 *cur, double2 *nxt, bool want_part, bool sgn,
                                                KelWarpSmem &w, int lane, int &bad, KelAcc &acc) {
-    constexpr int m = 2 * (S - J), m2 = m - 2, mm = m * m, mm2 = m2 * m2;
+    constexpr int m = 2 * (S - J), m2 = m - 2, rl = m - 1, rl2 = m2 - 1, mm = m * rl, mm2 = m2 * rl2;
     constexpr int nchild = 2 << J;
     if (lane < nchild) {
         const int alpha = lane & 1;
         const double2 *P = cur + (lane >> 1) * mm;
-        const double2 piv = P[alpha * m + alpha];
+        const double2 piv = P[alpha * rl];
         w.inv[lane] = crcp(piv, bad);
         const double2 nd = cneg_if(cmul(w.ndet[J & 1][lane >> 1], piv), sgn && alpha);
         w.ndet[(J + 1) & 1][lane] = nd;
@@ -142,38 +154,41 @@ __device__ __forceinline__ void kel_tail_level(const double2 *cur, double2 *nxt,
     for (int idx = lane; idx < nchild * m2; idx += 32) {
         const int c = idx / m2, r = idx - c * m2, alpha = c & 1;
         const double2 *P = cur + (c >> 1) * mm;
-        w.fac[idx] = cmul(P[(r + 2) * m + alpha], w.inv[c]);
+        w.fac[idx] = cmul(P[(r + 2) * rl + alpha], w.inv[c]);
     }
     __syncwarp();
     for (int e = lane; e < nchild * mm2; e += 32) {
-        const int c = e / mm2, rem = e - c * mm2, r = rem / m2, q = rem - r * m2, alpha = c & 1;
+        const int c = e / mm2, rem = e - c * mm2, r = rem / rl2, cc = rem - r * rl2, alpha = c & 1;
+        const int q = cc + (cc >= (r ^ 1));
         const double2 *P = cur + (c >> 1) * mm;
-        nxt[e] = cfms(w.fac[c * m2 + r], P[alpha * m + q + 2], P[(r + 2) * m + q + 2]);
+        nxt[e] = cfms(w.fac[c * m2 + r], P[alpha * rl + q + 1], P[(r + 2) * rl + cc + 2]);
     }
     __syncwarp();
 }
 
-// Closed form for the last three vertices of NODES nodes (6 x 6 each, node
-// determinants nd[]): four lanes per node, lane (a0, a1) forms the two 3 x 3
-// XOR minors with rows/columns (0,a0), (1,a1), (2,a2), a2 = 0, 1, by expansion
-// along the last row; the leading 2 x 2 cofactor and the leading entry are the
-// node's contributions to the two orders below. No pivots, no divisions.
+// Closed form for the last three vertices of NODES nodes (6 x 6 each, compact
+// rows of 5, node determinants nd[]): four lanes per node, lane (a0, a1) forms
+// the two 3 x 3 XOR minors with rows/columns (0,a0), (1,a1), (2,a2), a2 = 0, 1,
+// by expansion along the last row; the leading 2 x 2 cofactor and the leading
+// entry are the node's contributions to the two orders below. No pivots, no
+// divisions. Entry (i, j) of another block than i's is at compact column
+// j - (j > i), the diagonal entry (i, i) at column i & ~1.
 template <int NODES>
 __device__ __forceinline__ void kel_closed3(const double2 *cur, const double2 *nd, bool want_part, bool sgn,
                                             int lane, KelAcc &acc) {
     for (int idx = lane; idx < 4 * NODES; idx += 32) {
         const int k = idx >> 2, a0 = idx & 1, a1 = (idx >> 1) & 1;
-        const double2 *M = cur + k * 36;
+        const double2 *M = cur + k * 30;
         const int r0 = a0, r1 = 2 + a1;
-        const double2 A = M[r0 * 6 + r0], B = M[r0 * 6 + r1];
-        const double2 Dv = M[r1 * 6 + r0], E = M[r1 * 6 + r1];
+        const double2 A = M[r0 * 5], B = M[r0 * 5 + r1 - 1];
+        const double2 Dv = M[r1 * 5 + r0], E = M[r1 * 5 + 2];
         const double2 C2 = cfms(B, Dv, cmul(A, E));  // A E - B D
         double2 tot = make_double2(0.0, 0.0);
 #pragma unroll
         for (int a2 = 0; a2 < 2; ++a2) {
             const int r2 = 4 + a2;
-            const double2 C = M[r0 * 6 + r2], F = M[r1 * 6 + r2];
-            const double2 G = M[r2 * 6 + r0], H = M[r2 * 6 + r1], Iv = M[r2 * 6 + r2];
+            const double2 C = M[r0 * 5 + r2 - 1], F = M[r1 * 5 + r2 - 1];
+            const double2 G = M[r2 * 5 + r0], H = M[r2 * 5 + r1], Iv = M[r2 * 5 + 4];
             const double2 u = cfms(C, E, cmul(B, F));   // B F - C E
             const double2 v = cfms(C, Dv, cmul(A, F));  // A F - C D
             const double2 det = cfma(Iv, C2, cfms(H, v, cmul(G, u)));
@@ -188,20 +203,20 @@ __device__ __forceinline__ void kel_closed3(const double2 *cur, const double2 *n
     }
 }
 
-// Orders 1 and 2 (one node, the whole matrix).
+// Orders 1 and 2 (one node, the whole matrix; compact rows of 3 and 1).
 __device__ __forceinline__ void kel_closed2(const double2 *M, double2 det0, bool want_part, bool sgn, int lane,
                                             KelAcc &acc) {
     if (lane < 4) {
         const int a0 = lane & 1, a1 = lane >> 1;
-        const double2 A = M[a0 * 4 + a0], B = M[a0 * 4 + 2 + a1];
-        const double2 Dv = M[(2 + a1) * 4 + a0], E = M[(2 + a1) * 4 + 2 + a1];
+        const double2 A = M[a0 * 3], B = M[a0 * 3 + 1 + a1];
+        const double2 Dv = M[(2 + a1) * 3 + a0], E = M[(2 + a1) * 3 + 2];
         const double2 dk = cneg_if(det0, sgn && (a0 ^ a1));
         acc.v[0] = cfma(dk, cfms(B, Dv, cmul(A, E)), acc.v[0]);
         if (want_part && a1 == 0) acc.v[1] = cfma(dk, A, acc.v[1]);
     }
 }
 __device__ __forceinline__ void kel_closed1(const double2 *M, double2 det0, bool sgn, int lane, KelAcc &acc) {
-    if (lane == 0) acc.v[0] = cfma(det0, sgn ? csub(M[0], M[3]) : cadd(M[0], M[3]), acc.v[0]);
+    if (lane == 0) acc.v[0] = cfma(det0, sgn ? csub(M[0], M[1]) : cadd(M[0], M[1]), acc.v[0]);
 }
 
 template <int S, int J>
@@ -265,7 +280,10 @@ __device__ __forceinline__ void kel_matrix(const double2 *A, int n, bool sgn, bo
     if (lane == 0) w.pdet[0] = make_double2(1.0, 0.0);
     __syncwarp();
     if (D == 0) {
-        for (int e = lane; e < m0 * m0; e += 32) w.bufE[e] = A[e];
+        for (int e = lane; e < m0 * (m0 - 1); e += 32) {  // compact tail root
+            const int r = e / (m0 - 1), c = e - r * (m0 - 1);
+            w.bufE[e] = A[r * m0 + c + (c >= (r ^ 1))];
+        }
         __syncwarp();
         kel_tail_order<kKelTail>(n, want_part, sgn, w, lane, bad, acc);
     } else {
@@ -282,7 +300,7 @@ __device__ __forceinline__ void kel_matrix(const double2 *A, int n, bool sgn, bo
                 if (d > 0) off += static_cast<size_t>(m) * m;
                 double2 *dst = (d + 1 == D) ? w.bufE : stack + off;
                 double2 piv;
-                kel_schur(src, m, alpha, dst, w, lane, piv, bad);
+                kel_schur(src, m, alpha, dst, d + 1 == D, w, lane, piv, bad);
                 if (lane == 0) {
                     const double2 pd = cneg_if(cmul(w.pdet[d], piv), sgn && alpha);
                     w.pdet[d + 1] = pd;

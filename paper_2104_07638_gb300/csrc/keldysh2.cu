@@ -25,9 +25,12 @@
 namespace apm {
 
 constexpr int kK2Tail = 6;
-constexpr int kK2Warps = 11;  // 19.6 KB of shared memory per warp: 11 warps fill an SM
-// per spin: bufE holds the root (144) and level 1 (256), bufO levels 0 (200) and 2 (288)
-constexpr int kK2BufE = 256, kK2BufO = 288;
+constexpr int kK2Warps = 12;  // 17 KB of shared memory per warp, 168 registers per thread: 12 warps fill an SM
+// Tail nodes are stored as in keldysh.cu, without the off-diagonal entries of
+// the 2 x 2 blocks (never read by an XOR minor): row r of a node of size m
+// holds its m - 1 columns q != r ^ 1 in order. Per spin: bufE holds the root
+// (132) and level 1 (224), bufO levels 0 (180) and 2 (240).
+constexpr int kK2BufE = 224, kK2BufO = 240;
 constexpr int kK2Fac = 48;  // row factors per spin: 8 children x 6 rows at level 2; 30 for a depth-first step
 constexpr int kK2MaxN = 16;
 
@@ -54,22 +57,25 @@ struct K2Acc {
 };
 
 // One breadth-first level J of a tail over S vertices, both spins: the 2^J node
-// pairs of size m = 2(S-J) in cur give 2^(J+1) children of size m-2 in nxt.
+// pairs of size m = 2(S-J) in cur give 2^(J+1) children of size m-2 in nxt
+// (compact layout: the pivot (alpha, alpha) is compact column 0 of row alpha,
+// entry (r+2, alpha) column alpha of row r+2, entry (alpha, q+2) column q+1 of
+// row alpha, entry (r+2, q+2) the child's compact column of (r, q) plus 2).
 template <int S, int J>
 __device__ __forceinline__ void k2_tail_level(const double2 *cur0, const double2 *cur1, double2 *nxt0,
                                               double2 *nxt1, bool want_part, bool sgn, K2WarpSmem &w, int lane,
                                               int &bad, K2Acc &acc) {
-    constexpr int m = 2 * (S - J), m2 = m - 2, mm = m * m, mm2 = m2 * m2;
+    constexpr int m = 2 * (S - J), m2 = m - 2, rl = m - 1, rl2 = m2 - 1, mm = m * rl, mm2 = m2 * rl2;
     constexpr int nchild = 2 << J;
     static_assert(2 * nchild <= 32, "a lane per child and spin");
     if (lane < 2 * nchild) {  // lanes [0, nchild) spin up, [nchild, 2 nchild) spin down
         const int sp = lane >= nchild ? 1 : 0, c = lane - sp * nchild, alpha = c & 1;
-        w.inv[sp][c] = crcp((sp ? cur1 : cur0)[(c >> 1) * mm + alpha * m + alpha], bad);
+        w.inv[sp][c] = crcp((sp ? cur1 : cur0)[(c >> 1) * mm + alpha * rl], bad);
     }
     if (lane < nchild) {
         const int alpha = lane & 1;
-        const double2 p0 = cur0[(lane >> 1) * mm + alpha * m + alpha];
-        const double2 p1 = cur1[(lane >> 1) * mm + alpha * m + alpha];
+        const double2 p0 = cur0[(lane >> 1) * mm + alpha * rl];
+        const double2 p1 = cur1[(lane >> 1) * mm + alpha * rl];
         const double2 nd = cneg_if(cmul(cmul(w.ndet[J & 1][lane >> 1], p0), p1), sgn && alpha);
         w.ndet[(J + 1) & 1][lane] = nd;
         if (want_part) acc.v[S - 1 - J] = cadd(acc.v[S - 1 - J], nd);
@@ -79,35 +85,37 @@ __device__ __forceinline__ void k2_tail_level(const double2 *cur0, const double2
         const int sp = idx / (nchild * m2), i = idx - sp * nchild * m2;
         const int c = i / m2, r = i - c * m2, alpha = c & 1;
         const double2 *P = (sp ? cur1 : cur0) + (c >> 1) * mm;
-        w.fac[sp][i] = cmul(P[(r + 2) * m + alpha], w.inv[sp][c]);
+        w.fac[sp][i] = cmul(P[(r + 2) * rl + alpha], w.inv[sp][c]);
     }
     __syncwarp();
     for (int e = lane; e < 2 * nchild * mm2; e += 32) {
         const int sp = e / (nchild * mm2), i = e - sp * nchild * mm2;
-        const int c = i / mm2, rem = i - c * mm2, r = rem / m2, q = rem - r * m2, alpha = c & 1;
+        const int c = i / mm2, rem = i - c * mm2, r = rem / rl2, cc = rem - r * rl2, alpha = c & 1;
+        const int q = cc + (cc >= (r ^ 1));
         const double2 *P = (sp ? cur1 : cur0) + (c >> 1) * mm;
-        (sp ? nxt1 : nxt0)[i] = cfms(w.fac[sp][c * m2 + r], P[alpha * m + q + 2], P[(r + 2) * m + q + 2]);
+        (sp ? nxt1 : nxt0)[i] = cfms(w.fac[sp][c * m2 + r], P[alpha * rl + q + 1], P[(r + 2) * rl + cc + 2]);
     }
     __syncwarp();
 }
 
-// Per spin, for lane (a0, a1) of a 6 x 6 node: the leading entry A, the leading
-// 2 x 2 cofactor C2 and the two 3 x 3 XOR minors (a2 = 0, 1), by expansion
-// along the last row.
+// Per spin, for lane (a0, a1) of a 6 x 6 node (compact rows of 5): the leading
+// entry A, the leading 2 x 2 cofactor C2 and the two 3 x 3 XOR minors (a2 = 0,
+// 1), by expansion along the last row. Entry (i, j) of another block than i's
+// is at compact column j - (j > i), the diagonal entry (i, i) at i & ~1.
 struct K2Minors {
     double2 A, C2, d0, d1;
 };
 __device__ __forceinline__ K2Minors k2_minors3(const double2 *M, int a0, int a1) {
     const int r0 = a0, r1 = 2 + a1;
     K2Minors o;
-    o.A = M[r0 * 6 + r0];
-    const double2 B = M[r0 * 6 + r1], Dv = M[r1 * 6 + r0], E = M[r1 * 6 + r1];
+    o.A = M[r0 * 5];
+    const double2 B = M[r0 * 5 + r1 - 1], Dv = M[r1 * 5 + r0], E = M[r1 * 5 + 2];
     o.C2 = cfms(B, Dv, cmul(o.A, E));
 #pragma unroll
     for (int a2 = 0; a2 < 2; ++a2) {
         const int r2 = 4 + a2;
-        const double2 C = M[r0 * 6 + r2], F = M[r1 * 6 + r2];
-        const double2 G = M[r2 * 6 + r0], H = M[r2 * 6 + r1], Iv = M[r2 * 6 + r2];
+        const double2 C = M[r0 * 5 + r2 - 1], F = M[r1 * 5 + r2 - 1];
+        const double2 G = M[r2 * 5 + r0], H = M[r2 * 5 + r1], Iv = M[r2 * 5 + 4];
         const double2 u = cfms(C, E, cmul(B, F));
         const double2 v = cfms(C, Dv, cmul(o.A, F));
         const double2 det = cfma(Iv, o.C2, cfms(H, v, cmul(G, u)));
@@ -124,8 +132,8 @@ __device__ __forceinline__ void k2_closed3(const double2 *cur0, const double2 *c
                                            bool want_part, bool sgn, int lane, K2Acc &acc) {
     for (int idx = lane; idx < 4 * NODES; idx += 32) {
         const int k = idx >> 2, a0 = idx & 1, a1 = (idx >> 1) & 1;
-        const K2Minors u = k2_minors3(cur0 + k * 36, a0, a1);
-        const K2Minors d = k2_minors3(cur1 + k * 36, a0, a1);
+        const K2Minors u = k2_minors3(cur0 + k * 30, a0, a1);
+        const K2Minors d = k2_minors3(cur1 + k * 30, a0, a1);
         const double2 t0 = cmul(u.d0, d.d0), t1 = cmul(u.d1, d.d1);
         const double2 tot = sgn ? csub(t0, t1) : cadd(t0, t1);
         const double2 dk = cneg_if(nd[k], sgn && (a0 ^ a1));
@@ -137,7 +145,7 @@ __device__ __forceinline__ void k2_closed3(const double2 *cur0, const double2 *c
     }
 }
 
-// Orders 1 and 2 (one node pair, the whole matrices).
+// Orders 1 and 2 (one node pair, the whole matrices; compact rows of 3 and 1).
 __device__ __forceinline__ void k2_closed2(const double2 *M0, const double2 *M1, double2 det0, bool want_part,
                                            bool sgn, int lane, K2Acc &acc) {
     if (lane < 4) {
@@ -146,8 +154,8 @@ __device__ __forceinline__ void k2_closed2(const double2 *M0, const double2 *M1,
 #pragma unroll
         for (int sp = 0; sp < 2; ++sp) {
             const double2 *M = sp ? M1 : M0;
-            A[sp] = M[a0 * 4 + a0];
-            d[sp] = cfms(M[a0 * 4 + 2 + a1], M[(2 + a1) * 4 + a0], cmul(A[sp], M[(2 + a1) * 4 + 2 + a1]));
+            A[sp] = M[a0 * 3];
+            d[sp] = cfms(M[a0 * 3 + 1 + a1], M[(2 + a1) * 3 + a0], cmul(A[sp], M[(2 + a1) * 3 + 2]));
         }
         const double2 dk = cneg_if(det0, sgn && (a0 ^ a1));
         acc.v[0] = cfma(dk, cmul(d[0], d[1]), acc.v[0]);
@@ -157,7 +165,7 @@ __device__ __forceinline__ void k2_closed2(const double2 *M0, const double2 *M1,
 __device__ __forceinline__ void k2_closed1(const double2 *M0, const double2 *M1, double2 det0, bool sgn, int lane,
                                            K2Acc &acc) {
     if (lane == 0) {
-        const double2 t0 = cmul(M0[0], M1[0]), t1 = cmul(M0[3], M1[3]);
+        const double2 t0 = cmul(M0[0], M1[0]), t1 = cmul(M0[1], M1[1]);
         acc.v[0] = cfma(det0, sgn ? csub(t0, t1) : cadd(t0, t1), acc.v[0]);
     }
 }
@@ -197,10 +205,12 @@ __device__ __forceinline__ void k2_tail_order(int n, bool want_part, bool sgn, K
     }
 }
 
-// One depth-first Schur step for both spins: src (m x m) -> dst ((m-2) x (m-2)).
+// One depth-first Schur step for both spins: src (m x m, dense) -> dst ((m-2) x
+// (m-2)): the entries a minor can read, dense on the stack (the blocks'
+// off-diagonal entries left unwritten) or compact in the tail root.
 __device__ __forceinline__ void k2_schur(const double2 *s0, const double2 *s1, int m, int alpha, double2 *d0,
-                                         double2 *d1, K2WarpSmem &w, int lane, double2 &p0, double2 &p1,
-                                         int &bad) {
+                                         double2 *d1, bool root, K2WarpSmem &w, int lane, double2 &p0,
+                                         double2 &p1, int &bad) {
     p0 = s0[alpha * m + alpha];
     p1 = s1[alpha * m + alpha];
     // one reciprocal per lane (even lanes spin up, odd lanes spin down), then
@@ -214,10 +224,11 @@ __device__ __forceinline__ void k2_schur(const double2 *s0, const double2 *s1, i
         w.fac[sp][r] = cmul((sp ? s1 : s0)[(r + 2) * m + alpha], sp ? iv1 : iv0);
     }
     __syncwarp();
-    for (int e = lane; e < 2 * m2 * m2; e += 32) {
-        const int sp = e >= m2 * m2, i = e - sp * m2 * m2, r = i / m2, q = i - r * m2;
+    const int rl2 = m2 - 1, mm2 = m2 * rl2;
+    for (int e = lane; e < 2 * mm2; e += 32) {
+        const int sp = e >= mm2, i = e - sp * mm2, r = i / rl2, c = i - r * rl2, q = c + (c >= (r ^ 1));
         const double2 *P = sp ? s1 : s0;
-        (sp ? d1 : d0)[i] = cfms(w.fac[sp][r], P[alpha * m + q + 2], P[(r + 2) * m + q + 2]);
+        (sp ? d1 : d0)[root ? i : r * m2 + q] = cfms(w.fac[sp][r], P[alpha * m + q + 2], P[(r + 2) * m + q + 2]);
     }
     __syncwarp();
 }
@@ -244,9 +255,10 @@ __device__ __forceinline__ void k2_matrix(const double2 *Au, const double2 *Ad, 
     if (lane == 0) w.pdet[0] = make_double2(1.0, 0.0);
     __syncwarp();
     if (D == 0) {
-        for (int e = lane; e < m0 * m0; e += 32) {
-            w.bufE[0][e] = Au[e];
-            w.bufE[1][e] = Ad[e];
+        for (int e = lane; e < m0 * (m0 - 1); e += 32) {  // compact tail roots
+            const int r = e / (m0 - 1), c = e - r * (m0 - 1), q = c + (c >= (r ^ 1));
+            w.bufE[0][e] = Au[r * m0 + q];
+            w.bufE[1][e] = Ad[r * m0 + q];
         }
         __syncwarp();
         k2_tail_order<kK2Tail>(n, want_part, sgn, w, lane, bad, acc);
@@ -265,7 +277,7 @@ __device__ __forceinline__ void k2_matrix(const double2 *Au, const double2 *Ad, 
                 double2 *t0 = (d + 1 == D) ? w.bufE[0] : stack + off;
                 double2 *t1 = (d + 1 == D) ? w.bufE[1] : stack + half + off;
                 double2 p0, p1;
-                k2_schur(s0, s1, m, alpha, t0, t1, w, lane, p0, p1, bad);
+                k2_schur(s0, s1, m, alpha, t0, t1, d + 1 == D, w, lane, p0, p1, bad);
                 if (lane == 0) {
                     const double2 pd = cneg_if(cmul(cmul(w.pdet[d], p0), p1), sgn && alpha);
                     w.pdet[d + 1] = pd;

@@ -53,13 +53,30 @@ def test_fast_subset_convolution_count_and_switch():
             assert bench.cdet_path_flops(n) == bench.flops_per_set(n) - bench.sc_flops(n) + bench.fsc_flops(n)
 
 
+def readable_entries(m):
+    """Entries of an m x m node (m even) that a minor keeping at most one row and
+    column of each 2 x 2 diagonal block can contain: the diagonal and every
+    entry between two different blocks."""
+    return sum(1 for r in range(m) for q in range(m) if r == q or r // 2 != q // 2)
+
+
 def test_keldysh_tree_count():
     """Complex Schur updates of the XOR tree (8 real flops each): every node at
-    depth l has two children, each an update of order 2(n - l - 1)."""
+    depth l has two children, each an update of the readable entries of order
+    2(n - l - 1)."""
     for n in range(1, 9):
-        cfma = sum((1 << l) * 2 * (2 * (n - l - 1)) ** 2 for l in range(n - 1))
+        cfma = sum((1 << l) * 2 * readable_entries(2 * (n - l - 1)) for l in range(n - 1))
         children = sum(1 << (l + 1) for l in range(n))   # a pivot reciprocal and product each (12 flops)
         assert bench.keldysh_flops(n) == 8 * cfma + 12 * children + 2 * (1 << n)
+
+
+def test_nand_tree_count():
+    """The ternary tree: every node at depth l has two kept children of order
+    m = 2(n - l - 1), each a rank-1 update of its readable entries (an FMA), m
+    row factors and 3 flops for the pivot reciprocal and node product."""
+    for n in range(1, 9):
+        per_child = [2 * readable_entries(2 * (n - l - 1)) + 2 * (n - l - 1) + 3 for l in range(n)]
+        assert bench.nand_flops(n) == sum(3 ** l * 2 * per_child[l] for l in range(n))
 
 
 def test_throughput_helpers():
