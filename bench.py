@@ -598,30 +598,21 @@ def main():
     value = job_throughput(B, world, args.steps, dev_s)
     ms_per_step = 1000.0 * dev_s / args.steps
 
-    # ---- end to end through the public API from pinned host memory ----
-    # 32 chunks over 4 streams: the copies of one chunk overlap the kernels of
-    # the others, and only the last chunk's device->host copy is left exposed
+    # ---- end to end through the C ABI on host buffers (apm_cdet_connected_host) ----
+    # 32 chunks over 4 streams inside the library: the copies of one chunk
+    # overlap the kernels of the others, and only the last chunk's device->host
+    # copy is left exposed
     chunks, nstreams = 32, 4
     cb = B // chunks
     A_host = torch.as_tensor(A_np).pin_memory()
     c_host = torch.empty((B, N), dtype=torch.float64).pin_memory()
     m_host = torch.empty((B, N), dtype=torch.float64).pin_memory()
-    streams = [torch.cuda.Stream(dev) for _ in range(nstreams)]
-    A_d = [torch.empty((cb, n, n), dtype=torch.float64, device=dev) for _ in range(nstreams)]
-    c_d = [torch.empty((cb, N), dtype=torch.float64, device=dev) for _ in range(nstreams)]
-    m_d = [torch.empty((cb, N), dtype=torch.float64, device=dev) for _ in range(nstreams)]
+    ws_host = torch.empty(max(apm.cdet_connected_host_workspace_size(n, cb, nstreams), 256), dtype=torch.uint8,
+                          device=dev)
 
     def e2e_step():
-        for k in range(chunks):
-            q = k % nstreams
-            sl = slice(k * cb, (k + 1) * cb)
-            with torch.cuda.stream(streams[q]):
-                A_d[q].copy_(A_host[sl], non_blocking=True)
-                apm.cdet_connected(A_d[q], out_c=c_d[q], out_minors=m_d[q])
-                c_host[sl].copy_(c_d[q], non_blocking=True)
-                m_host[sl].copy_(m_d[q], non_blocking=True)
-        for s in streams:
-            s.synchronize()
+        apm.cdet_connected_host(A_host, out_c=c_host, out_minors=m_host, chunk=cb, nstreams=nstreams,
+                                workspace=ws_host)
 
     e2e_step()
     torch.cuda.synchronize()

@@ -136,6 +136,47 @@ apm_status_t apm_cdet_connected(const double *A_up, const double *A_dn, int n, i
                                 const apm_pivot_opts *opt, uint32_t *status, void *workspace,
                                 size_t workspace_bytes, apm_stream_t stream);
 
+/* Most streams apm_cdet_connected_host runs its chunks on. */
+#define APM_HOST_MAX_STREAMS 8
+
+/*
+ * apm_cdet_connected_host -- apm_cdet_connected (Section V.A, Eq. recursion:
+ * the same arithmetic, bit for bit) on matrices and outputs in HOST memory. The
+ * transfer pipeline has no counterpart in the paper: the batch is cut into
+ * chunks of `chunk` matrices that go in turn to `nstreams` slots of the device
+ * workspace, each with a stream the call creates; a slot copies its chunk in,
+ * runs the kernels of apm_cdet_connected on it and copies the outputs back, so
+ * the copies of one chunk overlap the kernels of the others. The kernels
+ * only ever touch device memory. The exceptions to the conventions at the top
+ * of this header: A_up, A_dn, c, minors_out and status are host pointers (any
+ * alignment), and the call is blocking.
+ *   A_up, A_dn, n, batch, flags, opt: as apm_cdet_connected (host memory).
+ *   c, minors_out, status: host outputs, laid out as apm_cdet_connected's.
+ *   chunk      matrices per chunk, >= 1 (a value above batch acts as batch).
+ *   nstreams   1..APM_HOST_MAX_STREAMS.
+ *   workspace  device memory of the current device, 256-byte aligned, at least
+ *              apm_cdet_connected_host_workspace_size(n, chunk, nstreams,
+ *              A_dn != NULL) bytes: per slot the chunk's inputs, outputs and
+ *              status words and the kernels' scratch.
+ *   stream     work already queued on it is complete before the call touches
+ *              the workspace (NULL = the legacy default stream).
+ * Page-locked host memory (cudaHostAlloc, cudaHostRegister) lets the copies
+ * run asynchronously; pageable memory gives the same results with the copies
+ * serialised. Returns when every output is in host memory. Argument errors
+ * return before any copy; a CUDA error stops the pipeline, waits for the work
+ * already issued and returns APM_ERR_CUDA (outputs then partly written).
+ */
+apm_status_t apm_cdet_connected_host(const double *A_up, const double *A_dn, int n, int64_t batch,
+                                     int flags, double *c, double *minors_out,
+                                     const apm_pivot_opts *opt, uint32_t *status, int64_t chunk,
+                                     int nstreams, void *workspace, size_t workspace_bytes,
+                                     apm_stream_t stream);
+
+/* Device workspace bytes of apm_cdet_connected_host for these arguments
+ * (two_mats: 1 when A_dn is given). */
+apm_status_t apm_cdet_connected_host_workspace_size(int n, int64_t chunk, int nstreams, int two_mats,
+                                                    size_t *bytes);
+
 /*
  * apm_cdet_from_weights -- the CDet recursion (Eq. recursion) applied to given
  * weights a[S] (e.g. permanent minors for the bosonic connected sum of
@@ -282,8 +323,8 @@ apm_status_t apm_keldysh2_sum(const double *Mu, const double *Md, int n, int64_t
  * pool owns the memory), and plugin hosts that only pass device pointers in.
  * There is no counterpart in the paper; it is a packaging of the same kernel.
  *   Instead of a caller workspace, the depth-first stack uses a fixed array in
- *   device memory that belongs to the library: 605 warp slots (55 CTAs of 11
- *   warps) for orders up to 14, 26.3 MB, held on every GPU that loads the
+ *   device memory that belongs to the library: 600 warp slots (50 CTAs of 12
+ *   warps) for orders up to 14, 26.1 MB, held on every GPU that loads the
  *   library until the process exits; matrices are never split over warps here. Orders above 14 are rejected with APM_ERR_UNSUPPORTED_N (use
  *   apm_keldysh_sum with a workspace). The call allocates nothing.
  *   The first call on a device looks up the array's device address (once per

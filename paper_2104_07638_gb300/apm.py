@@ -60,6 +60,8 @@ def lib():
             sig = {
                 "apm_all_minors": [P, i32, i64, P, OPT, P, P, sz, P],
                 "apm_cdet_connected": [P, P, i32, i64, i32, P, P, OPT, P, P, sz, P],
+                "apm_cdet_connected_host": [P, P, i32, i64, i32, P, P, OPT, P, i64, i32, P, sz, P],
+                "apm_cdet_connected_host_workspace_size": [i32, i64, i32, i32, ctypes.POINTER(sz)],
                 "apm_cdet_from_weights": [P, i32, i64, P, P, sz, P],
                 "apm_cdet_from_weights_fsc": [P, i32, i64, P, P, sz, P],
                 "apm_keldysh_sum": [P, i32, i64, i32, P, P, P, P, sz, P],
@@ -184,6 +186,75 @@ def cdet_connected(A_up: torch.Tensor, A_dn: torch.Tensor | None = None, single_
     _check(lib().apm_cdet_connected(_ptr(A_up), _ptr(A_dn), n, b, flags, _ptr(c), _ptr(mo),
                                     _opts(piv_threshold, piv_shift), _ptr(st), _ptr(ws), nb,
                                     _stream(A_up)), "apm_cdet_connected")
+    res = [c]
+    if return_minors:
+        res.append(mo)
+    if return_status:
+        res.append(st)
+    return res[0] if len(res) == 1 else tuple(res)
+
+
+def _host_mat_batch(A: torch.Tensor, name="A"):
+    if not isinstance(A, torch.Tensor) or A.device.type != "cpu":
+        raise TypeError(f"{name} must be a CPU (host) tensor")
+    if A.dtype != torch.float64:
+        raise TypeError(f"{name} must be torch.float64")
+    if A.dim() == 2:
+        A = A.unsqueeze(0)
+    if A.dim() != 3 or A.shape[-1] != A.shape[-2]:
+        raise ValueError(f"{name} must be (batch, n, n)")
+    return A.contiguous()
+
+
+def cdet_connected_host_workspace_size(n: int, chunk: int, nstreams: int = 4, two_mats=False) -> int:
+    nb = ctypes.c_size_t(0)
+    _check(lib().apm_cdet_connected_host_workspace_size(n, chunk, nstreams, 1 if two_mats else 0,
+                                                        ctypes.byref(nb)),
+           "apm_cdet_connected_host_workspace_size")
+    return nb.value
+
+
+def cdet_connected_host(A_up: torch.Tensor, A_dn: torch.Tensor | None = None, single_det=False,
+                        return_minors=False, return_status=False, chunk=2048, nstreams=4, out_c=None,
+                        out_minors=None, workspace=None, device=None, piv_threshold=None, piv_shift=None):
+    """cdet_connected on matrices in host memory through apm_cdet_connected_host:
+    the library copies chunks in, runs the kernels and copies the outputs back
+    on its own streams, and returns when the outputs (CPU tensors, page-locked
+    when A_up is) are filled. workspace: a uint8 CUDA tensor of at least
+    cdet_connected_host_workspace_size bytes, allocated here when None."""
+    A_up = _host_mat_batch(A_up, "A_up")
+    b, n, _ = A_up.shape
+    if A_dn is not None:
+        A_dn = _host_mat_batch(A_dn, "A_dn")
+        if A_dn.shape != A_up.shape:
+            raise ValueError("A_dn must match A_up")
+    pin = A_up.is_pinned()
+    N = 1 << n
+
+    def host_out(t, shape, dtype, what):
+        if t is None:
+            return torch.empty(shape, dtype=dtype, pin_memory=pin)
+        if t.device.type != "cpu" or tuple(t.shape) != shape or t.dtype != dtype or not t.is_contiguous():
+            raise ValueError(f"{what} must be a contiguous CPU tensor {shape} {dtype}")
+        return t
+
+    c = host_out(out_c, (b, N), torch.float64, "out_c")
+    mo = None
+    if return_minors or out_minors is not None:
+        mo = host_out(out_minors, (b, 2, N) if A_dn is not None else (b, N), torch.float64, "out_minors")
+    st = torch.zeros(b, dtype=torch.int32, pin_memory=pin) if return_status else None
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    with torch.cuda.device(dev):
+        if workspace is None:
+            nb = cdet_connected_host_workspace_size(n, min(chunk, max(b, 1)), nstreams, A_dn is not None)
+            workspace = torch.empty(max(nb, 256), dtype=torch.uint8, device=dev)
+        if not workspace.is_cuda or workspace.dtype != torch.uint8:
+            raise TypeError("workspace must be a uint8 CUDA tensor")
+        flags = CDET_SINGLE_DET if single_det else 0
+        _check(lib().apm_cdet_connected_host(_ptr(A_up), _ptr(A_dn), n, b, flags, _ptr(c), _ptr(mo),
+                                             _opts(piv_threshold, piv_shift), _ptr(st), chunk, nstreams,
+                                             _ptr(workspace), workspace.numel(), _stream(workspace)),
+               "apm_cdet_connected_host")
     res = [c]
     if return_minors:
         res.append(mo)

@@ -58,6 +58,30 @@ apm_status_t cdet_common(apm::CdetArgs &a, void *workspace, size_t workspace_byt
     return e ? cuda_fail(e) : APM_OK;
 }
 
+size_t round256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
+
+// One slot of the host pipeline's workspace: byte sizes of its parts, each a
+// multiple of 256 so that every part stays aligned.
+struct HostSlot {
+    size_t a_up, a_dn, c, m, st, ws, total;
+};
+
+apm_status_t host_slot_layout(int n, int64_t chunk, bool two, HostSlot *L) {
+    const size_t N = static_cast<size_t>(1) << n, nn = static_cast<size_t>(n) * n;
+    const size_t cb = static_cast<size_t>(chunk), mats = two ? 2 : 1;
+    L->a_up = round256(cb * nn * sizeof(double));
+    L->a_dn = two ? L->a_up : 0;
+    L->c = round256(cb * N * sizeof(double));
+    L->m = round256(cb * mats * N * sizeof(double));
+    L->st = round256(cb * sizeof(uint32_t));
+    size_t ws = 0;
+    const apm_status_t s = apm_workspace_size(APM_OP_CDET, n, chunk, two ? 1 : 0, &ws);
+    if (s) return s;
+    L->ws = round256(ws);
+    L->total = L->a_up + L->a_dn + L->c + L->m + L->st + L->ws;
+    return APM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -105,6 +129,90 @@ apm_status_t apm_cdet_connected(const double *A_up, const double *A_dn, int n, i
     a.two_mats = A_dn ? 1 : 0;
     pivot_values(opt, &a.piv_thr, &a.piv_shift);
     return cdet_common(a, workspace, workspace_bytes, reinterpret_cast<cudaStream_t>(stream));
+}
+
+apm_status_t apm_cdet_connected_host_workspace_size(int n, int64_t chunk, int nstreams, int two_mats,
+                                                    size_t *bytes) {
+    if (!bytes) return APM_ERR_ARG;
+    *bytes = 0;
+    if (n < 1 || n > APM_MAX_N_MINORS) return APM_ERR_UNSUPPORTED_N;
+    if (chunk < 1 || nstreams < 1 || nstreams > APM_HOST_MAX_STREAMS) return APM_ERR_ARG;
+    HostSlot L;
+    const apm_status_t st = host_slot_layout(n, chunk, two_mats != 0, &L);
+    if (st) return st;
+    *bytes = L.total * static_cast<size_t>(nstreams);
+    return APM_OK;
+}
+
+apm_status_t apm_cdet_connected_host(const double *A_up, const double *A_dn, int n, int64_t batch, int flags,
+                                     double *c, double *minors_out, const apm_pivot_opts *opt,
+                                     uint32_t *status, int64_t chunk, int nstreams, void *workspace,
+                                     size_t workspace_bytes, apm_stream_t stream) {
+    if (n < 1 || n > APM_MAX_N_MINORS) return APM_ERR_UNSUPPORTED_N;
+    if (batch < 0 || chunk < 1 || nstreams < 1 || nstreams > APM_HOST_MAX_STREAMS ||
+        (flags & ~APM_CDET_SINGLE_DET))
+        return APM_ERR_ARG;
+    if ((flags & APM_CDET_SINGLE_DET) && A_dn) return APM_ERR_ARG;
+    if (batch == 0) return APM_OK;
+    if (!A_up || !c) return APM_ERR_ARG;
+    if (chunk > batch) chunk = batch;  // the workspace size does not grow as the chunk shrinks
+    const bool two = A_dn != nullptr;
+    HostSlot L;
+    apm_status_t res = host_slot_layout(n, chunk, two, &L);
+    if (res) return res;
+    if (!workspace || workspace_bytes < L.total * static_cast<size_t>(nstreams) ||
+        (reinterpret_cast<uintptr_t>(workspace) & 255u))
+        return APM_ERR_WORKSPACE;
+
+    const size_t N = static_cast<size_t>(1) << n, nn = static_cast<size_t>(n) * n, mats = two ? 2 : 1;
+
+    cudaStream_t ss[APM_HOST_MAX_STREAMS] = {};
+    int made = 0;
+    cudaError_t err = cudaSuccess;
+    cudaEvent_t ready = nullptr;
+    err = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
+    if (err == cudaSuccess) err = cudaEventRecord(ready, reinterpret_cast<cudaStream_t>(stream));
+    for (; err == cudaSuccess && made < nstreams; ++made) {
+        err = cudaStreamCreateWithFlags(&ss[made], cudaStreamNonBlocking);
+        if (err != cudaSuccess) break;
+        err = cudaStreamWaitEvent(ss[made], ready, 0);  // the caller's earlier work on the workspace
+    }
+    const int64_t nchunks = (batch + chunk - 1) / chunk;
+    // chunk k goes to slot k % nstreams: a slot's buffers are reused only by
+    // chunks on its own stream, so stream order keeps them apart
+    for (int64_t k = 0; err == cudaSuccess && res == APM_OK && k < nchunks; ++k) {
+        const int q = static_cast<int>(k % nstreams);
+        const int64_t b0 = k * chunk, cb = batch - b0 < chunk ? batch - b0 : chunk;
+        const size_t ub = static_cast<size_t>(b0), ucb = static_cast<size_t>(cb);
+        char *base = static_cast<char *>(workspace) + static_cast<size_t>(q) * L.total;
+        double *dA = reinterpret_cast<double *>(base);
+        double *dB = two ? reinterpret_cast<double *>(base + L.a_up) : nullptr;
+        double *dc = reinterpret_cast<double *>(base + L.a_up + L.a_dn);
+        double *dm = reinterpret_cast<double *>(base + L.a_up + L.a_dn + L.c);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(base + L.a_up + L.a_dn + L.c + L.m);
+        void *dws = L.ws ? static_cast<void *>(base + L.a_up + L.a_dn + L.c + L.m + L.st) : nullptr;
+        err = cudaMemcpyAsync(dA, A_up + ub * nn, ucb * nn * sizeof(double), cudaMemcpyHostToDevice, ss[q]);
+        if (err == cudaSuccess && two)
+            err = cudaMemcpyAsync(dB, A_dn + ub * nn, ucb * nn * sizeof(double), cudaMemcpyHostToDevice, ss[q]);
+        if (err != cudaSuccess) break;
+        res = apm_cdet_connected(dA, dB, n, cb, flags, dc, minors_out ? dm : nullptr, opt, status ? dst : nullptr,
+                                 dws, L.ws, reinterpret_cast<apm_stream_t>(ss[q]));
+        if (res != APM_OK) break;
+        err = cudaMemcpyAsync(c + ub * N, dc, ucb * N * sizeof(double), cudaMemcpyDeviceToHost, ss[q]);
+        if (err == cudaSuccess && minors_out)
+            err = cudaMemcpyAsync(minors_out + ub * mats * N, dm, ucb * mats * N * sizeof(double),
+                                  cudaMemcpyDeviceToHost, ss[q]);
+        if (err == cudaSuccess && status)
+            err = cudaMemcpyAsync(status + ub, dst, ucb * sizeof(uint32_t), cudaMemcpyDeviceToHost, ss[q]);
+    }
+    for (int i = 0; i < made; ++i) {  // wait for everything issued, even after an error
+        const cudaError_t e = cudaStreamSynchronize(ss[i]);
+        if (err == cudaSuccess) err = e;
+        cudaStreamDestroy(ss[i]);
+    }
+    if (ready) cudaEventDestroy(ready);
+    if (res != APM_OK) return res;
+    return err != cudaSuccess ? cuda_fail(static_cast<int>(err)) : APM_OK;
 }
 
 apm_status_t apm_cdet_from_weights(const double *a_in, int n, int64_t batch, double *c,

@@ -51,6 +51,25 @@ def test_host_side_argument_errors(lib):
     g.restype = ctypes.c_int
     assert g(fake, fake, 8, 1, 1, fake, None, None, None, None, 0, None) == 1  # single-det with A_dn
     assert g(fake, None, 8, 1, 4, fake, None, None, None, None, 0, None) == 1  # unknown flag
+    h = lib.apm_cdet_connected_host
+    h.argtypes = [P, P, i32, i64, i32, P, P, P, P, i64, i32, P, sz, P]
+    h.restype = ctypes.c_int
+    assert h(fake, None, 0, 1, 0, fake, None, None, None, 8, 2, fake, 1 << 20, None) == 2   # n out of range
+    assert h(fake, None, 8, 1, 0, fake, None, None, None, 0, 2, fake, 1 << 20, None) == 1   # chunk 0
+    assert h(fake, None, 8, 1, 0, fake, None, None, None, 8, 0, fake, 1 << 20, None) == 1   # no stream
+    assert h(fake, None, 8, 1, 0, fake, None, None, None, 8, 9, fake, 1 << 20, None) == 1   # > 8 streams
+    assert h(fake, None, 8, 1, 4, fake, None, None, None, 8, 2, fake, 1 << 20, None) == 1   # unknown flag
+    assert h(fake, fake, 8, 1, 1, fake, None, None, None, 8, 2, fake, 1 << 20, None) == 1   # single-det, A_dn
+    assert h(None, None, 8, 1, 0, fake, None, None, None, 8, 2, fake, 1 << 20, None) == 1   # null input
+    assert h(None, None, 8, 0, 0, None, None, None, None, 8, 2, None, 0, None) == 0         # empty batch
+    hw = lib.apm_cdet_connected_host_workspace_size
+    hw.argtypes = [i32, i64, i32, i32, ctypes.POINTER(sz)]
+    hw.restype = ctypes.c_int
+    nb = sz(7)
+    assert hw(8, 16, 2, 0, None) == 1
+    assert hw(17, 16, 2, 0, ctypes.byref(nb)) == 2 and nb.value == 0
+    assert hw(8, 0, 2, 0, ctypes.byref(nb)) == 1
+    assert hw(8, 16, 9, 0, ctypes.byref(nb)) == 1
     lib.apm_status_string.restype = ctypes.c_char_p
     assert b"WORKSPACE" in lib.apm_status_string(6)
     lib.apm_version.restype = ctypes.c_int
