@@ -56,9 +56,9 @@ typedef enum {
 /* Per-matrix status bits. */
 #define APM_ST_PIVOT_CORRECTED     0x01u /* a pivot correction was applied and back-propagated */
 #define APM_ST_NONFINITE_INPUT     0x02u /* the input held a NaN or an infinity */
-#define APM_ST_ZERO_PIVOT          0x04u /* Keldysh: a zero or non-finite pivot; sum set to NaN */
-#define APM_ST_CORRECTION_OVERFLOW 0x08u /* more pivot corrections than the per-matrix log holds
-                                            (256); outputs set to NaN */
+#define APM_ST_ZERO_PIVOT          0x04u /* Keldysh, XNOR, NAND: a zero or non-finite pivot; outputs NaN */
+#define APM_ST_CORRECTION_OVERFLOW 0x08u /* more pivot corrections than the per-matrix records
+                                            hold (256 for the FPM tree); outputs set to NaN */
 #define APM_ST_BAD_ORDER           0x10u /* uneven batch: order outside 1..n_max; matrix skipped */
 #define APM_ST_ERROR_MASK          (APM_ST_NONFINITE_INPUT | APM_ST_ZERO_PIVOT | APM_ST_CORRECTION_OVERFLOW | \
                                     APM_ST_BAD_ORDER)
@@ -238,18 +238,26 @@ apm_status_t apm_nambu_cdet(const double *M, int n, int64_t batch, double *minor
  * base-3 digit i of the index: 0 keeps neither row/column 2i nor 2i+1, 1 keeps
  * row and column 2i, 2 keeps row and column 2i+1) the determinant of the kept
  * submatrix; minors3[0] = 1. Ternary tree of Schur complements with scalar
- * pivots, O(3^n). Pivot corrections, which the paper allows here, are not
- * applied: a zero or non-finite pivot is flagged instead.
+ * pivots, O(3^n), with the pivot correction the paper allows here (Section
+ * III.C: as in the FPM tree, back-propagated at the end): a pivot p with
+ * |p| <= piv_threshold ||M||max becomes p + C, C = sign(p) piv_shift ||M||max,
+ * and afterwards det(M[S]) = det(M~[S]) - C det(M[S \ {row}]) is applied over
+ * the kept child's subtree, deepest vertex first.
  *   M        [batch][2n][2n] float64, row-major.
  *   n        1..APM_MAX_N_NAND_MINORS.
  *   minors3  [batch][3^n] float64 output.
- *   status   [batch] or NULL; APM_ST_ZERO_PIVOT (a zero or non-finite pivot met
- *            on the way) or APM_ST_NONFINITE_INPUT make that matrix's row NaN.
- *   workspace / workspace_bytes: scratch for the depth-first part, needed for
- *            n > 7 (apm_workspace_size with APM_OP_NAND_MINORS).
+ *   opt      pivot-correction options or NULL (the defaults of apm_pivot_opts).
+ *   status   [batch] or NULL; APM_ST_PIVOT_CORRECTED when a pivot was shifted;
+ *            APM_ST_ZERO_PIVOT (a zero or non-finite pivot left after the
+ *            shift), APM_ST_NONFINITE_INPUT, or APM_ST_CORRECTION_OVERFLOW
+ *            (more than 256 corrected pivots above the last 6 vertices) make
+ *            that matrix's row NaN.
+ *   workspace / workspace_bytes: per resident warp the depth-first part of the
+ *            tree and the correction records (apm_workspace_size with
+ *            APM_OP_NAND_MINORS; needed for every n).
  */
-apm_status_t apm_nand_minors(const double *M, int n, int64_t batch, double *minors3, uint32_t *status,
-                             void *workspace, size_t workspace_bytes, apm_stream_t stream);
+apm_status_t apm_nand_minors(const double *M, int n, int64_t batch, double *minors3, const apm_pivot_opts *opt,
+                             uint32_t *status, void *workspace, size_t workspace_bytes, apm_stream_t stream);
 
 /*
  * apm_two_type_cdet -- the CDet summed over two vertex types (Section V.C):
@@ -258,10 +266,13 @@ apm_status_t apm_nand_minors(const double *M, int n, int64_t batch, double *mino
  * recursion (Eq. recursion; summing over types block by block is exact because
  * the recursion is a sum over set partitions of products of block weights).
  *   abar, c  [batch][2^n] float64 outputs.   n  1..APM_MAX_N_TWO_TYPE.
- *   Other arguments as for apm_nand_minors; workspace: apm_workspace_size with
- *   APM_OP_TWO_TYPE_CDET (zero for n <= 7).
+ *   Other arguments as for apm_nand_minors (corrections above the last 6
+ *   vertices enter the sums through a list of at most 16 target sets per tree
+ *   path; more set APM_ST_CORRECTION_OVERFLOW); workspace: apm_workspace_size
+ *   with APM_OP_TWO_TYPE_CDET.
  */
-apm_status_t apm_two_type_cdet(const double *M, int n, int64_t batch, double *abar, double *c, uint32_t *status,
+apm_status_t apm_two_type_cdet(const double *M, int n, int64_t batch, double *abar, double *c,
+                               const apm_pivot_opts *opt, uint32_t *status,
                                void *workspace, size_t workspace_bytes, apm_stream_t stream);
 
 /* flags for apm_keldysh_sum and apm_keldysh_sum_noalloc */

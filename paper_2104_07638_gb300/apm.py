@@ -71,8 +71,8 @@ def lib():
                 "apm_keldysh_sum_varlen": [P, P, P, i64, i32, i32, P, P, P, P, sz, P],
                 "apm_xnor_minors": [P, i32, i64, P, P, P, sz, P],
                 "apm_nambu_cdet": [P, i32, i64, P, P, P, P, sz, P],
-                "apm_nand_minors": [P, i32, i64, P, P, P, sz, P],
-                "apm_two_type_cdet": [P, i32, i64, P, P, P, P, sz, P],
+                "apm_nand_minors": [P, i32, i64, P, OPT, P, P, sz, P],
+                "apm_two_type_cdet": [P, i32, i64, P, P, OPT, P, P, sz, P],
                 "apm_keldysh2_sum": [P, P, i32, i64, i32, P, P, P, P, sz, P],
                 "apm_cdet_tune_set": [P],
                 "apm_cdet_tune_get": [i32, ctypes.POINTER(ctypes.c_uint64)],
@@ -360,7 +360,7 @@ def nambu_cdet(M: torch.Tensor, return_minors=False, return_status=False):
     return res[0] if len(res) == 1 else tuple(res)
 
 
-def nand_minors(M: torch.Tensor, return_status=False):
+def nand_minors(M: torch.Tensor, return_status=False, piv_threshold=None, piv_shift=None):
     """All 3^n NAND principal minors (apm_nand_minors); M (batch, 2n, 2n) float64;
     index sum_i sigma_i 3^i (0 none, 1 row/column 2i, 2 row/column 2i+1)."""
     M, b, n = _nambu_batch(M)
@@ -368,12 +368,14 @@ def nand_minors(M: torch.Tensor, return_status=False):
     out = torch.empty((b, 3 ** n), dtype=torch.float64, device=dev)
     st = torch.zeros(b, dtype=torch.int32, device=dev) if return_status else None
     ws, nb = _workspace(OP_NAND_MINORS, n, b, dev)
-    _check(lib().apm_nand_minors(_ptr(M), n, b, _ptr(out), _ptr(st), _ptr(ws), nb, _stream(M)),
+    _check(lib().apm_nand_minors(_ptr(M), n, b, _ptr(out), _opts(piv_threshold, piv_shift), _ptr(st), _ptr(ws),
+                                 nb, _stream(M)),
            "apm_nand_minors")
     return (out, st) if return_status else out
 
 
-def two_type_cdet(M: torch.Tensor, return_weights=False, return_status=False):
+def two_type_cdet(M: torch.Tensor, return_weights=False, return_status=False, piv_threshold=None,
+                  piv_shift=None):
     """CDet summed over two vertex types (apm_two_type_cdet): weights abar[S] =
     NAND minors summed over the types of S, then the CDet recursion."""
     M, b, n = _nambu_batch(M)
@@ -382,7 +384,8 @@ def two_type_cdet(M: torch.Tensor, return_weights=False, return_status=False):
     c = torch.empty((b, 1 << n), dtype=torch.float64, device=dev)
     st = torch.zeros(b, dtype=torch.int32, device=dev) if return_status else None
     ws, nb = _workspace(OP_TWO_TYPE_CDET, n, b, dev)
-    _check(lib().apm_two_type_cdet(_ptr(M), n, b, _ptr(abar), _ptr(c), _ptr(st), _ptr(ws), nb, _stream(M)),
+    _check(lib().apm_two_type_cdet(_ptr(M), n, b, _ptr(abar), _ptr(c), _opts(piv_threshold, piv_shift), _ptr(st),
+                                   _ptr(ws), nb, _stream(M)),
            "apm_two_type_cdet")
     res = [c]
     if return_weights:

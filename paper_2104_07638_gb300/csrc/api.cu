@@ -283,8 +283,8 @@ apm_status_t apm_nambu_cdet(const double *M, int n, int64_t batch, double *minor
     return cdet_common(a, workspace, workspace_bytes, s);
 }
 
-apm_status_t apm_nand_minors(const double *M, int n, int64_t batch, double *minors3, uint32_t *status,
-                             void *workspace, size_t workspace_bytes, apm_stream_t stream) {
+apm_status_t apm_nand_minors(const double *M, int n, int64_t batch, double *minors3, const apm_pivot_opts *opt,
+                             uint32_t *status, void *workspace, size_t workspace_bytes, apm_stream_t stream) {
     if (n < 1 || n > APM_MAX_N_NAND_MINORS) return APM_ERR_UNSUPPORTED_N;
     if (batch < 0) return APM_ERR_ARG;
     apm_status_t st;
@@ -293,13 +293,16 @@ apm_status_t apm_nand_minors(const double *M, int n, int64_t batch, double *mino
     size_t need = 0;
     if ((st = apm_workspace_size(APM_OP_NAND_MINORS, n, batch, 0, &need))) return st;
     if (need > 0 && (!workspace || workspace_bytes < need || !aligned16(workspace))) return APM_ERR_WORKSPACE;
-    const int e = apm::launch_nand(M, n, batch, minors3, false, status, workspace,
+    double thr, shift;
+    pivot_values(opt, &thr, &shift);
+    const int e = apm::launch_nand(M, n, batch, minors3, false, thr, shift, status, workspace,
                                    reinterpret_cast<cudaStream_t>(stream));
     return e ? cuda_fail(e) : APM_OK;
 }
 
-apm_status_t apm_two_type_cdet(const double *M, int n, int64_t batch, double *abar, double *c, uint32_t *status,
-                               void *workspace, size_t workspace_bytes, apm_stream_t stream) {
+apm_status_t apm_two_type_cdet(const double *M, int n, int64_t batch, double *abar, double *c,
+                               const apm_pivot_opts *opt, uint32_t *status, void *workspace,
+                               size_t workspace_bytes, apm_stream_t stream) {
     if (n < 1 || n > APM_MAX_N_TWO_TYPE) return APM_ERR_UNSUPPORTED_N;
     if (batch < 0) return APM_ERR_ARG;
     apm_status_t st;
@@ -311,7 +314,9 @@ apm_status_t apm_two_type_cdet(const double *M, int n, int64_t batch, double *ab
     if ((st = apm_workspace_size(APM_OP_TWO_TYPE_CDET, n, batch, 0, &need))) return st;
     if (need > 0 && (!workspace || workspace_bytes < need || !aligned16(workspace))) return APM_ERR_WORKSPACE;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    const int e = apm::launch_nand(M, n, batch, abar, true, status, workspace, s);
+    double thr, shift;
+    pivot_values(opt, &thr, &shift);
+    const int e = apm::launch_nand(M, n, batch, abar, true, thr, shift, status, workspace, s);
     if (e) return cuda_fail(e);
     // the same scratch serves the recursion: the two launches run in order on s
     apm::CdetArgs a = {};

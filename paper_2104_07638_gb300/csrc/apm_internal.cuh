@@ -108,8 +108,8 @@ int launch_keldysh2(const double *Mu, const double *Md, int n, int64_t batch, in
 // two vertex types (type_sums = true: 2^n per matrix); one warp per matrix.
 int nand_grid(int64_t batch, int *err);
 size_t nand_workspace_bytes(int n, int64_t batch, int *err);
-int launch_nand(const double *M, int n, int64_t batch, double *out, bool type_sums, uint32_t *status,
-                void *workspace, cudaStream_t s);
+int launch_nand(const double *M, int n, int64_t batch, double *out, bool type_sums, double thr, double shf,
+                uint32_t *status, void *workspace, cudaStream_t s);
 
 // connected sums by the fast subset convolution (from weights)
 int fsc_grid(int n, int64_t batch, int *err);

@@ -122,18 +122,18 @@ def test_nand_and_two_type_argument_errors(lib):
     P, i32, i64, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_size_t
     fake = ctypes.c_void_p(1 << 20)
     f = lib.apm_nand_minors
-    f.argtypes = [P, i32, i64, P, P, P, sz, P]
+    f.argtypes = [P, i32, i64, P, P, P, P, sz, P]
     f.restype = ctypes.c_int
-    assert f(fake, 14, 1, fake, None, None, 0, None) == 2           # 3^14 per matrix: beyond the limit
-    assert f(fake, 0, 1, fake, None, None, 0, None) == 2
-    assert f(None, 5, 1, fake, None, None, 0, None) == 1
-    assert f(None, 5, 0, None, None, None, 0, None) == 0
+    assert f(fake, 14, 1, fake, None, None, None, 0, None) == 2     # 3^14 per matrix: beyond the limit
+    assert f(fake, 0, 1, fake, None, None, None, 0, None) == 2
+    assert f(None, 5, 1, fake, None, None, None, 0, None) == 1
+    assert f(None, 5, 0, None, None, None, None, 0, None) == 0
     g = lib.apm_two_type_cdet
-    g.argtypes = [P, i32, i64, P, P, P, P, sz, P]
+    g.argtypes = [P, i32, i64, P, P, P, P, P, sz, P]
     g.restype = ctypes.c_int
-    assert g(fake, 17, 1, fake, fake, None, None, 0, None) == 2
-    assert g(fake, 16, -1, fake, fake, None, None, 0, None) == 1
-    assert g(fake, 6, 1, fake, None, None, None, 0, None) == 1
+    assert g(fake, 17, 1, fake, fake, None, None, None, 0, None) == 2
+    assert g(fake, 16, -1, fake, fake, None, None, None, 0, None) == 1
+    assert g(fake, 6, 1, fake, None, None, None, None, 0, None) == 1
 
 
 def test_keldysh2_argument_errors(lib):
