@@ -416,27 +416,42 @@ def measure_rows(args, dev, peak):
     return rows
 
 
-def cpu_oracle_rate(A_np, seconds: float):
-    """Oracle minor sets per second on the host cores (bounded sample)."""
+def cpu_rate(run, A_np, seconds: float, threads: int):
+    """Minor sets per second of run(sample, threads) -> c on `threads` host
+    cores, over a bounded sample of the workload sized to about `seconds`."""
     import numpy as np
-    import oracle
-    threads = len(os.sched_getaffinity(0))
-    oracle.minors_lu(A_np[:2], nthreads=threads)      # build + warm
+    run(A_np[:2], threads)                              # build + warm
     t0 = time.perf_counter()
     probe = A_np[:threads]
-    m = oracle.minors_lu(probe, nthreads=threads)
-    oracle.cdet_recursion(m * m, nthreads=threads)
-    dt = time.perf_counter() - t0
-    per = dt / probe.shape[0]
+    run(probe, threads)
+    per = (time.perf_counter() - t0) / probe.shape[0]
     count = int(max(threads, min(A_np.shape[0], seconds / max(per, 1e-9))))
     count = (count // threads) * threads or threads
     sample = A_np[:count]
     t0 = time.perf_counter()
-    m = oracle.minors_lu(sample, nthreads=threads)
-    c = oracle.cdet_recursion(m * m, nthreads=threads)
+    c = run(sample, threads)
     dt = time.perf_counter() - t0
     assert np.isfinite(c).all()
     return count / dt, threads, count, dt
+
+
+def oracle_run(sample, threads):
+    """The oracle's minor sets: one partial-pivot LU per minor, then the plain recursion."""
+    import oracle
+    m = oracle.minors_lu(sample, nthreads=threads)
+    return oracle.cdet_recursion(m * m, nthreads=threads)
+
+
+def fpm_sc_run(sample, threads):
+    """The paper's own algorithm on the host: the depth-first tree with pivot
+    correction, then the recursion (cpu_baseline/, C with OpenMP)."""
+    import cpu_baseline
+    return cpu_baseline.fpm_sc(sample, nthreads=threads)[1]
+
+
+def cpu_oracle_rate(A_np, seconds: float):
+    """Oracle minor sets per second on all the host cores (bounded sample)."""
+    return cpu_rate(oracle_run, A_np, seconds, len(os.sched_getaffinity(0)))
 
 
 def run_reference(args, rank, world):
@@ -660,9 +675,18 @@ def main():
         result["rows"] = measure_rows(args, dev, peak)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r, threads, count, dt = cpu_oracle_rate(A_np, args.cpu_seconds)
-        result["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": threads, "kind": "oracle",
-                                  "sample": f"{count} of the {B} matrices (per-minor partial-pivot "
-                                            f"LU + plain recursion, OpenMP), {dt:.1f} s"}
+        r1, _, count1, dt1 = cpu_rate(oracle_run, A_np, args.cpu_seconds / 4, 1)
+        f, _, fcount, fdt = cpu_rate(fpm_sc_run, A_np, args.cpu_seconds / 3, threads)
+        f1, _, fcount1, fdt1 = cpu_rate(fpm_sc_run, A_np, args.cpu_seconds / 4, 1)
+        result["cpu_baseline"] = {
+            "value": r, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{count} of the {B} matrices (per-minor partial-pivot LU + plain recursion, "
+                      f"OpenMP), {dt:.1f} s",
+            "value_1core": r1, "sample_1core": f"{count1} matrices on 1 core, {dt1:.1f} s",
+            "fpm_sc": {"value": f, "unit": UNIT, "cores": threads, "value_1core": f1,
+                       "kind": "the paper's depth-first tree with pivot correction + the recursion, C/OpenMP",
+                       "sample": f"{fcount} matrices on {threads} cores ({fdt:.1f} s), "
+                                 f"{fcount1} on 1 core ({fdt1:.1f} s)"}}
     if rank == 0:
         print(json.dumps(result), flush=True)
     if world > 1:

@@ -43,7 +43,7 @@ def _rank_main(rank, world, port, out):
 def test_two_gloo_ranks_take_slowest_time_and_count_all_units():
     world = 2
     port = _free_port()
-    with mp.Manager() as man:
+    with mp.get_context("spawn").Manager() as man:  # no fork of a process that holds threads
         out = man.dict()
         mp.spawn(_rank_main, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)
