@@ -186,6 +186,13 @@ def nand_flops(n: int) -> int:
                for l in range(n))
 
 
+def minors_flops(n: int) -> int:
+    """Algorithmic flops of all 2^n minors by the tree alone (Section II): per
+    node of level l a Schur complement of (n-l-1)^2 FMAs, and a reciprocal and a
+    product per minor."""
+    return 2 * sum(2 ** l * (n - l - 1) ** 2 for l in range(n)) + 2 * (2 ** n - 1)
+
+
 def sc_flops(n: int) -> int:
     """Flops of the CDet recursion alone: one FMA per (T, S) pair with the
     lowest element of S in T, T a proper non-empty subset."""
@@ -315,6 +322,32 @@ def measure_rows(args, dev, peak):
         "tflops": fl / (ms * 1e-3) / 1e12, "frac_fp64_peak": fl / (ms * 1e-3) / 1e12 / peak,
         "launch": "NAND-minor kernel (type sums), then the CDet recursion"}
     del M
+    # a1 alone (Section II): all 2^12 minors of the 65536 Hubbard matrices, no
+    # recursion (one warp per matrix; small pivots redone by the fused kernel)
+    A = torch.as_tensor(inputs.hubbard_batch(65536, 12, seed=2)).to(dev)
+    ms = _event_ms(lambda: apm.all_minors(A))
+    fl = 65536 * minors_flops(12)
+    rows["all_minors_65536_n12"] = {
+        "value": 65536 / (ms * 1e-3), "unit": "minor-sets/s", "ms": ms,
+        "tflops": fl / (ms * 1e-3) / 1e12, "frac_fp64_peak": fl / (ms * 1e-3) / 1e12 / peak,
+        "minors_written_gbs": 65536 * 8 * 4096 / (ms * 1e-3) / 1e9,
+        "launch": "warp-per-matrix minors kernel, then the fused kernel on the flagged matrices"}
+    del A
+    torch.cuda.empty_cache()
+    # Section II at orders past the fused kernel's own: all 2^24 minors of 16
+    # matrices of order 24 (the upper 12 levels breadth first, 16 x 4096 leaves of
+    # order 12 through the warp-per-matrix minors kernel, scaled); 2.1 GB of minors
+    A = torch.as_tensor(np.random.default_rng(24).standard_normal((16, 24, 24)) + 2.0 * np.eye(24)).to(dev)
+    ms = _event_ms(lambda: apm.all_minors(A))
+    fl = 16 * minors_flops(24)
+    out_bytes = 16 * 8 * 2 ** 24
+    rows["all_minors_16_n24"] = {
+        "value": 16 / (ms * 1e-3), "unit": "minor-sets/s", "ms": ms,
+        "tflops": fl / (ms * 1e-3) / 1e12, "frac_fp64_peak": fl / (ms * 1e-3) / 1e12 / peak,
+        "minors_written_gbs": out_bytes / (ms * 1e-3) / 1e9,
+        "launch": "12 upper-level launches, the minors kernels on the 65536 leaves, scale, back-propagation, status"}
+    del A
+    torch.cuda.empty_cache()
     # next (Section V.A): the connected sums by the fast subset convolution against
     # the direct recursion, from the same weights (det^2 of Hubbard matrices)
     fsc = {}

@@ -65,6 +65,7 @@ typedef enum {
 
 /* Largest supported orders. */
 #define APM_MAX_N_MINORS   16
+#define APM_MAX_N_ALL_MINORS 24 /* apm_all_minors alone (2^24 minors per matrix) */
 #define APM_MAX_N_KELDYSH  16
 #define APM_MAX_N_PERM     16
 #define APM_MAX_N_XNOR     16
@@ -95,13 +96,27 @@ typedef struct {
  * subset S_i is the minor of S_i \ {l} times the (1,1) entry of the Schur
  * complement reached along the tree path of S_i.
  *   A       [batch][n][n] float64, input.
- *   n       1..APM_MAX_N_MINORS.
+ *   n       1..APM_MAX_N_ALL_MINORS.
  *   batch   >= 0 (0 launches nothing).
  *   minors  [batch][2^n] float64, output, minors[b][S] = det(A_b[S]).
  *   opt     pivot-correction options or NULL.
  *   status  [batch] uint32 or NULL.
- *   workspace / workspace_bytes: scratch for n > 12 (see apm_workspace_size);
- *           may be NULL/0 for n <= 12.
+ *   workspace / workspace_bytes: scratch for n >= 9 (see apm_workspace_size),
+ *           256-byte aligned; may be NULL/0 for n <= 8.
+ * For n = 9..16 one warp takes a matrix (elements decided from the last one
+ * down, the upper ones depth first, the last 9 breadth first in shared memory,
+ * the 16 minors of every 4 x 4 node of the last level in closed form); it
+ * shifts no pivot, and the matrices that meet a pivot with |p| <= piv_threshold
+ * ||A||max are computed again, with the correction, by the one-CTA-per-matrix
+ * kernel of apm_cdet_connected, launched after it on those matrices only.
+ * For n = 17..24 the tree is cut in two: its upper n - 12 levels (elements n-1
+ * down to 12) run breadth first over the batch, one launch per level, and each
+ * of the 2^(n-12) leaves, the 12 x 12 Schur complement M_T of the kept upper
+ * set T, goes through the n = 12 path above, whose 4096 minors fill the row at
+ * T * 4096 and are scaled by det(A[T]): det(A[T u U]) = det(A[T]) det(M_T[U]).
+ * Upper-level pivots are corrected as above (threshold against ||A||max; at
+ * most 256 per matrix, more set APM_ST_CORRECTION_OVERFLOW), the leaves' own
+ * against ||M_T||max. An error bit anywhere makes the matrix's whole row NaN.
  */
 apm_status_t apm_all_minors(const double *A, int n, int64_t batch, double *minors,
                             const apm_pivot_opts *opt, uint32_t *status, void *workspace,

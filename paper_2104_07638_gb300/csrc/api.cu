@@ -89,11 +89,37 @@ extern "C" {
 apm_status_t apm_all_minors(const double *A, int n, int64_t batch, double *minors,
                             const apm_pivot_opts *opt, uint32_t *status, void *workspace,
                             size_t workspace_bytes, apm_stream_t stream) {
-    if (n < 1 || n > APM_MAX_N_MINORS) return APM_ERR_UNSUPPORTED_N;
+    if (n < 1 || n > APM_MAX_N_ALL_MINORS) return APM_ERR_UNSUPPORTED_N;
     if (batch < 0) return APM_ERR_ARG;
     apm_status_t st;
     if ((st = check_ptr(A, batch)) || (st = check_ptr(minors, batch)) || (st = check_opt_ptr(status)))
         return st;
+    if (n > APM_MAX_N_MINORS) {  // the upper levels breadth first, the 12 x 12 leaves by warps
+        if (batch == 0) return APM_OK;
+        if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255u)) return APM_ERR_WORKSPACE;
+        int err = 0;
+        const size_t need = apm::fpm_big_workspace_bytes(n, batch, &err);
+        if (err) return cuda_fail(err);
+        if (workspace_bytes < need) return APM_ERR_WORKSPACE;
+        double thr, shift;
+        pivot_values(opt, &thr, &shift);
+        const int e = apm::launch_fpm_big(A, n, batch, minors, thr, shift, status, workspace,
+                                          reinterpret_cast<cudaStream_t>(stream));
+        return e ? cuda_fail(e) : APM_OK;
+    }
+    if (n >= apm::kWarpMinorsFromN) {  // one warp per matrix; small pivots redone by the fused kernel
+        if (batch == 0) return APM_OK;
+        if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255u)) return APM_ERR_WORKSPACE;
+        int err = 0;
+        const size_t need = apm::fpm_warp_workspace_bytes(n, batch, &err);
+        if (err) return cuda_fail(err);
+        if (workspace_bytes < need) return APM_ERR_WORKSPACE;
+        double thr, shift;
+        pivot_values(opt, &thr, &shift);
+        const int e = apm::launch_fpm_warp(A, n, batch, minors, thr, shift, status, workspace,
+                                           reinterpret_cast<cudaStream_t>(stream));
+        return e ? cuda_fail(e) : APM_OK;
+    }
     apm::CdetArgs a = {};
     a.A_up = A;
     a.minors_out = minors;
@@ -467,6 +493,16 @@ apm_status_t apm_workspace_size(int op, int n_max, int64_t batch, int two_mats, 
         case APM_OP_ALL_MINORS:
         case APM_OP_CDET:
         case APM_OP_CDET_FROM_WEIGHTS: {
+            if (op == APM_OP_ALL_MINORS && n_max > APM_MAX_N_MINORS && n_max <= APM_MAX_N_ALL_MINORS) {
+                int err = 0;
+                *bytes = apm::fpm_big_workspace_bytes(n_max, batch, &err);
+                return err ? cuda_fail(err) : APM_OK;
+            }
+            if (op == APM_OP_ALL_MINORS && n_max >= apm::kWarpMinorsFromN && n_max <= APM_MAX_N_MINORS) {
+                int err = 0;
+                *bytes = apm::fpm_warp_workspace_bytes(n_max, batch, &err);
+                return err ? cuda_fail(err) : APM_OK;
+            }
             if (n_max < 1 || n_max > APM_MAX_N_MINORS) return APM_ERR_UNSUPPORTED_N;
             const bool two = op == APM_OP_CDET && two_mats;
             if (n_max <= apm::cdet_smem_max_n(two) || batch == 0) return APM_OK;

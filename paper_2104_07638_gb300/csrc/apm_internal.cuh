@@ -61,6 +61,7 @@ struct CdetArgs {
     double piv_thr;
     double piv_shift;
     int fsc_from_n;  // orders >= this (0: none) leave the weights a[] in c for the fast subset convolution
+    const uint32_t *redo;  // fixed-order launch: if set, only the matrices b with redo[b] != 0
 };
 
 // Orders whose connected sums apm_cdet_connected and its uneven-batch form take
@@ -69,6 +70,19 @@ constexpr int kFscFromN = 16;
 
 // Launches the fused minors / connected-sum kernel. Returns a cudaError_t.
 int launch_fpm_cdet(const CdetArgs &a, cudaStream_t s);
+
+// All principal minors for orders 9..16 (minors only), one warp per matrix;
+// matrices with a small pivot are redone by the fused kernel (fpm_warp.cu).
+constexpr int kWarpMinorsFromN = 9;
+size_t fpm_warp_workspace_bytes(int n, int64_t batch, int *err);
+int launch_fpm_warp(const double *A, int n, int64_t batch, double *minors, double thr, double shf,
+                    uint32_t *status, void *workspace, cudaStream_t s);
+
+// All principal minors for orders 17..24: the upper levels of the tree breadth
+// first, the 12 x 12 leaves by the fused kernel (fpm_big.cu).
+size_t fpm_big_workspace_bytes(int n, int64_t batch, int *err);
+int launch_fpm_big(const double *A, int n, int64_t batch, double *minors, double thr, double shf,
+                   uint32_t *status, void *workspace, cudaStream_t s);
 
 // Uploads the popcount-ordered mask table on the current device (idempotent).
 int ensure_tables();

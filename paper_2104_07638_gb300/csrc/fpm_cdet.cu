@@ -515,6 +515,7 @@ __global__ void __launch_bounds__(kCdetThreads, 3) fpm_cdet_kernel(const CdetKer
     double *MU = MC + NC;
     const int64_t mat = static_cast<int64_t>(n) * n;
     for (int64_t b = blockIdx.x; b < p.batch; b += gridDim.x) {
+        if (p.redo && p.redo[b] == 0u) continue;  // done by the warp-per-matrix minors kernel
         cdet_item(p, n, p.A_up ? p.A_up + b * mat : nullptr, p.A_dn ? p.A_dn + b * mat : nullptr,
                   p.a_in ? p.a_in + b * N : nullptr,
                   p.minors_out ? p.minors_out + b * (p.two_mats ? 2 * N : N) : nullptr,

@@ -41,7 +41,8 @@ def test_host_side_argument_errors(lib):
     f.restype = ctypes.c_int
     fake = ctypes.c_void_p(1 << 20)           # never dereferenced: the call must fail first
     assert f(fake, 0, 1, fake, None, None, None, 0, None) == 2      # n out of range
-    assert f(fake, 17, 1, fake, None, None, None, 0, None) == 2
+    assert f(fake, 25, 1, fake, None, None, None, 0, None) == 2
+    assert f(fake, 17, 1, fake, None, None, None, 0, None) == 6     # orders 17..24 need the workspace
     assert f(fake, 8, -1, fake, None, None, None, 0, None) == 1     # negative batch
     assert f(None, 8, 1, fake, None, None, None, 0, None) == 1      # null input
     assert f(ctypes.c_void_p((1 << 20) + 8), 8, 1, fake, None, None, None, 0, None) == 1  # misaligned

@@ -83,3 +83,10 @@ def test_throughput_helpers():
     assert bench.job_throughput(1000, 1, 10, 2.0) == 5000.0
     assert bench.job_throughput(1000, 4, 10, 2.0) == 20000.0
     assert bench.max_over_ranks(1.5, 1) == 1.5
+
+
+def test_minor_set_count_splits_into_tree_and_recursion():
+    """A minor set's flops are the tree's (Schur updates, reciprocals and
+    products), the squares of the minors, and the recursion's FMAs."""
+    for n in range(1, 17):
+        assert bench.flops_per_set(n) == bench.minors_flops(n) + (2 ** n - 1) + bench.sc_flops(n)

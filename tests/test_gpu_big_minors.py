@@ -1,0 +1,147 @@
+"""All principal minors for orders 17..24 (apm_all_minors beyond the fused
+kernel's own range): the upper tree levels breadth first, the 12 x 12 leaves
+by the fused kernel, scaled, and the upper pivot corrections back-propagated.
+Against the oracle's one elimination per minor, within 1e-10 of the row-sum
+bound prod_{i in S} sum_{j in S} |A_ij| (perm(|A[S]|) costs 3^n here), and at
+n = 24 on sampled masks against numpy determinants."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2104_07638_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def apm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2104_07638_gb300 import apm as m
+    m.lib()
+    return m
+
+
+def dev(x):
+    return torch.as_tensor(np.ascontiguousarray(x)).cuda()
+
+
+ERROR_BITS = 2 | 4 | 8 | 16   # non-finite input, zero pivot, correction overflow, bad order
+
+
+def check_full(apm, A, expect_corrected=False, tol=TOL, **kw):
+    """Every minor against the oracle; no error bit; with expect_corrected the
+    correction bit on every matrix (without it, a correction here and there
+    among the 2^n tree nodes is allowed: it does not change the minors)."""
+    m, st = apm.all_minors(dev(A), return_status=True, **kw)
+    m, st = m.cpu().numpy(), st.cpu().numpy()
+    ref = oracle.minors_lu(A)
+    scale = oracle.minors_rowsum_bound(A)
+    err = float(np.max(np.abs(m - ref) / np.maximum(scale, 1e-300)))
+    assert err <= tol, err
+    assert np.all(m[:, 0] == 1.0)
+    assert np.all((st & ERROR_BITS) == 0), st
+    if expect_corrected:
+        assert np.all(st & apm.ST_PIVOT_CORRECTED), st
+
+
+@pytest.mark.parametrize("n", [17, 18, 20])
+def test_random_matrices_against_oracle(apm, n):
+    rng = np.random.default_rng(7000 + n)
+    check_full(apm, rng.standard_normal((2, n, n)) + 2.0 * np.eye(n))
+
+
+def test_hubbard_matrices_n19(apm):
+    check_full(apm, I.hubbard_batch(2, 19, seed=7100))
+
+
+@pytest.mark.parametrize("n", [17, 19])
+def test_upper_and_leaf_pivot_corrections(apm, n):
+    """A zero diagonal corrects the first pivot of the upper levels and of the
+    leaves; a threshold of 0.7 ||A||max corrects most of the upper ones, nested.
+    The zero-diagonal case is held to 1e-9: the tree divides by its pivots with
+    no row exchange (Section II), and on such a matrix the pivots just above the
+    threshold amplify rounding by about ||A|| / |p|, which depends on the order in
+    which the elements are decided (the leaves' kernel decides them from the
+    last one, the fused kernel from the first)."""
+    rng = np.random.default_rng(7200 + n)
+    A = rng.standard_normal((2, n, n))
+    for b in range(2):
+        np.fill_diagonal(A[b], 0.0)
+    check_full(apm, A, expect_corrected=True, tol=1e-9)
+    B = rng.standard_normal((2, n, n))
+    check_full(apm, B, expect_corrected=True, piv_threshold=0.7)
+
+
+def test_order_24_sampled(apm):
+    rng = np.random.default_rng(7300)
+    n = 24
+    A = rng.standard_normal((1, n, n)) + 2.0 * np.eye(n)
+    m, st = apm.all_minors(dev(A), return_status=True)
+    m = m[0].cpu().numpy()
+    assert int(st.cpu()[0]) & ERROR_BITS == 0 and m.shape == (1 << n,) and m[0] == 1.0
+    masks = np.concatenate([rng.integers(1, 1 << n, 3000), [(1 << n) - 1, 1 << 23, (1 << 12) - 1, 1 << 12]])
+    absA = np.abs(A[0])
+    for S in masks:
+        idx = [i for i in range(n) if S >> i & 1]
+        sub = A[0][np.ix_(idx, idx)]
+        bound = np.prod(absA[np.ix_(idx, idx)].sum(axis=1))
+        assert abs(m[S] - np.linalg.det(sub)) <= TOL * bound, S
+
+
+def test_leading_block_matches_order_16_path(apm):
+    """Masks within the first 16 elements are the minors of the leading 16 x 16
+    block, which the fused kernel computes directly."""
+    rng = np.random.default_rng(7400)
+    A = rng.standard_normal((2, 18, 18)) + 2.0 * np.eye(18)
+    big = apm.all_minors(dev(A)).cpu().numpy()[:, :1 << 16]
+    small = apm.all_minors(dev(A[:, :16, :16])).cpu().numpy()
+    scale = oracle.minors_rowsum_bound(A[:, :16, :16])
+    assert np.all(np.abs(big - small) <= 2 * TOL * scale)
+
+
+def test_nonfinite_input_and_workspace_query(apm):
+    rng = np.random.default_rng(7500)
+    A = rng.standard_normal((3, 17, 17)) + 2.0 * np.eye(17)
+    A[1, 3, 5] = np.inf
+    m, st = apm.all_minors(dev(A), return_status=True)
+    st = st.cpu().numpy()
+    assert st[1] & apm.ST_NONFINITE_INPUT and st[0] == 0 and st[2] == 0
+    assert bool(torch.isnan(m[1]).all()) and bool(torch.isfinite(m[0]).all())
+    assert apm.workspace_size(apm.OP_ALL_MINORS, 24, 4) > apm.workspace_size(apm.OP_ALL_MINORS, 17, 4) > 0
+    with pytest.raises(apm.ApmError):
+        apm.all_minors(dev(rng.standard_normal((1, 25, 25))))
+
+
+@pytest.mark.parametrize("n", [9, 10, 12, 13, 16])
+def test_warp_minors_path(apm, n):
+    """Orders 9..16 (one warp per matrix), random and Hubbard matrices."""
+    rng = np.random.default_rng(7600 + n)
+    check_full(apm, rng.standard_normal((5, n, n)) + 2.0 * np.eye(n))
+    check_full(apm, I.hubbard_batch(3, n, seed=7650 + n))
+
+
+@pytest.mark.parametrize("n", [9, 12, 14])
+def test_warp_path_redo_and_nonfinite(apm, n):
+    """In one batch: plain matrices (the warp kernel), matrices with a zero
+    diagonal entry (flagged by the warp kernel and redone by the fused kernel,
+    which decides the elements from the first one: its own pivots, corrected
+    where small) and a non-finite one (flagged by the fused kernel, as in
+    apm_cdet_connected)."""
+    rng = np.random.default_rng(7700 + n)
+    A = rng.standard_normal((6, n, n)) + 2.0 * np.eye(n)
+    A[1, n - 1, n - 1] = 0.0          # the first pivot of the tree
+    A[3, 2, 2] = 0.0                  # a pivot of the tail
+    A[4] = rng.standard_normal((n, n))
+    np.fill_diagonal(A[4], 0.0)
+    ok = [0, 1, 2, 3, 4]
+    check_full(apm, A[ok])
+    A[5, 0, 1] = np.nan
+    m, st = apm.all_minors(dev(A), return_status=True)
+    m, st = m.cpu().numpy(), st.cpu().numpy()
+    assert st[4] & apm.ST_PIVOT_CORRECTED and np.all(st[:5] & ERROR_BITS == 0) and st[0] == 0 and st[2] == 0
+    assert st[5] & apm.ST_NONFINITE_INPUT and np.isnan(m[5, -1])   # flagged; NaN where the entry enters
+    ref = oracle.minors_lu(A[ok])
+    assert np.all(np.abs(m[ok] - ref) <= TOL * oracle.minors_rowsum_bound(A[ok]))

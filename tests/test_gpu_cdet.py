@@ -178,7 +178,7 @@ def test_empty_batch_and_bad_args(apm):
     A = torch.zeros((0, 8, 8), dtype=torch.float64, device="cuda")
     assert apm.all_minors(A).shape == (0, 256)
     with pytest.raises(apm.ApmError):
-        apm.all_minors(torch.zeros((1, 17, 17), dtype=torch.float64, device="cuda"))
+        apm.all_minors(torch.zeros((1, 25, 25), dtype=torch.float64, device="cuda"))
 
 
 def test_hubbard_n12_full_batch_sampled(apm):
