@@ -90,7 +90,7 @@ def parse():
     ap.add_argument("--mc-steps", type=int, default=100)
     ap.add_argument("--case", default=None,
                     choices=["cdet_n12", "cdet_n16", "keldysh_n12", "ppm_n14", "cdet_uneven", "xnor_n12",
-                             "nand_n10", "keldysh2_n12", "mlp_gemm", "fsc_n16"],
+                             "nand_n10", "keldysh2_n12", "mlp_gemm", "fsc_n16", "minors_n12", "minors_n20"],
                     help="run 3 launches of one kernel on a small case (for profiling) and exit")
     return ap.parse_args()
 
@@ -538,6 +538,14 @@ def profile_case(name: str):
         Mu, Md = inputs.keldysh2_batch(8192, 12, seed=8)
         Mu, Md = torch.as_tensor(Mu).to(dev), torch.as_tensor(Md).to(dev)
         run = lambda: apm.keldysh2_sum(Mu, Md)
+    elif name == "minors_n12":
+        # the minors alone (one warp per matrix): 4096 matrices, 134 MB of minors (> L2)
+        A = torch.as_tensor(inputs.hubbard_batch(4096, 12, seed=2)).to(dev)
+        run = lambda: apm.all_minors(A)
+    elif name == "minors_n20":
+        # orders past 16: 64 matrices of order 20 (the upper levels, then 1024 leaves each)
+        A = torch.as_tensor(np.random.default_rng(20).standard_normal((64, 20, 20)) + 2.0 * np.eye(20)).to(dev)
+        run = lambda: apm.all_minors(A)
     elif name == "nand_n10":
         M = torch.as_tensor(inputs.two_type_batch(16384, 10, seed=7)).to(dev)
         run = lambda: apm.two_type_cdet(M)

@@ -107,26 +107,30 @@ __device__ __forceinline__ void fw_tail_level(const double *cur, double *nxt, Fw
     __syncwarp();
 }
 
-// The 16 principal minors of every 4 x 4 node i (node minor nd[i]) in closed
-// form, out[16 i + X] for X within {0,1,2,3}: with s_jk the 2 x 2 minors of rows
-// 0,1 and c_jk those of rows 2,3 on columns j,k, the triples by expansion along
-// their third row and the whole by Laplace expansion along rows 0,1.
+// The 16 principal minors of every 4 x 4 node i (node minor d = nd[i]) in
+// closed form, out[16 i + X] for X within {0,1,2,3}: with s_jk the 2 x 2 minors
+// of rows 0,1 and c_jk those of rows 2,3 on columns j,k, the triples by
+// expansion along their third row and the whole by Laplace expansion along rows
+// 0,1. Row 0 is scaled by d first, so that every minor holding element 0 comes
+// out scaled; the other seven are multiplied by d. No pivot, no division.
 template <int S>
 __device__ __forceinline__ void fw_bottom(const double *cur, const double *nd, double *out, int lane) {
     constexpr int nodes = 1 << (S - 4);
     for (int i = lane; i < nodes; i += 32) {
         const double *M = cur + 16 * i;
-        const double s01 = fma(M[0], M[5], -M[1] * M[4]), s02 = fma(M[0], M[6], -M[2] * M[4]);
-        const double s03 = fma(M[0], M[7], -M[3] * M[4]), s12 = fma(M[1], M[6], -M[2] * M[5]);
-        const double s13 = fma(M[1], M[7], -M[3] * M[5]), s23 = fma(M[2], M[7], -M[3] * M[6]);
+        const double d = nd[i];
+        const double a0 = d * M[0], a1 = d * M[1], a2 = d * M[2], a3 = d * M[3];
+        const double s01 = fma(a0, M[5], -a1 * M[4]), s02 = fma(a0, M[6], -a2 * M[4]);
+        const double s03 = fma(a0, M[7], -a3 * M[4]), s12 = fma(a1, M[6], -a2 * M[5]);
+        const double s13 = fma(a1, M[7], -a3 * M[5]), s23 = fma(a2, M[7], -a3 * M[6]);
         const double c01 = fma(M[8], M[13], -M[9] * M[12]), c02 = fma(M[8], M[14], -M[10] * M[12]);
         const double c03 = fma(M[8], M[15], -M[11] * M[12]), c12 = fma(M[9], M[14], -M[10] * M[13]);
         const double c13 = fma(M[9], M[15], -M[11] * M[13]), c23 = fma(M[10], M[15], -M[11] * M[14]);
-        const double p02 = fma(M[0], M[10], -M[2] * M[8]), p03 = fma(M[0], M[15], -M[3] * M[12]);
+        const double p02 = fma(a0, M[10], -a2 * M[8]), p03 = fma(a0, M[15], -a3 * M[12]);
         const double p12 = fma(M[5], M[10], -M[6] * M[9]), p13 = fma(M[5], M[15], -M[7] * M[13]);
         const double t012 = fma(M[10], s01, fma(-M[9], s02, M[8] * s12));
         const double t013 = fma(M[15], s01, fma(-M[13], s03, M[12] * s13));
-        const double t023 = fma(M[0], c23, fma(-M[2], c03, M[3] * c02));
+        const double t023 = fma(a0, c23, fma(-a2, c03, a3 * c02));
         const double t123 = fma(M[5], c23, fma(-M[6], c13, M[7] * c12));
         double q = s01 * c23;
         q = fma(-s02, c13, q);
@@ -134,16 +138,15 @@ __device__ __forceinline__ void fw_bottom(const double *cur, const double *nd, d
         q = fma(s12, c03, q);
         q = fma(-s13, c02, q);
         q = fma(s23, c01, q);
-        const double d = nd[i];
         double2 *o = reinterpret_cast<double2 *>(out + 16 * i);
-        o[0] = make_double2(d, d * M[0]);
-        o[1] = make_double2(d * M[5], d * s01);
-        o[2] = make_double2(d * M[10], d * p02);
-        o[3] = make_double2(d * p12, d * t012);
-        o[4] = make_double2(d * M[15], d * p03);
-        o[5] = make_double2(d * p13, d * t013);
-        o[6] = make_double2(d * c23, d * t023);
-        o[7] = make_double2(d * t123, d * q);
+        o[0] = make_double2(d, a0);
+        o[1] = make_double2(d * M[5], s01);
+        o[2] = make_double2(d * M[10], p02);
+        o[3] = make_double2(d * p12, t012);
+        o[4] = make_double2(d * M[15], p03);
+        o[5] = make_double2(d * p13, t013);
+        o[6] = make_double2(d * c23, t023);
+        o[7] = make_double2(d * t123, q);
     }
 }
 
