@@ -75,8 +75,11 @@ int launch_fpm_cdet(const CdetArgs &a, cudaStream_t s);
 // matrices with a small pivot are redone by the fused kernel (fpm_warp.cu).
 constexpr int kWarpMinorsFromN = 9;
 size_t fpm_warp_workspace_bytes(int n, int64_t batch, int *err);
+// pre (or NULL): a factor per matrix on all its minors, not applied to the
+// matrices redone by the fused kernel, whose flags come back in *redo_out.
 int launch_fpm_warp(const double *A, int n, int64_t batch, double *minors, double thr, double shf,
-                    uint32_t *status, void *workspace, cudaStream_t s);
+                    uint32_t *status, void *workspace, cudaStream_t s, const double *pre = nullptr,
+                    uint32_t **redo_out = nullptr);
 
 // All principal minors for orders 17..24: the upper levels of the tree breadth
 // first, the 12 x 12 leaves by the fused kernel (fpm_big.cu).

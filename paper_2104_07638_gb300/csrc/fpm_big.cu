@@ -15,10 +15,10 @@
 // binary number, first decision most significant, so that the 2^H leaves come
 // out in the order of T. Every leaf is a 12 x 12 matrix M_T with the minor
 // det(A[T]): det(A[T u U]) = det(A[T]) det(M_T[U]) for U within 0..11, so the
-// warp-per-matrix minors kernel writes the 2^12 minors of M_T straight into
-// the output row at T * 4096 (the fused kernel redoing, with its own pivot
-// correction, the leaves that meet a small pivot), and a last pass scales the
-// row by det(A[T]). A pivot of the upper levels with |p| <= thr ||A||max is
+// warp-per-matrix minors kernel writes the 2^12 minors of M_T, times det(A[T])
+// (its root minor), straight into the output row at T * 4096; the leaves that
+// meet a small pivot are redone by the fused kernel with its own pivot
+// correction, and only their rows are then scaled by det(A[T]). A pivot of the upper levels with |p| <= thr ||A||max is
 // shifted by C = sign(p) shift ||A||max and recorded; after the scaling,
 // deepest level first, det[m] -= C det[m without the element] over the kept
 // child's subtree (all T in its range, all U), the dropped sibling's rows
@@ -149,13 +149,18 @@ __global__ void big_level_kernel(const double *__restrict__ src, double *__restr
     }
 }
 
-// out[b][T 4096 + U] *= det(A[T]) (the leaf minors of M_T times the leaf's minor).
-__global__ void big_scale_kernel(double *out, int n, int H, int64_t batch, const double *__restrict__ dleaf) {
-    const int64_t total = batch << n;
-    for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
-         e += static_cast<int64_t>(gridDim.x) * blockDim.x)
-        out[e] *= dleaf[e >> kBigLeafN];
-    (void)H;
+// The leaves redone by the fused kernel (redo[L] != 0, usually none): their
+// 4096 minors times det(A[T]). One warp per leaf.
+__global__ void big_scale_redo_kernel(double *out, int64_t leaves, const uint32_t *__restrict__ redo,
+                                      const double *__restrict__ dleaf) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t L = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; L < leaves; L += nw) {
+        if (redo[L] == 0u) continue;
+        const double f = dleaf[L];
+        double *row = out + (L << kBigLeafN);
+        for (int e = lane; e < (1 << kBigLeafN); e += 32) row[e] *= f;
+    }
 }
 
 // One CTA per matrix: the upper-level corrections, deepest level first:
@@ -246,9 +251,10 @@ int launch_fpm_big(const double *A, int n, int64_t batch, double *minors, double
     err = static_cast<int>(cudaGetLastError());
     if (err) return err;
     // the leaves: 12 x 12 matrices in the order of T, their minors into the rows
-    err = launch_fpm_warp(src, kBigLeafN, batch << H, minors, thr, shf, lstat, leafws, s);
+    uint32_t *redo = nullptr;
+    err = launch_fpm_warp(src, kBigLeafN, batch << H, minors, thr, shf, lstat, leafws, s, det[H & 1], &redo);
     if (err) return err;
-    big_scale_kernel<<<1216, 256, 0, s>>>(minors, n, H, batch, det[H & 1]);
+    big_scale_redo_kernel<<<1216, 256, 0, s>>>(minors, batch << H, redo, det[H & 1]);
     big_backprop_kernel<<<static_cast<unsigned>(batch), 512, 0, s>>>(minors, n, H, ccount, clog, flags);
     big_status_kernel<<<static_cast<unsigned>(batch), 512, 0, s>>>(minors, n, H, flags, lstat, status);
     return static_cast<int>(cudaGetLastError());

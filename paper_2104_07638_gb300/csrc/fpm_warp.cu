@@ -161,10 +161,11 @@ __device__ __forceinline__ void fw_tail_levels(double *cur, double *nxt, double 
     }
 }
 
-// One matrix of order n (9..16), whole warp: its 2^n minors into out. Returns 1
-// when a pivot is below thrA or zero (the fused kernel redoes the matrix) or
-// the input is not finite (the fused kernel then sets the status and NaN).
-__device__ __forceinline__ int fw_matrix(const double *A, int n, double *out, double thr, double *stack,
+// One matrix of order n (9..16), whole warp: its 2^n minors, each times pre,
+// into out. Returns 1 when a pivot is below thrA or zero (the fused kernel
+// redoes the matrix) or the input is not finite (the fused kernel then sets the
+// status and NaN).
+__device__ __forceinline__ int fw_matrix(const double *A, int n, double *out, double thr, double pre, double *stack,
                                          FwWarpSmem &w, int lane) {
     const int D = n - kFwTail;
     int bad = 0, small = 0, nonfin = 0;
@@ -181,7 +182,7 @@ __device__ __forceinline__ int fw_matrix(const double *A, int n, double *out, do
     if (lane == 0) {
         w.vp[0] = A;
         w.vs[0] = n;
-        w.pdet[0] = 1.0;
+        w.pdet[0] = pre;
     }
     __syncwarp();
     for (int64_t t = 0; t < (int64_t(1) << D); ++t) {
@@ -238,11 +239,13 @@ __device__ __forceinline__ int fw_matrix(const double *A, int n, double *out, do
     return __any_sync(0xffffffffu, bad | small);
 }
 
-// Every matrix; redo[b] = 1 where the fused kernel must compute it again.
+// Every matrix; redo[b] = 1 where the fused kernel must compute it again. pre
+// (or NULL for 1): a factor per matrix on all its minors.
 __global__ void __launch_bounds__(kFwWarps * 32, 4) fpm_warp_kernel(const double *__restrict__ A, int n,
                                                                   int64_t batch, double *minors, double thr,
-                                                                  uint32_t *redo, uint32_t *status,
-                                                                  double *stack_base, size_t stack_per_warp) {
+                                                                  const double *__restrict__ pre, uint32_t *redo,
+                                                                  uint32_t *status, double *stack_base,
+                                                                  size_t stack_per_warp) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     FwWarpSmem &w = reinterpret_cast<FwWarpSmem *>(smem_raw)[wid];
@@ -251,7 +254,7 @@ __global__ void __launch_bounds__(kFwWarps * 32, 4) fpm_warp_kernel(const double
     double *stack = stack_base ? stack_base + gw * stack_per_warp : nullptr;
     const int64_t nn = static_cast<int64_t>(n) * n, N = int64_t(1) << n;
     for (int64_t b = gw; b < batch; b += nw) {
-        const int r = fw_matrix(A + b * nn, n, minors + b * N, thr, stack, w, lane);
+        const int r = fw_matrix(A + b * nn, n, minors + b * N, thr, pre ? pre[b] : 1.0, stack, w, lane);
         if (lane == 0) {
             redo[b] = static_cast<uint32_t>(r);
             if (status && !r) status[b] = 0u;
@@ -311,7 +314,7 @@ size_t fpm_warp_workspace_bytes(int n, int64_t batch, int *err) {
 }
 
 int launch_fpm_warp(const double *A, int n, int64_t batch, double *minors, double thr, double shf,
-                    uint32_t *status, void *workspace, cudaStream_t s) {
+                    uint32_t *status, void *workspace, cudaStream_t s, const double *pre, uint32_t **redo_out) {
     FwPlan plan;
     int grid = 0;
     int err = fw_plan(n, batch, &plan, &grid);
@@ -322,10 +325,12 @@ int launch_fpm_warp(const double *A, int n, int64_t batch, double *minors, doubl
     double *stack = per ? reinterpret_cast<double *>(ws) : nullptr;
     uint32_t *redo = reinterpret_cast<uint32_t *>(ws + plan.stack);
     double *fused = plan.fused ? reinterpret_cast<double *>(ws + plan.stack + plan.redo) : nullptr;
-    fpm_warp_kernel<<<grid, kFwWarps * 32, smem, s>>>(A, n, batch, minors, thr, redo, status, stack, per);
+    if (redo_out) *redo_out = redo;
+    fpm_warp_kernel<<<grid, kFwWarps * 32, smem, s>>>(A, n, batch, minors, thr, pre, redo, status, stack, per);
     err = static_cast<int>(cudaGetLastError());
     if (err) return err;
     // the flagged matrices again, by the fused kernel with the pivot correction
+    // (without the factor pre: the caller scales those rows)
     CdetArgs a = {};
     a.A_up = A;
     a.minors_out = minors;
