@@ -14,17 +14,18 @@
 // of the last row and column over the pivot). Its index is the path read as a
 // binary number, first decision most significant, so that the 2^H leaves come
 // out in the order of T. Every leaf is a 12 x 12 matrix M_T with the minor
-// det(A[T]): det(A[T u U]) = det(A[T]) det(M_T[U]) for U within 0..11, so the
-// warp-per-matrix minors kernel writes the 2^12 minors of M_T, times det(A[T])
-// (its root minor), straight into the output row at T * 4096; the leaves that
-// meet a small pivot are redone by the fused kernel with its own pivot
-// correction, and only their rows are then scaled by det(A[T]). A pivot of the upper levels with |p| <= thr ||A||max is
-// shifted by C = sign(p) shift ||A||max and recorded; after the scaling,
-// deepest level first, det[m] -= C det[m without the element] over the kept
-// child's subtree (all T in its range, all U), the dropped sibling's rows
-// supplying the second
-// minor. The status word of a matrix collects its leaves' bits; an error bit
-// makes the whole row NaN.
+// det(A[T]), and det(A[T u U]) = det(A[T]) det(M_T[U]) for U within 0..11: the
+// warp-per-matrix minors kernel, with det(A[T]) as its root minor, writes the
+// 2^12 minors of M_T already scaled straight into the output row at T * 4096;
+// the leaves that meet a small pivot are redone by the fused kernel with its
+// own pivot correction, and only their rows are scaled afterwards.
+//
+// A pivot of the upper levels with |p| <= thr ||A||max is shifted by
+// C = sign(p) shift ||A||max and recorded; once the rows are complete, deepest
+// level first, det[m] -= C det[m without the element] over the kept child's
+// subtree (all T in its range, all U), the dropped sibling's rows supplying
+// the second minor. The status word of a matrix collects its leaves' bits; an
+// error bit makes the whole row NaN.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
