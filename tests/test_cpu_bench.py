@@ -90,3 +90,18 @@ def test_minor_set_count_splits_into_tree_and_recursion():
     products), the squares of the minors, and the recursion's FMAs."""
     for n in range(1, 17):
         assert bench.flops_per_set(n) == bench.minors_flops(n) + (2 ** n - 1) + bench.sc_flops(n)
+
+
+def test_cpu_rate_sizes_a_bounded_sample():
+    """The CPU baselines time a sample sized from a probe: whole multiples of
+    the thread count, never more than the workload, at least one per thread."""
+    import numpy as np
+    A = np.zeros((100, 3, 3))
+    calls = []
+
+    def run(sample, threads):
+        calls.append(sample.shape[0])
+        return np.zeros((sample.shape[0], 8))
+    r, threads, count, dt = bench.cpu_rate(run, A, 0.0, 4)
+    assert threads == 4 and count % 4 == 0 and 4 <= count <= 100 and r > 0
+    assert calls[0] == 2 and calls[1] == 4 and calls[2] == count
