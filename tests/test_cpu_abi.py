@@ -169,3 +169,21 @@ def test_mlp_gemm_and_status_argument_errors(lib):
     g.argtypes = [P, sz, ctypes.POINTER(ctypes.c_uint32), P]
     g.restype = ctypes.c_int
     assert g(None, 0, None, None) == 6
+
+
+def test_host_call_workspace_layout(lib):
+    """apm_cdet_connected_host's workspace for n <= 12 (no kernel scratch): per
+    slot the chunk's matrices (one or two), connected sums, minors (one or two
+    rows) and status words, each rounded up to 256 bytes; times the streams."""
+    sz = ctypes.c_size_t
+    hw = lib.apm_cdet_connected_host_workspace_size
+    hw.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.POINTER(sz)]
+    hw.restype = ctypes.c_int
+    r256 = lambda x: (x + 255) // 256 * 256
+    for n, chunk, ns, two in ((10, 100, 3, 0), (12, 2048, 4, 0), (7, 33, 1, 1), (1, 5, 8, 1)):
+        out = sz(0)
+        assert hw(n, chunk, ns, two, ctypes.byref(out)) == 0
+        mats, N = (2 if two else 1), 1 << n
+        slot = (mats * r256(chunk * n * n * 8) + r256(chunk * N * 8) + r256(chunk * mats * N * 8)
+                + r256(chunk * 4))
+        assert out.value == ns * slot, (n, chunk, ns, two)
