@@ -7,16 +7,23 @@
 // The fused minors / connected-sum kernel runs one matrix per CTA, which pays
 // when the recursion follows; for the minors alone its tree levels, one CTA
 // barrier each, leave the SM waiting. Here a warp takes a matrix, as in the
-// XNOR and NAND kernels: elements are decided from the last one down, the
-// upper n-9 depth first (the matrices of kept pivots on a per-warp stack in
-// caller scratch), the last 9 breadth first in shared memory (a node of level
-// J holds the Schur complement on elements 0 .. 8-J of the elements kept on
-// its path; child 2i drops element 8-J, the leading block; child 2i+1 keeps
-// it, the leading block less the rank-1 term over the pivot), and the 16
-// principal minors of every 4 x 4 node of the last level in closed form. Node
-// i of that level is element e's decision in bit e-4 of i, so lane i writes
-// the 16 minors of the sets (i << 4) | X contiguously, and a tail fills 2^9
-// consecutive entries of the row.
+// XNOR and NAND kernels, and elements are decided from the last one down. The
+// FP64 pipe is the bound (one warp instruction per 16 SM cycles), and it is
+// charged for a whole warp instruction whatever the number of active lanes, so
+// the tree is laid out to keep the lanes busy:
+//   * above the last T = min(n, 12) elements, depth first (the matrices of kept
+//     pivots on a per-warp stack in caller scratch);
+//   * the first 5 levels of the T-element tail breadth first in shared memory
+//     (a node of level J holds the Schur complement on elements 0 .. T-1-J of
+//     the elements kept on its path; child 2i drops element T-1-J, the leading
+//     block; child 2i+1 keeps it, the leading block less the rank-1 term over
+//     the pivot), which leaves 32 nodes of order L = T - 5;
+//   * lane i then takes node i and finishes its whole subtree in registers:
+//     fully unrolled Schur steps down to order 3, and the 8 principal minors of
+//     each 3 x 3 node in closed form (row 0 scaled by the node minor first, the
+//     whole by expansion along row 0; no pivot, no division).
+// Node i of the lane level carries element e's decision in bit e - L, so lane i
+// writes the minors of the sets (i << L) | X, X within 0 .. L-1, contiguously.
 //
 // Pivot correction (Section II): this kernel shifts nothing. A matrix that
 // meets a pivot with |p| <= thr ||A||max is flagged, and the fused kernel,
@@ -30,38 +37,39 @@
 
 namespace apm {
 
-constexpr int kFwTail = 9;   // elements expanded breadth first
-constexpr int kFwWarps = 4;  // warps per CTA
+constexpr int kFwTail = 12;   // elements below the depth-first part
+constexpr int kFwBfs = 5;     // tail levels expanded breadth first (32 nodes after them)
+constexpr int kFwWarps = 4;   // warps per CTA
 constexpr int kFwMaxN = 16;
 
-// Tail level J (J = 0..S-4) holds 2^J nodes of size S-J; even levels in bufE,
-// odd in bufO. S = 9: bufE 81, 196, 400; bufO 128, 288, 512.
-__host__ __device__ constexpr int fw_level_entries(int S, int J) { return (1 << J) * (S - J) * (S - J); }
-__host__ __device__ constexpr int fw_buf_entries(int S, int parity) {
+// Tail level J (J = 0..kFwBfs) holds 2^J nodes of size T-J; even levels in
+// bufE, odd in bufO. T = 12: bufE 144, 400, 1024; bufO 242, 648, 1568.
+__host__ __device__ constexpr int fw_level_entries(int T, int J) { return (1 << J) * (T - J) * (T - J); }
+__host__ __device__ constexpr int fw_buf_entries(int T, int parity) {
     int b = 0;
-    for (int J = parity; J <= S - 4; J += 2) b = b > fw_level_entries(S, J) ? b : fw_level_entries(S, J);
+    for (int J = parity; J <= kFwBfs; J += 2) b = b > fw_level_entries(T, J) ? b : fw_level_entries(T, J);
     return b;
 }
 constexpr int kFwBufE = fw_buf_entries(kFwTail, 0);
 constexpr int kFwBufO = fw_buf_entries(kFwTail, 1);
-static_assert(kFwBufE == 400 && kFwBufO == 512, "9-element tail");
-// row factors: one per row of every kept child (2^J (S-J-1), at most 16 x 4), or
-// of one depth-first step (at most 15)
-constexpr int kFwFac = 64;
+static_assert(kFwBufE == 1024 && kFwBufO == 1568, "12-element tail");
+// row factors of one breadth-first level (2^J (T-J-1), at most 16 x 7), or of
+// one depth-first step (at most 15)
+constexpr int kFwFac = 112;
 
 struct alignas(16) FwWarpSmem {
     double bufE[kFwBufE];
     double bufO[kFwBufO];
     double f[kFwFac];
-    double inv[1 << (kFwTail - 5)];  // reciprocal pivots of one level (at most 16 nodes)
-    double nd[2][1 << (kFwTail - 4)];  // node minors of the current and the next level
+    double inv[1 << (kFwBfs - 1)];  // reciprocal pivots of one level (at most 16 nodes)
+    double nd[2][1 << kFwBfs];      // node minors of the current and the next level
     double pdet[kFwMaxN + 1];
     const double *vp[kFwMaxN + 1];  // depth-first views: first element and row stride
     int vs[kFwMaxN + 1];
 };
 static_assert(sizeof(FwWarpSmem) % 16 == 0, "per-warp blocks stay 16-byte aligned");
 
-// stack entries (doubles) for order n: the kept-pivot matrices of depths 1..D-1 (D = n - 9)
+// stack entries (doubles) for order n: the kept-pivot matrices of depths 1..D-1 (D = n - 12)
 __host__ __device__ constexpr size_t fw_stack_entries(int n) {
     const int D = n > kFwTail ? n - kFwTail : 0;
     size_t t = 0;
@@ -77,19 +85,19 @@ __device__ __forceinline__ double fw_inv(double p, double thrA, int &bad, int &s
     return rcp_nr(p);
 }
 
-// One breadth-first level J of the tail: 2^J nodes of size k = S-J in cur give
-// 2^(J+1) children of size k-1 in nxt.
-template <int S, int J>
+// One breadth-first level J of a T-element tail: 2^J nodes of size k = T-J in
+// cur give 2^(J+1) children of size k-1 in nxt.
+template <int T, int J>
 __device__ __forceinline__ void fw_tail_level(const double *cur, double *nxt, FwWarpSmem &w, int lane, double thrA,
                                               int &bad, int &small) {
-    constexpr int k = S - J, k1 = k - 1, kk = k * k, kk1 = k1 * k1, nodes = 1 << J;
+    constexpr int k = T - J, k1 = k - 1, kk = k * k, kk1 = k1 * k1, nodes = 1 << J;
     const double *ndc = w.nd[J & 1];
     double *ndn = w.nd[(J + 1) & 1];
-    for (int i = lane; i < nodes; i += 32) {
-        const double p = cur[i * kk + k1 * k + k1];
-        w.inv[i] = fw_inv(p, thrA, bad, small);
-        ndn[2 * i] = ndc[i];
-        ndn[2 * i + 1] = ndc[i] * p;
+    if (lane < nodes) {
+        const double p = cur[lane * kk + k1 * k + k1];
+        w.inv[lane] = fw_inv(p, thrA, bad, small);
+        ndn[2 * lane] = ndc[lane];
+        ndn[2 * lane + 1] = ndc[lane] * p;
     }
     __syncwarp();
     for (int idx = lane; idx < nodes * k1; idx += 32) {
@@ -107,67 +115,107 @@ __device__ __forceinline__ void fw_tail_level(const double *cur, double *nxt, Fw
     __syncwarp();
 }
 
-// The 16 principal minors of every 4 x 4 node i (node minor d = nd[i]) in
-// closed form, out[16 i + X] for X within {0,1,2,3}: with s_jk the 2 x 2 minors
-// of rows 0,1 and c_jk those of rows 2,3 on columns j,k, the triples by
-// expansion along their third row and the whole by Laplace expansion along rows
-// 0,1. Row 0 is scaled by d first, so that every minor holding element 0 comes
-// out scaled; the other seven are multiplied by d. No pivot, no division.
-template <int S>
-__device__ __forceinline__ void fw_bottom(const double *cur, const double *nd, double *out, int lane) {
-    constexpr int nodes = 1 << (S - 4);
-    for (int i = lane; i < nodes; i += 32) {
-        const double *M = cur + 16 * i;
-        const double d = nd[i];
-        const double a0 = d * M[0], a1 = d * M[1], a2 = d * M[2], a3 = d * M[3];
-        const double s01 = fma(a0, M[5], -a1 * M[4]), s02 = fma(a0, M[6], -a2 * M[4]);
-        const double s03 = fma(a0, M[7], -a3 * M[4]), s12 = fma(a1, M[6], -a2 * M[5]);
-        const double s13 = fma(a1, M[7], -a3 * M[5]), s23 = fma(a2, M[7], -a3 * M[6]);
-        const double c01 = fma(M[8], M[13], -M[9] * M[12]), c02 = fma(M[8], M[14], -M[10] * M[12]);
-        const double c03 = fma(M[8], M[15], -M[11] * M[12]), c12 = fma(M[9], M[14], -M[10] * M[13]);
-        const double c13 = fma(M[9], M[15], -M[11] * M[13]), c23 = fma(M[10], M[15], -M[11] * M[14]);
-        const double p02 = fma(a0, M[10], -a2 * M[8]), p03 = fma(a0, M[15], -a3 * M[12]);
-        const double p12 = fma(M[5], M[10], -M[6] * M[9]), p13 = fma(M[5], M[15], -M[7] * M[13]);
-        const double t012 = fma(M[10], s01, fma(-M[9], s02, M[8] * s12));
-        const double t013 = fma(M[15], s01, fma(-M[13], s03, M[12] * s13));
-        const double t023 = fma(a0, c23, fma(-a2, c03, a3 * c02));
-        const double t123 = fma(M[5], c23, fma(-M[6], c13, M[7] * c12));
-        double q = s01 * c23;
-        q = fma(-s02, c13, q);
-        q = fma(s03, c12, q);
-        q = fma(s12, c03, q);
-        q = fma(-s13, c02, q);
-        q = fma(s23, c01, q);
-        double2 *o = reinterpret_cast<double2 *>(out + 16 * i);
-        o[0] = make_double2(d, a0);
-        o[1] = make_double2(d * M[5], s01);
-        o[2] = make_double2(d * M[10], p02);
-        o[3] = make_double2(d * p12, t012);
-        o[4] = make_double2(d * M[15], p03);
-        o[5] = make_double2(d * p13, t013);
-        o[6] = make_double2(d * c23, t023);
-        o[7] = make_double2(d * t123, q);
+// The 8 principal minors of a 3 x 3 node C with node minor d, out[X] for X
+// within {0,1,2}: row 0 scaled by d first, so that the four minors holding
+// element 0 come out scaled; the 2 x 2 minors directly; the whole by expansion
+// along row 0. 19 FP64 operations, no division.
+__device__ __forceinline__ void fw_cf3(const double (&C)[3][3], double d, double *out) {
+    const double a0 = d * C[0][0], a1 = d * C[0][1], a2 = d * C[0][2];
+    const double m12 = fma(C[1][1], C[2][2], -C[1][2] * C[2][1]);
+    const double m02 = fma(C[1][0], C[2][2], -C[1][2] * C[2][0]);
+    const double m01 = fma(C[1][0], C[2][1], -C[1][1] * C[2][0]);
+    const double s01 = fma(a0, C[1][1], -a1 * C[1][0]);
+    const double s02 = fma(a0, C[2][2], -a2 * C[2][0]);
+    const double t = fma(a0, m12, fma(-a1, m02, a2 * m01));
+    double2 *o = reinterpret_cast<double2 *>(out);
+    o[0] = make_double2(d, a0);
+    o[1] = make_double2(d * C[1][1], s01);
+    o[2] = make_double2(d * C[2][2], s02);
+    o[3] = make_double2(d * m12, t);
+}
+
+// All 2^K principal minors of a K x K node M in registers (node minor d) into
+// out[0 .. 2^K): the last element's pivot gives the kept child (the Schur
+// complement) at out + 2^(K-1), the leading block the dropped one at out.
+template <int K>
+__device__ __forceinline__ void fw_lane_tree(const double (&M)[K][K], double d, double *out, double thrA, int &bad,
+                                             int &small) {
+    if constexpr (K == 3) {
+        fw_cf3(M, d, out);
+    } else {
+        constexpr int K1 = K - 1;
+        const double p = M[K1][K1];
+        const double iv = fw_inv(p, thrA, bad, small);
+        double S[K1][K1];
+#pragma unroll
+        for (int r = 0; r < K1; ++r) {
+            const double f = M[r][K1] * iv;
+#pragma unroll
+            for (int q = 0; q < K1; ++q) S[r][q] = fma(-f, M[K1][q], M[r][q]);
+        }
+        fw_lane_tree<K1>(S, d * p, out + (1 << K1), thrA, bad, small);
+        double Lb[K1][K1];
+#pragma unroll
+        for (int r = 0; r < K1; ++r)
+#pragma unroll
+            for (int q = 0; q < K1; ++q) Lb[r][q] = M[r][q];
+        fw_lane_tree<K1>(Lb, d, out, thrA, bad, small);
     }
 }
 
-template <int S, int J>
+// A lane's node of size K, read from shared memory (row-major), node minor d:
+// its kept child is formed in registers; its dropped child, the leading block,
+// is read again from shared memory, so that the two need not be live at once.
+template <int K>
+__device__ __forceinline__ void fw_lane_root(const double *P, double d, double *out, double thrA, int &bad,
+                                             int &small) {
+    constexpr int K1 = K - 1;
+    const double p = P[K1 * K + K1];
+    const double iv = fw_inv(p, thrA, bad, small);
+    {
+        double S[K1][K1];
+#pragma unroll
+        for (int r = 0; r < K1; ++r) {
+            const double f = P[r * K + K1] * iv;
+#pragma unroll
+            for (int q = 0; q < K1; ++q) S[r][q] = fma(-f, P[K1 * K + q], P[r * K + q]);
+        }
+        fw_lane_tree<K1>(S, d * p, out + (1 << K1), thrA, bad, small);
+    }
+    double Lb[K1][K1];
+#pragma unroll
+    for (int r = 0; r < K1; ++r)
+#pragma unroll
+        for (int q = 0; q < K1; ++q) Lb[r][q] = P[r * K + q];
+    fw_lane_tree<K1>(Lb, d, out, thrA, bad, small);
+}
+
+template <int T, int J>
 __device__ __forceinline__ void fw_tail_levels(double *cur, double *nxt, double *out, FwWarpSmem &w, int lane,
                                                double thrA, int &bad, int &small) {
-    if constexpr (J <= S - 5) {
-        fw_tail_level<S, J>(cur, nxt, w, lane, thrA, bad, small);
-        fw_tail_levels<S, J + 1>(nxt, cur, out, w, lane, thrA, bad, small);
+    if constexpr (J < kFwBfs) {
+        fw_tail_level<T, J>(cur, nxt, w, lane, thrA, bad, small);
+        fw_tail_levels<T, J + 1>(nxt, cur, out, w, lane, thrA, bad, small);
     } else {
-        fw_bottom<S>(cur, w.nd[J & 1], out, lane);
+        constexpr int L = T - kFwBfs;
+        fw_lane_root<L>(cur + lane * L * L, w.nd[J & 1][lane], out + (lane << L), thrA, bad, small);
     }
+}
+
+// The tail of T elements whose root matrix is in w.bufE (node minor w.nd[0][0]).
+template <int T>
+__device__ __forceinline__ void fw_tail(double *out, FwWarpSmem &w, int lane, double thrA, int &bad, int &small) {
+    fw_tail_levels<T, 0>(w.bufE, w.bufO, out, w, lane, thrA, bad, small);
 }
 
 // One matrix of order n (9..16), whole warp: its 2^n minors, each times pre,
 // into out. Returns 1 when a pivot is below thrA or zero (the fused kernel
 // redoes the matrix) or the input is not finite (the fused kernel then sets the
 // status and NaN).
-__device__ __forceinline__ int fw_matrix(const double *A, int n, double *out, double thr, double pre, double *stack,
-                                         FwWarpSmem &w, int lane) {
-    const int D = n - kFwTail;
+template <int T>
+__device__ __forceinline__ int fw_matrix(const double *A, int n, double *out, double thr, double pre,
+                                         const double *anorm, double *stack, FwWarpSmem &w, int lane) {
+    const int D = n - T;
     int bad = 0, small = 0, nonfin = 0;
     double amax = 0.0;
     for (int e = lane; e < n * n; e += 32) {
@@ -178,6 +226,7 @@ __device__ __forceinline__ int fw_matrix(const double *A, int n, double *out, do
     nonfin = __any_sync(0xffffffffu, nonfin);
     if (nonfin) return 1;
     for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    if (anorm) amax = *anorm;
     const double thrA = thr * (amax > 0.0 ? amax : 1.0);
     if (lane == 0) {
         w.vp[0] = A;
@@ -233,19 +282,27 @@ __device__ __forceinline__ int fw_matrix(const double *A, int n, double *out, do
         }
         if (lane == 0) w.nd[0][0] = w.pdet[D];
         __syncwarp();
-        fw_tail_levels<kFwTail, 0>(w.bufE, w.bufO, out + (t << kFwTail), w, lane, thrA, bad, small);
+        fw_tail<T>(out + (t << T), w, lane, thrA, bad, small);
         __syncwarp();
     }
     return __any_sync(0xffffffffu, bad | small);
 }
 
 // Every matrix; redo[b] = 1 where the fused kernel must compute it again. pre
-// (or NULL for 1): a factor per matrix on all its minors.
-__global__ void __launch_bounds__(kFwWarps * 32, 4) fpm_warp_kernel(const double *__restrict__ A, int n,
+// (or NULL for 1): a factor per matrix on all its minors; anorm (or NULL): the
+// scale of the threshold, anorm[b >> anorm_shift], in place of the matrix's own
+// ||A||max (the leaves of a larger matrix take its norm). T = min(n, 12), one
+// instantiation each, so that the register allocation of the largest lane
+// subtree does not burden the others. Shared memory (90 KB per CTA) admits two
+// CTAs per SM, so each thread may use up to 255 registers.
+template <int T>
+__global__ void __launch_bounds__(kFwWarps * 32, 2) fpm_warp_kernel(const double *__restrict__ A, int n,
                                                                   int64_t batch, double *minors, double thr,
                                                                   const double *__restrict__ pre, uint32_t *redo,
                                                                   uint32_t *status, double *stack_base,
-                                                                  size_t stack_per_warp) {
+                                                                  size_t stack_per_warp,
+                                                                  const double *__restrict__ anorm,
+                                                                  int anorm_shift) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     FwWarpSmem &w = reinterpret_cast<FwWarpSmem *>(smem_raw)[wid];
@@ -254,7 +311,8 @@ __global__ void __launch_bounds__(kFwWarps * 32, 4) fpm_warp_kernel(const double
     double *stack = stack_base ? stack_base + gw * stack_per_warp : nullptr;
     const int64_t nn = static_cast<int64_t>(n) * n, N = int64_t(1) << n;
     for (int64_t b = gw; b < batch; b += nw) {
-        const int r = fw_matrix(A + b * nn, n, minors + b * N, thr, pre ? pre[b] : 1.0, stack, w, lane);
+        const int r = fw_matrix<T>(A + b * nn, n, minors + b * N, thr, pre ? pre[b] : 1.0,
+                                   anorm ? anorm + (b >> anorm_shift) : nullptr, stack, w, lane);
         if (lane == 0) {
             redo[b] = static_cast<uint32_t>(r);
             if (status && !r) status[b] = 0u;
@@ -262,15 +320,27 @@ __global__ void __launch_bounds__(kFwWarps * 32, 4) fpm_warp_kernel(const double
     }
 }
 
-int fpm_warp_grid(int64_t batch, int *err) {
+using FwKernel = void (*)(const double *, int, int64_t, double *, double, const double *, uint32_t *, uint32_t *,
+                         double *, size_t, const double *, int);
+static FwKernel fw_kernel_for(int n) {
+    switch (n < kFwTail ? n : kFwTail) {
+        case 9: return fpm_warp_kernel<9>;
+        case 10: return fpm_warp_kernel<10>;
+        case 11: return fpm_warp_kernel<11>;
+        default: return fpm_warp_kernel<12>;
+    }
+}
+
+static int fpm_warp_grid(int n, int64_t batch, int *err) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const size_t smem = kFwWarps * sizeof(FwWarpSmem);
+    const FwKernel kern = fw_kernel_for(n);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(fpm_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fpm_warp_kernel, kFwWarps * 32, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kFwWarps * 32, smem);
     if (e != cudaSuccess || per_sm < 1) {
         *err = e != cudaSuccess ? static_cast<int>(e) : static_cast<int>(cudaErrorInvalidConfiguration);
         return 0;
@@ -289,7 +359,7 @@ struct FwPlan {
 };
 static int fw_plan(int n, int64_t batch, FwPlan *p, int *grid) {
     int err = 0;
-    *grid = fpm_warp_grid(batch, &err);
+    *grid = fpm_warp_grid(n, batch, &err);
     if (err) return err;
     auto al = [](size_t x) { return (x + 255) & ~static_cast<size_t>(255); };
     p->stack = al(static_cast<size_t>(*grid) * kFwWarps * fw_stack_entries(n) * sizeof(double));
@@ -314,7 +384,8 @@ size_t fpm_warp_workspace_bytes(int n, int64_t batch, int *err) {
 }
 
 int launch_fpm_warp(const double *A, int n, int64_t batch, double *minors, double thr, double shf,
-                    uint32_t *status, void *workspace, cudaStream_t s, const double *pre, uint32_t **redo_out) {
+                    uint32_t *status, void *workspace, cudaStream_t s, const double *pre, uint32_t **redo_out,
+                    const double *anorm_in, int anorm_shift) {
     FwPlan plan;
     int grid = 0;
     int err = fw_plan(n, batch, &plan, &grid);
@@ -326,7 +397,8 @@ int launch_fpm_warp(const double *A, int n, int64_t batch, double *minors, doubl
     uint32_t *redo = reinterpret_cast<uint32_t *>(ws + plan.stack);
     double *fused = plan.fused ? reinterpret_cast<double *>(ws + plan.stack + plan.redo) : nullptr;
     if (redo_out) *redo_out = redo;
-    fpm_warp_kernel<<<grid, kFwWarps * 32, smem, s>>>(A, n, batch, minors, thr, pre, redo, status, stack, per);
+    fw_kernel_for(n)<<<grid, kFwWarps * 32, smem, s>>>(A, n, batch, minors, thr, pre, redo, status, stack, per,
+                                                        anorm_in, anorm_shift);
     err = static_cast<int>(cudaGetLastError());
     if (err) return err;
     // the flagged matrices again, by the fused kernel with the pivot correction
@@ -342,6 +414,8 @@ int launch_fpm_warp(const double *A, int n, int64_t batch, double *minors, doubl
     a.piv_shift = shf;
     a.redo = redo;
     a.gscratch = fused;
+    a.anorm_in = anorm_in;
+    a.anorm_shift = anorm_shift;
     return launch_fpm_cdet(a, s);
 }
 
