@@ -78,16 +78,21 @@ typedef enum {
  * it is replaced by p + C with C = sign(p)*piv_shift*||A||max (sign(0) = +1),
  * the node's minor is stored with the shifted pivot, and after the tree the
  * shift is removed exactly by det(A[S]) = det(A~[S]) - C det(A[S \ {l}]),
- * applied to the node and its whole right subtree, deepest level first.
- * Any choice gives the same exact result; the threshold trades stability.
+ * applied to the node's whole right subtree, deepest level first; the node's
+ * own minor is written as det(A[S \ {l}]) p with the unshifted pivot.
+ * Any choice gives the same exact result; the threshold trades stability. An
+ * uncorrected pivot p amplifies the rounding of the minors below it by about
+ * ||A||max / |p|, so the default 1e-4 keeps that factor under 10^4 (about
+ * 2e-12 relative to the sum of absolute terms); the minors of the Hubbard
+ * Green's-function matrices of Section V meet no pivot below 1e-2 ||A||max.
  * NULL selects the defaults below (||A||max = 0 is treated as 1).
  */
 typedef struct {
-    double piv_threshold; /* default 1e-6 */
+    double piv_threshold; /* default 1e-4 */
     double piv_shift;     /* default 1.0 */
 } apm_pivot_opts;
 
-#define APM_DEFAULT_PIV_THRESHOLD 1e-6
+#define APM_DEFAULT_PIV_THRESHOLD 1e-4
 #define APM_DEFAULT_PIV_SHIFT 1.0
 
 /*
@@ -104,9 +109,9 @@ typedef struct {
  *   workspace / workspace_bytes: scratch for n >= 9 (see apm_workspace_size),
  *           256-byte aligned; may be NULL/0 for n <= 8.
  * For n = 9..16 one warp takes a matrix (elements decided from the last one
- * down, the upper ones depth first, the last 9 breadth first in shared memory,
- * the 16 minors of every 4 x 4 node of the last level in closed form); it
- * shifts no pivot, and the matrices that meet a pivot with |p| <= piv_threshold
+ * down: above the last 12 depth first, then 5 levels breadth first in shared
+ * memory, then each lane finishes one of the 32 nodes left, in registers, down
+ * to 3 x 3 nodes whose 8 minors it writes in closed form); it shifts no pivot, and the matrices that meet a pivot with |p| <= piv_threshold
  * ||A||max are computed again, with the correction, by the one-CTA-per-matrix
  * kernel of apm_cdet_connected, launched after it on those matrices only.
  * For n = 17..24 the tree is cut in two: its upper n - 12 levels (elements n-1
@@ -114,9 +119,11 @@ typedef struct {
  * of the 2^(n-12) leaves, the 12 x 12 Schur complement M_T of the kept upper
  * set T, goes through the n = 12 path above, whose 4096 minors fill the row at
  * T * 4096 and are scaled by det(A[T]): det(A[T u U]) = det(A[T]) det(M_T[U]).
- * Upper-level pivots are corrected as above (threshold against ||A||max; at
- * most 256 per matrix, more set APM_ST_CORRECTION_OVERFLOW), the leaves' own
- * against ||M_T||max. An error bit anywhere makes the matrix's whole row NaN.
+ * Upper-level pivots are corrected as above (at most 256 per matrix, more set
+ * APM_ST_CORRECTION_OVERFLOW), and so are the leaves' own: threshold and shift
+ * of both are relative to ||A||max of the whole matrix (a leaf's entries can be
+ * inflated by a small upper pivot; its pivots are pivots of the same tree). An
+ * error bit anywhere makes the matrix's whole row NaN.
  */
 apm_status_t apm_all_minors(const double *A, int n, int64_t batch, double *minors,
                             const apm_pivot_opts *opt, uint32_t *status, void *workspace,
@@ -353,9 +360,14 @@ apm_status_t apm_keldysh2_sum(const double *Mu, const double *Md, int n, int64_t
  *   warps) for orders up to 14, 26.1 MB, held on every GPU that loads the
  *   library until the process exits; matrices are never split over warps here. Orders above 14 are rejected with APM_ERR_UNSUPPORTED_N (use
  *   apm_keldysh_sum with a workspace). The call allocates nothing.
- *   The first call on a device looks up the array's device address (once per
- *   device, with that device current); make that first call before any stream
- *   capture. Every call shares the one array: calls that overlap on the GPU (for
+ *   The first call on a device, even one with batch 0, looks up the array's
+ *   device address (once per device, with that device current), which also
+ *   loads the library's device code, array included, if lazy module loading
+ *   has not yet done so; make that first call before any stream capture and
+ *   before a pool allocator takes the device's free memory. The address is kept
+ *   for the life of the process: after cudaDeviceReset on that device (which
+ *   destroys the context the array lived in) this entry point must not be
+ *   called again. Every call shares the one array: calls that overlap on the GPU (for
  *   example on two streams) race and give wrong results; serialise them. The
  *   array keeps whatever the last call left there; nothing in it needs to start
  *   at zero, because every entry is written before it is read.
@@ -544,6 +556,39 @@ apm_status_t apm_mlp_forward(const apm_mlp *net, const uint16_t *X, int batch_pa
 apm_status_t apm_mlp_train_step(const apm_mlp *net, const uint16_t *X, const float *target, int batch_padded,
                                 int batch_valid, float lr, int step, float *loss_acc, void *workspace,
                                 size_t workspace_bytes, apm_stream_t stream);
+/* The two halves of apm_mlp_train_step, for data-parallel training across
+ * processes (no counterpart in the paper): apm_mlp_gradient writes the gradient
+ * of the mean squared error over the first batch_valid rows into net->grad (and
+ * adds the loss to *loss_acc); the caller may then replace net->grad by its
+ * average over the processes; apm_mlp_adam_step applies one Adam step from
+ * net->grad and refreshes param_bf16. Together they do exactly what
+ * apm_mlp_train_step does, bit for bit. */
+apm_status_t apm_mlp_gradient(const apm_mlp *net, const uint16_t *X, const float *target, int batch_padded,
+                              int batch_valid, float *loss_acc, void *workspace, size_t workspace_bytes,
+                              apm_stream_t stream);
+apm_status_t apm_mlp_adam_step(const apm_mlp *net, float lr, int step, apm_stream_t stream);
+
+/*
+ * apm_order_sums -- per-order sums of the connected sums of whole vertex sets,
+ * the data of the power-series estimator (Section V, Eq. series: the order-m
+ * term is the integral of c_m over the configurations of m vertices; a sample of
+ * configurations estimates it by their mean, its sign problem by the ratio of
+ * sum c to sum |c|). A data-parallel job reduces its rows on each device with
+ * this call and adds the few resulting numbers across processes on the host.
+ *   c      connected-sum rows (device): with n_arr NULL, row b has 2^n_fixed
+ *          doubles at c + b 2^n_fixed; else row b has 2^n_arr[b] doubles at
+ *          c + c_off[b] (the layout of apm_cdet_connected_varlen).
+ *   n_arr, c_off  both NULL (fixed order n_fixed in 1..n_max) or both set.
+ *   n_max  1..16.
+ *   out    [n_max+1][4] device doubles, overwritten: out[m] = (count, sum c,
+ *          sum |c|, sum c^2) over the rows of order m of c_m = c[2^m - 1], the
+ *          connected sum of the whole vertex set; out[0] = 0, and rows whose
+ *          order lies outside 1..n_max count nowhere.
+ * One CTA adds in a fixed order: repeated calls give bit-identical results.
+ * Asynchronous on `stream`; allocates nothing.
+ */
+apm_status_t apm_order_sums(const double *c, int n_fixed, const int32_t *n_arr, const int64_t *c_off,
+                            int64_t batch, int n_max, double *out, apm_stream_t stream);
 
 /*
  * apm_workspace_size -- bytes of device scratch the call `op` needs for orders up

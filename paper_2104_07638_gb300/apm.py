@@ -79,6 +79,7 @@ def lib():
                 "apm_workspace_size": [i32, i32, i64, i32, ctypes.POINTER(sz)],
                 "apm_status_reduce": [P, i64, ctypes.POINTER(ctypes.c_uint32), P],
                 "apm_fp64_fma_probe": [P, i32, i32, i32, P],
+                "apm_order_sums": [P, i32, P, P, i64, i32, P, P],
             }
             for name, args in sig.items():
                 f = getattr(L, name)
@@ -124,7 +125,7 @@ def _mat_batch(A: torch.Tensor, dtype=torch.float64, name="A"):
 def _opts(piv_threshold, piv_shift):
     if piv_threshold is None and piv_shift is None:
         return None
-    return ctypes.pointer(PivotOpts(1e-6 if piv_threshold is None else piv_threshold,
+    return ctypes.pointer(PivotOpts(1e-4 if piv_threshold is None else piv_threshold,
                                     1.0 if piv_shift is None else piv_shift))
 
 
@@ -418,6 +419,31 @@ def keldysh2_sum(Mu: torch.Tensor, Md: torch.Tensor, signed=False, partial=False
     return res[0] if len(res) == 1 else tuple(res)
 
 
+def order_sums(c: torch.Tensor, n: int | None = None, n_arr: torch.Tensor | None = None,
+               c_off: torch.Tensor | None = None, n_max: int | None = None) -> torch.Tensor:
+    """apm_order_sums: a (n_max+1, 4) float64 device tensor whose row m holds
+    (count, sum c, sum |c|, sum c^2) of c_m = c[2^m - 1], the connected sum of
+    the whole vertex set, over the rows of order m. c is (batch, 2^n) for a
+    fixed order n, or the packed rows of an uneven batch with n_arr (int32) and
+    c_off (int64) as in cdet_connected_varlen."""
+    if not isinstance(c, torch.Tensor) or not c.is_cuda or c.dtype != torch.float64 or not c.is_contiguous():
+        raise TypeError("c must be a contiguous float64 CUDA tensor")
+    if n_arr is None:
+        if n is None or c.dim() != 2 or c.shape[1] != 1 << n:
+            raise ValueError("fixed order: c must be (batch, 2^n)")
+        b, n_max = c.shape[0], n if n_max is None else n_max
+    else:
+        if c_off is None or n_arr.dtype != torch.int32 or c_off.dtype != torch.int64:
+            raise TypeError("uneven batch: n_arr int32 and c_off int64")
+        b = n_arr.numel()
+        n_max = int(n_arr.max()) if n_max is None else n_max
+    out = torch.empty((n_max + 1, 4), dtype=torch.float64, device=c.device)
+    with torch.cuda.device(c.device):
+        _check(lib().apm_order_sums(_ptr(c), 0 if n is None else n, _ptr(n_arr), _ptr(c_off), b, n_max, _ptr(out),
+                                    _stream(c)), "apm_order_sums")
+    return out
+
+
 def keldysh_sum_noalloc(Mt: torch.Tensor, signed=False, partial=False, return_status=False):
     """apm_keldysh_sum_noalloc: the Keldysh sum without a caller workspace (the
     library's fixed device array serves as scratch; orders 1..14; calls that
@@ -431,8 +457,9 @@ def keldysh_sum_noalloc(Mt: torch.Tensor, signed=False, partial=False, return_st
     s = torch.empty((b, 2), dtype=torch.float64, device=dev)
     p = torch.empty((b, n + 1, 2), dtype=torch.float64, device=dev) if partial else None
     st = torch.zeros(b, dtype=torch.int32, device=dev) if return_status else None
-    _check(lib().apm_keldysh_sum_noalloc(_ptr(Mt), n, b, KELDYSH_SIGNED if signed else 0, _ptr(s),
-                                         _ptr(p), _ptr(st), _stream(Mt)), "apm_keldysh_sum_noalloc")
+    with torch.cuda.device(dev):   # the library resolves its array on the current device
+        _check(lib().apm_keldysh_sum_noalloc(_ptr(Mt), n, b, KELDYSH_SIGNED if signed else 0, _ptr(s),
+                                             _ptr(p), _ptr(st), _stream(Mt)), "apm_keldysh_sum_noalloc")
     res = [torch.view_as_complex(s)]
     if partial:
         res.append(torch.view_as_complex(p))

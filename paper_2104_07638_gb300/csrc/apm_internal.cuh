@@ -62,6 +62,11 @@ struct CdetArgs {
     double piv_shift;
     int fsc_from_n;  // orders >= this (0: none) leave the weights a[] in c for the fast subset convolution
     const uint32_t *redo;  // fixed-order launch: if set, only the matrices b with redo[b] != 0
+    // fixed-order launch: if set, matrix b scales its pivot threshold and shift
+    // by anorm_in[b >> anorm_shift] instead of its own ||A||max (the leaves of
+    // a larger matrix take that matrix's norm)
+    const double *anorm_in;
+    int anorm_shift;
 };
 
 // Orders whose connected sums apm_cdet_connected and its uneven-batch form take
@@ -77,9 +82,11 @@ constexpr int kWarpMinorsFromN = 9;
 size_t fpm_warp_workspace_bytes(int n, int64_t batch, int *err);
 // pre (or NULL): a factor per matrix on all its minors, not applied to the
 // matrices redone by the fused kernel, whose flags come back in *redo_out.
+// anorm_in (or NULL): per matrix b the scale anorm_in[b >> anorm_shift] of the
+// pivot threshold and shift instead of the matrix's own ||A||max.
 int launch_fpm_warp(const double *A, int n, int64_t batch, double *minors, double thr, double shf,
                     uint32_t *status, void *workspace, cudaStream_t s, const double *pre = nullptr,
-                    uint32_t **redo_out = nullptr);
+                    uint32_t **redo_out = nullptr, const double *anorm_in = nullptr, int anorm_shift = 0);
 
 // All principal minors for orders 17..24: the upper levels of the tree breadth
 // first, the 12 x 12 leaves by the fused kernel (fpm_big.cu).
@@ -174,6 +181,7 @@ struct MlpWork {
     float *part;    // split-K partial tiles
     __nv_bfloat16 *h1, *h2, *h3, *dzb, *t1, *t2, *wt;
     float *y, *dy, *dz32, *dh32;
+    float *pcol, *pcol2, *pvec, *pvec2;  // per-block partial column sums of the backward pass
 };
 // C = A * Bt^T (+ bias) (ReLU) on the tensor cores; part (part_floats) holds
 // split-K partials when K is long next to M x N
@@ -188,6 +196,9 @@ int mlp_forward(const MlpParams &P, const __nv_bfloat16 *X, int Bp, float *y, Ml
 int mlp_train_step(MlpParams &P, const __nv_bfloat16 *X, const float *target, int Bp, int B_valid, MlpWork &w,
                    float lr, int step, float *loss_acc, cudaStream_t s);
 int mlp_refresh_bf16(MlpParams &P, cudaStream_t s);
+int mlp_gradient(MlpParams &P, const __nv_bfloat16 *X, const float *target, int Bp, int B_valid, MlpWork &w,
+                 float *loss_acc, cudaStream_t s);
+int mlp_adam(MlpParams &P, float lr, int step, cudaStream_t s);
 
 int launch_fp64_probe(double *sink, int blocks, int threads, int iters, cudaStream_t s);
 

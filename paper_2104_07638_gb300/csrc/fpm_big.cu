@@ -21,11 +21,16 @@
 // own pivot correction, and only their rows are scaled afterwards.
 //
 // A pivot of the upper levels with |p| <= thr ||A||max is shifted by
-// C = sign(p) shift ||A||max and recorded; once the rows are complete, deepest
-// level first, det[m] -= C det[m without the element] over the kept child's
-// subtree (all T in its range, all U), the dropped sibling's rows supplying
-// the second minor. The status word of a matrix collects its leaves' bits; an
-// error bit makes the whole row NaN.
+// C = sign(p) shift ||A||max and recorded with its unshifted value; once the
+// rows are complete, deepest level first, det[m] -= C det[m without the
+// element] over the kept child's subtree (all T in its range, all U), the
+// dropped sibling's rows supplying the second minor, except for the node's own
+// minor (the first T of the range, U empty), which is written as the sibling's
+// minor times the unshifted pivot. The leaves take the threshold and the shift
+// relative to ||A||max of their matrix, not to their own largest entry: a leaf
+// is a Schur complement whose entries a small upper pivot can inflate, and its
+// pivots are pivots of the same tree as the upper ones. The status word of a
+// matrix collects its leaves' bits; an error bit makes the whole row NaN.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -40,7 +45,7 @@ constexpr int kBigThreads = 256;
 // Workspace parts (bytes, each a multiple of 256).
 struct BigPlan {
     int H;
-    size_t thr, cm, flags, ccount, clog, det, nodeE, nodeO, lstat, leafws, total;
+    size_t thr, cm, an, flags, ccount, clog, det, nodeE, nodeO, lstat, leafws, total;
 };
 
 static size_t big_align(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
@@ -57,6 +62,7 @@ static int big_plan(int n, int64_t batch, BigPlan *p) {
     }
     p->thr = big_align(b * sizeof(double));
     p->cm = p->thr;
+    p->an = p->thr;
     p->flags = big_align(b * sizeof(uint32_t));
     p->ccount = big_align(b * sizeof(int));
     p->clog = big_align(b * kBigCorrCap * 2 * sizeof(double));
@@ -66,7 +72,7 @@ static int big_plan(int n, int64_t batch, BigPlan *p) {
     p->lstat = big_align(b * (static_cast<size_t>(1) << p->H) * sizeof(uint32_t));
     int err = 0;
     p->leafws = big_align(fpm_warp_workspace_bytes(kBigLeafN, batch << p->H, &err));
-    p->total = p->thr + p->cm + p->flags + p->ccount + p->clog + 2 * p->det + p->nodeE + p->nodeO + p->lstat +
+    p->total = p->thr + p->cm + p->an + p->flags + p->ccount + p->clog + 2 * p->det + p->nodeE + p->nodeO + p->lstat +
                p->leafws;
     return err;
 }
@@ -80,9 +86,10 @@ size_t fpm_big_workspace_bytes(int n, int64_t batch, int *err) {
 }
 
 // One warp per matrix: ||A||max and finiteness; the scaled threshold and
-// shift, the root's minor 1, a cleared record count.
+// shift, the norm itself (for the leaves), the root's minor 1, a cleared
+// record count.
 __global__ void big_prep_kernel(const double *__restrict__ A, int n, int64_t batch, double thr, double shf,
-                                double *thrA, double *Cm, uint32_t *flags, int *ccount, double *det0) {
+                                double *thrA, double *Cm, double *an, uint32_t *flags, int *ccount, double *det0) {
     const int lane = threadIdx.x & 31;
     const int64_t b = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     if (b >= batch) return;
@@ -100,6 +107,7 @@ __global__ void big_prep_kernel(const double *__restrict__ A, int n, int64_t bat
         const double sc = amax > 0.0 ? amax : 1.0;
         thrA[b] = thr * sc;
         Cm[b] = shf * sc;
+        an[b] = sc;
         flags[b] = nonfin ? APM_ST_NONFINITE_INPUT : 0u;
         ccount[b] = 0;
         det0[b] = 1.0;
@@ -141,7 +149,7 @@ __global__ void big_level_kernel(const double *__restrict__ src, double *__restr
             if (pos < kBigCorrCap) {
                 const int64_t i = w - (b << l);
                 clog[(b * kBigCorrCap + pos) * 2] = static_cast<double>(l) + 32.0 * static_cast<double>(i);
-                clog[(b * kBigCorrCap + pos) * 2 + 1] = C;
+                clog[(b * kBigCorrCap + pos) * 2 + 1] = p;
             } else {
                 atomicOr(&flags[b], APM_ST_CORRECTION_OVERFLOW);
             }
@@ -166,9 +174,10 @@ __global__ void big_scale_redo_kernel(double *out, int64_t leaves, const uint32_
 
 // One CTA per matrix: the upper-level corrections, deepest level first:
 // for the kept child of node (l, i), every T in its range and every U,
-// out[T, U] -= C out[T - span, U], span = 2^(H-1-l).
+// out[T, U] -= C out[T - span, U], span = 2^(H-1-l), C = sign(p) Cm; the
+// node's own minor (e = 0) is out[T - span, 0] p with the unshifted pivot p.
 __global__ void big_backprop_kernel(double *out, int n, int H, const int *ccount, const double *clog,
-                                    const uint32_t *flags) {
+                                    const double *Cm, const uint32_t *flags) {
     const int64_t b = blockIdx.x;
     const int cnt = ccount[b] < kBigCorrCap ? ccount[b] : kBigCorrCap;
     if (cnt == 0 || (flags[b] & APM_ST_ERROR_MASK)) return;
@@ -179,13 +188,15 @@ __global__ void big_backprop_kernel(double *out, int n, int H, const int *ccount
             const int64_t ci = static_cast<int64_t>(code);
             if (static_cast<int>(ci % 32) != l) continue;
             const int64_t i = ci / 32;
-            const double C = clog[(b * kBigCorrCap + j) * 2 + 1];
+            const double pv = clog[(b * kBigCorrCap + j) * 2 + 1];
+            const double C = pv >= 0.0 ? Cm[b] : -Cm[b];
             const int64_t span = int64_t(1) << (H - 1 - l);
             const int64_t t0 = (2 * i + 1) * span;
             const int64_t cnt_e = span << kBigLeafN;
             double *kept = row + (t0 << kBigLeafN);
             const double *drop = row + ((t0 - span) << kBigLeafN);
-            for (int64_t e = threadIdx.x; e < cnt_e; e += blockDim.x) kept[e] = fma(-C, drop[e], kept[e]);
+            for (int64_t e = threadIdx.x; e < cnt_e; e += blockDim.x)
+                kept[e] = e == 0 ? drop[0] * pv : fma(-C, drop[e], kept[e]);
         }
         __syncthreads();
     }
@@ -223,6 +234,8 @@ int launch_fpm_big(const double *A, int n, int64_t batch, double *minors, double
     w += p.thr;
     double *Cm = reinterpret_cast<double *>(w);
     w += p.cm;
+    double *an = reinterpret_cast<double *>(w);
+    w += p.an;
     uint32_t *flags = reinterpret_cast<uint32_t *>(w);
     w += p.flags;
     int *ccount = reinterpret_cast<int *>(w);
@@ -239,7 +252,7 @@ int launch_fpm_big(const double *A, int n, int64_t batch, double *minors, double
 
     const int64_t warps0 = batch;
     big_prep_kernel<<<static_cast<unsigned>((warps0 * 32 + kBigThreads - 1) / kBigThreads), kBigThreads, 0, s>>>(
-        A, n, batch, thr, shf, thrA, Cm, flags, ccount, det[0]);
+        A, n, batch, thr, shf, thrA, Cm, an, flags, ccount, det[0]);
     const double *src = A;
     for (int l = 0; l < H; ++l) {
         const int64_t nodes = batch << l;
@@ -253,10 +266,11 @@ int launch_fpm_big(const double *A, int n, int64_t batch, double *minors, double
     if (err) return err;
     // the leaves: 12 x 12 matrices in the order of T, their minors into the rows
     uint32_t *redo = nullptr;
-    err = launch_fpm_warp(src, kBigLeafN, batch << H, minors, thr, shf, lstat, leafws, s, det[H & 1], &redo);
+    err = launch_fpm_warp(src, kBigLeafN, batch << H, minors, thr, shf, lstat, leafws, s, det[H & 1], &redo, an,
+                          H);
     if (err) return err;
     big_scale_redo_kernel<<<1216, 256, 0, s>>>(minors, batch << H, redo, det[H & 1]);
-    big_backprop_kernel<<<static_cast<unsigned>(batch), 512, 0, s>>>(minors, n, H, ccount, clog, flags);
+    big_backprop_kernel<<<static_cast<unsigned>(batch), 512, 0, s>>>(minors, n, H, ccount, clog, Cm, flags);
     big_status_kernel<<<static_cast<unsigned>(batch), 512, 0, s>>>(minors, n, H, flags, lstat, status);
     return static_cast<int>(cudaGetLastError());
 }

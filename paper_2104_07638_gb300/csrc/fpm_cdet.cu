@@ -26,8 +26,11 @@
 //   matrix. The shift equals adding C to A_ll for every mask of that subtree, so
 //   by linearity in row l the exact minors follow from
 //       det[m] = det~[m] - C det[m \ {l}]
-//   for the node itself and every mask of its right subtree, applied deepest
-//   level first (a shallower correction must see deeper ones already removed).
+//   for every mask of its right subtree below the node, applied deepest level
+//   first (a shallower correction must see deeper ones already removed). The
+//   node's own minor is written as det[m \ {l}] p with the logged unshifted
+//   pivot: the subtraction would leave it with an error of eps C |det[m \ {l}]|,
+//   large next to the minor itself when p is tiny.
 //
 // Connected sums: popcount layers k = 2..n in order (every proper subset of a
 // k-set lies in an earlier layer). For S with lowest element j and
@@ -49,7 +52,7 @@ __device__ int g_popoff[18];              // first index of each popcount class
 __constant__ int c_binom[17][17];
 
 struct __align__(16) CdetSmemHdr {
-    double log_c[kCorrCap];
+    double log_p[kCorrCap];  // the unshifted pivot (C = sign(p) shift)
     int log_x[kCorrCap];
     int log_l[kCorrCap];
     double red[kCdetThreads / 32];
@@ -109,7 +112,10 @@ __device__ __forceinline__ void bulk_wait_all() {
 
 // max |A_ij| and finiteness of one n x n matrix, on integer bit patterns (the
 // magnitude order of finite doubles is the order of their bits without sign).
-__device__ __forceinline__ void matrix_norm(const double *__restrict__ Ag, int n, CdetSmemHdr &h) {
+// over (if not NULL): the scale to use instead of the matrix's own max (a leaf
+// of a larger matrix takes that matrix's ||A||max).
+__device__ __forceinline__ void matrix_norm(const double *__restrict__ Ag, int n, CdetSmemHdr &h,
+                                            const double *over) {
     const int tid = threadIdx.x;
     unsigned long long mx = 0ull;
     int bad = 0;
@@ -132,7 +138,7 @@ __device__ __forceinline__ void matrix_norm(const double *__restrict__ Ag, int n
     if (tid == 0) {
         unsigned long long m = 0ull;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = h.red_u[w] > m ? h.red_u[w] : m;
-        double an = __longlong_as_double(static_cast<long long>(m));
+        double an = over ? *over : __longlong_as_double(static_cast<long long>(m));
         h.anorm = an > 0.0 ? an : 1.0;
     }
     __syncthreads();
@@ -145,14 +151,13 @@ __device__ __forceinline__ void node_pivot(int x, int lev, double &v, double *MA
                                            double shift, CdetSmemHdr &h) {
     double piv = v;
     if (fabs(piv) <= thr) {
-        const double cs = piv >= 0.0 ? shift : -shift;
-        piv += cs;
         const int slot = atomicAdd(&h.ncorr, 1);
         if (slot < kCorrCap) {
             h.log_x[slot] = x;
             h.log_l[slot] = lev;
-            h.log_c[slot] = cs;
+            h.log_p[slot] = piv;
         }
+        piv += piv >= 0.0 ? shift : -shift;
     }
     MA[x | (1 << lev)] = MA[x] * piv;
     v = 1.0 / piv;
@@ -287,12 +292,13 @@ __device__ __forceinline__ void fpm_tree(const double *__restrict__ Ag, int n, d
     }
     for (int ci = nc - 1; ci >= 0; --ci) {
         const int x = h.log_x[ci], lv = h.log_l[ci];
-        const double cs = h.log_c[ci];
+        const double pv = h.log_p[ci];
+        const double cs = pv >= 0.0 ? shift : -shift;
         const int cnt = 1 << (n - lv - 1);
         for (int t = tid; t < cnt; t += T) {
             const int src = x | (t << (lv + 1));
             const int tgt = src | (1 << lv);
-            MA[tgt] = fma(-cs, MA[src], MA[tgt]);
+            MA[tgt] = t == 0 ? MA[src] * pv : fma(-cs, MA[src], MA[tgt]);
         }
         __syncthreads();
     }
@@ -436,7 +442,7 @@ __device__ __forceinline__ void cdet_item(const CdetArgs &p, int n, const double
                                           const double *ain, double *mo, double *co, uint32_t *st,
                                           double *MA, double *MC, double *MU, bool in_smem,
                                           unsigned long long gsel, unsigned long long gsel_b, double *blk,
-                                          CdetSmemHdr &h) {
+                                          CdetSmemHdr &h, const double *anorm_over) {
     const int tid = threadIdx.x;
     const int N = 1 << n;
     if (tid == 0) bulk_wait_read();  // the previous item's bulk stores have read their source
@@ -450,13 +456,13 @@ __device__ __forceinline__ void cdet_item(const CdetArgs &p, int n, const double
         __syncthreads();
     } else {
         if (p.two_mats) {
-            matrix_norm(Ad, n, h);
+            matrix_norm(Ad, n, h, anorm_over);
             fpm_tree(Ad, n, MA, MC, p.piv_thr * h.anorm, p.piv_shift * h.anorm, h);
             for (int t = tid; t < N; t += blockDim.x) MU[t] = MA[t];
             if (tid == 0) h.ncorr = 0;
             __syncthreads();
         }
-        matrix_norm(Au, n, h);
+        matrix_norm(Au, n, h, anorm_over);
         fpm_tree(Au, n, MA, MC, p.piv_thr * h.anorm, p.piv_shift * h.anorm, h);
         if (mo) {
             if (in_smem) {
@@ -520,7 +526,7 @@ __global__ void __launch_bounds__(kCdetThreads, 3) fpm_cdet_kernel(const CdetKer
                   p.a_in ? p.a_in + b * N : nullptr,
                   p.minors_out ? p.minors_out + b * (p.two_mats ? 2 * N : N) : nullptr,
                   p.c_out ? p.c_out + b * N : nullptr, p.status ? p.status + b : nullptr, MA, MC, MU,
-                  kSmemArrays, P.gsel, P.gsel_b, sbase, h);
+                  kSmemArrays, P.gsel, P.gsel_b, sbase, h, p.anorm_in ? p.anorm_in + (b >> p.anorm_shift) : nullptr);
     }
     if (threadIdx.x == 0) bulk_wait_all();
 }
@@ -559,7 +565,7 @@ __global__ void __launch_bounds__(kCdetThreads, 3) fpm_cdet_varlen_kernel(const 
                   p.a_in ? p.a_in + co : nullptr,
                   p.minors_out ? p.minors_out + (p.two_mats ? 2 * co : co) : nullptr,
                   p.c_out ? p.c_out + co : nullptr, p.status ? p.status + b : nullptr, MA, MC, MU, in_smem,
-                  gsel_s[n], gsel_s[kBlkB], sbase, h);
+                  gsel_s[n], gsel_s[kBlkB], sbase, h, nullptr);
     }
     if (threadIdx.x == 0) bulk_wait_all();
 }

@@ -60,19 +60,50 @@ def test_hubbard_matrices_n19(apm):
 @pytest.mark.parametrize("n", [17, 19])
 def test_upper_and_leaf_pivot_corrections(apm, n):
     """A zero diagonal corrects the first pivot of the upper levels and of the
-    leaves; a threshold of 0.7 ||A||max corrects most of the upper ones, nested.
-    The zero-diagonal case is held to 1e-9: the tree divides by its pivots with
-    no row exchange (Section II), and on such a matrix the pivots just above the
-    threshold amplify rounding by about ||A|| / |p|, which depends on the order in
-    which the elements are decided (the leaves' kernel decides them from the
-    last one, the fused kernel from the first)."""
+    leaves; a threshold of 0.7 ||A||max corrects most of the upper ones, nested."""
     rng = np.random.default_rng(7200 + n)
     A = rng.standard_normal((2, n, n))
     for b in range(2):
         np.fill_diagonal(A[b], 0.0)
-    check_full(apm, A, expect_corrected=True, tol=1e-9)
+    check_full(apm, A, expect_corrected=True)
     B = rng.standard_normal((2, n, n))
     check_full(apm, B, expect_corrected=True, piv_threshold=0.7)
+
+
+def small_pivot_matrices(n, deltas, seed):
+    """N(0,1) + 2I matrices whose tree meets pivots of about delta ||A||max: the
+    first pivot of either elimination order (A_00 and A_{n-1,n-1}), and the
+    pivot of element c once element a is kept, for four pairs (a, c) in both
+    orders: A_cc = A_ca A_ac / A_aa + delta ||A||max makes the 2 x 2 minor of
+    {a, c} equal to A_aa delta ||A||max."""
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((len(deltas), n, n)) + 2 * np.eye(n)
+    for b, d in enumerate(deltas):
+        amax = np.abs(A[b]).max()
+        A[b, 0, 0] = 1.3 * d * amax
+        A[b, n - 1, n - 1] = 0.7 * d * amax
+        for a, c in [(1, 3), (2, 6), (n - 2, n - 5), (n - 3, 4)]:
+            A[b, c, c] = A[b, c, a] * A[b, a, c] / A[b, a, a] + d * amax * (1 + 0.1 * a)
+    return A
+
+
+@pytest.mark.parametrize("n", [12, 17])
+def test_pivots_between_1e6_and_1e3_of_the_norm(apm, n):
+    """Pivots of 1e-6 .. 1e-3 ||A||max on both sides of the default threshold
+    (1e-4): the ones below are shifted, the ones above are divided by, and every
+    minor stays within 1e-10 of the row-sum bound (at n = 12 also through the
+    fused minors + connected-sum kernel, against the Leibniz scale)."""
+    A = small_pivot_matrices(n, [1e-6, 1e-5, 1e-4, 1e-3], 7800 + n)
+    check_full(apm, A)
+    if n <= 16:
+        c, mo = apm.cdet_connected(dev(A), return_minors=True)
+        ref = oracle.minors_lu(A)
+        sc = oracle.minors_scale(A)
+        assert np.max(np.abs(mo.cpu().numpy() - ref) / sc) <= TOL
+        cref = oracle.cdet_recursion(ref * ref)
+        csc = oracle.cdet_scale(sc * sc)
+        assert np.all(c.cpu().numpy()[:, 0] == 0.0)
+        assert np.max(np.abs(c.cpu().numpy() - cref)[:, 1:] / csc[:, 1:]) <= TOL
 
 
 def test_order_24_sampled(apm):
