@@ -542,14 +542,13 @@ int launch_keldysh(const double *Mt, int n, int64_t batch, int sgn, double *sum,
 // ---------------------------------------------------------------------------
 
 constexpr int kKelNoAllocMaxN = 14;
-constexpr int kKelNoAllocWarps = 608;
-constexpr int kKelNoAllocBlocks = kKelNoAllocWarps / kKelWarps;
+constexpr int kKelNoAllocBlocks = 50;
+constexpr int kKelNoAllocWarps = kKelNoAllocBlocks * kKelWarps;
 constexpr size_t kKelNoAllocStack = kel_stack_entries(kKelNoAllocMaxN);
-static_assert(kKelNoAllocStack <= 2912, "stack size of order 14");
+static_assert(kKelNoAllocWarps == 600 && kKelNoAllocStack == 2716, "600 warp slots of an order-14 stack");
 
-// 608 warps x at most 2912 complex entries x 16 B = 28.3 MB per device.
-static __device__ __align__(256) double2 g_kel_noalloc_stack[kKelNoAllocBlocks * kKelWarps *
-                                                            kKelNoAllocStack];
+// 600 warps x 2716 complex entries x 16 B = 26.1 MB per device.
+static __device__ __align__(256) double2 g_kel_noalloc_stack[kKelNoAllocWarps * kKelNoAllocStack];
 
 }  // namespace apm
 
@@ -570,25 +569,28 @@ extern "C" apm_status_t apm_keldysh_sum_noalloc(const double *Mt, int n, int64_t
     auto bad_ptr = [](const void *q) { return (reinterpret_cast<uintptr_t>(q) & 15u) != 0; };
     if (batch > 0 && (!Mt || !sum || bad_ptr(Mt) || bad_ptr(sum))) return APM_ERR_ARG;
     if ((partial && bad_ptr(partial)) || (status && bad_ptr(status))) return APM_ERR_ARG;
-    if (batch == 0) return APM_OK;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return APM_ERR_CUDA;
+    const size_t smem = kKelWarps * sizeof(KelWarpSmem);
     void *scratch = nullptr;
     {
-        // first call on this device: resolve the device address of the array
-        // (a host-side name of a __device__ array is not a device address)
+        // first call on this device, even with batch 0: resolve the device
+        // address of the array (a host-side name of a __device__ array is not a
+        // device address; the lookup also loads the module, and with it the
+        // array, if lazy loading has not done so yet) and allow the kernel its
+        // shared memory
         std::lock_guard<std::mutex> lk(g_noalloc_mu);
         if (!g_noalloc_addr[dev]) {
             void *q = nullptr;
             if (cudaGetSymbolAddress(&q, g_kel_noalloc_stack) != cudaSuccess || !q) return APM_ERR_CUDA;
+            if (cudaFuncSetAttribute(keldysh_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     static_cast<int>(smem)) != cudaSuccess)
+                return APM_ERR_CUDA;
             g_noalloc_addr[dev] = q;
         }
         scratch = g_noalloc_addr[dev];
     }
-    const size_t smem = kKelWarps * sizeof(KelWarpSmem);
-    if (cudaFuncSetAttribute(keldysh_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(smem)) != cudaSuccess)
-        return APM_ERR_CUDA;
+    if (batch == 0) return APM_OK;
     const int64_t need = (batch + kKelWarps - 1) / kKelWarps;
     const int grid = static_cast<int>(need < kKelNoAllocBlocks ? need : kKelNoAllocBlocks);
     keldysh_kernel<<<grid, kKelWarps * 32, smem, reinterpret_cast<cudaStream_t>(stream)>>>(
