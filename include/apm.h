@@ -461,6 +461,25 @@ apm_status_t apm_keldysh_sum_varlen(const double *Mt, const int64_t *m_off, cons
 apm_status_t apm_cdet_tune_set(const uint64_t *table);
 apm_status_t apm_cdet_tune_get(int n, uint64_t *packed);
 
+/*
+ * apm_tune_options_set -- the other knobs an autotuner sets (no counterpart in
+ * the paper; process-wide, for every device):
+ *   fsc_from_n        orders >= this take their connected sums through the fast
+ *                     subset convolution instead of the recursion, in
+ *                     apm_cdet_connected and apm_cdet_connected_varlen: 13..16,
+ *                     17 for never, 0 for the default 16.
+ *   cdet_ctas_per_sm  resident CTAs per SM of the persistent uneven-batch kernel
+ *                     of apm_cdet_connected_varlen: 1..3, 0 for as many as fit (3).
+ *   keldysh_warps     warps per CTA of apm_keldysh_sum_varlen: 4..12, 0 for 12
+ *                     (fewer warps per CTA let more CTAs share an SM).
+ * Workspace sizes depend on the first two: query apm_workspace_size after
+ * setting them (a smaller workspace than the options need is rejected with
+ * APM_ERR_WORKSPACE). Results differ between hand-off orders by rounding only.
+ * Returns APM_ERR_ARG for values out of range (nothing is changed then).
+ */
+apm_status_t apm_tune_options_set(int fsc_from_n, int cdet_ctas_per_sm, int keldysh_warps);
+apm_status_t apm_tune_options_get(int *fsc_from_n, int *cdet_ctas_per_sm, int *keldysh_warps);
+
 /* ------------------------------------------------------------------------
  * Learned Monte Carlo proposal (no counterpart in the paper: the paper's
  * Monte Carlo context is the power series of Section V, Eq. series, sampled

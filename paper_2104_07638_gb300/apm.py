@@ -80,6 +80,8 @@ def lib():
                 "apm_status_reduce": [P, i64, ctypes.POINTER(ctypes.c_uint32), P],
                 "apm_fp64_fma_probe": [P, i32, i32, i32, P],
                 "apm_order_sums": [P, i32, P, P, i64, i32, P, P],
+                "apm_tune_options_set": [i32, i32, i32],
+                "apm_tune_options_get": [P, P, P],
             }
             for name, args in sig.items():
                 f = getattr(L, name)
@@ -561,6 +563,20 @@ def tune_get(n: int) -> int:
     out = ctypes.c_uint64(0)
     _check(lib().apm_cdet_tune_get(n, ctypes.byref(out)), "apm_cdet_tune_get")
     return int(out.value)
+
+
+def tune_options_set(fsc_from_n: int = 0, cdet_ctas_per_sm: int = 0, keldysh_warps: int = 0):
+    """apm_tune_options_set: the order from which connected sums take the fast
+    subset convolution (13..16, 17 never, 0 default), the resident CTAs per SM
+    of the uneven connected-sum batch (1..3, 0 all), and the warps per CTA of
+    the uneven Keldysh batch (4..12, 0 default)."""
+    _check(lib().apm_tune_options_set(fsc_from_n, cdet_ctas_per_sm, keldysh_warps), "apm_tune_options_set")
+
+
+def tune_options_get() -> tuple[int, int, int]:
+    a, b, c = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    _check(lib().apm_tune_options_get(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "apm_tune_options_get")
+    return a.value, b.value, c.value
 
 
 def perm_minors(A: torch.Tensor):

@@ -46,7 +46,7 @@ apm_status_t cdet_common(apm::CdetArgs &a, void *workspace, size_t workspace_byt
         const int grid = apm::cdet_grid(a.n, a.batch, two, false, &err);
         if (err) return cuda_fail(err);
         size_t need = static_cast<size_t>(grid) * apm::cdet_slot_doubles(a.n) * sizeof(double);
-        if (a.mode == apm::kModeCdet && a.n >= apm::kFscFromN) {
+        if (a.mode == apm::kModeCdet && a.n >= apm::cdet_fsc_from_n()) {
             const size_t f = apm::fsc_workspace_bytes(a.n, a.batch, &err);
             if (err) return cuda_fail(err);
             if (f > need) need = f;
@@ -464,6 +464,23 @@ apm_status_t apm_keldysh_sum_varlen(const double *Mt, const int64_t *m_off, cons
     return e ? cuda_fail(e) : APM_OK;
 }
 
+apm_status_t apm_tune_options_set(int fsc_from_n, int cdet_ctas_per_sm, int keldysh_warps) {
+    if (fsc_from_n == 0) fsc_from_n = apm::kFscFromN;
+    if (fsc_from_n < apm::kFscMinFrom || fsc_from_n > 17 || cdet_ctas_per_sm < 0 || cdet_ctas_per_sm > 3 ||
+        keldysh_warps < 0 || (keldysh_warps && (keldysh_warps < 4 || keldysh_warps > 12)))
+        return APM_ERR_ARG;
+    apm::cdet_tune_options_set(fsc_from_n, cdet_ctas_per_sm);
+    apm::keldysh_varlen_warps_set(keldysh_warps);
+    return APM_OK;
+}
+
+apm_status_t apm_tune_options_get(int *fsc_from_n, int *cdet_ctas_per_sm, int *keldysh_warps) {
+    if (fsc_from_n) *fsc_from_n = apm::cdet_fsc_from_n();
+    if (cdet_ctas_per_sm) *cdet_ctas_per_sm = apm::cdet_varlen_ctas_per_sm();
+    if (keldysh_warps) *keldysh_warps = apm::keldysh_varlen_warps();
+    return APM_OK;
+}
+
 apm_status_t apm_cdet_tune_set(const uint64_t *table) {
     if (table) {
         for (int n = 0; n <= 16; ++n) {
@@ -510,7 +527,7 @@ apm_status_t apm_workspace_size(int op, int n_max, int64_t batch, int two_mats, 
             const int grid = apm::cdet_grid(n_max, batch, two, false, &err);
             if (err) return cuda_fail(err);
             *bytes = static_cast<size_t>(grid) * apm::cdet_slot_doubles(n_max) * sizeof(double);
-            if (op == APM_OP_CDET && n_max >= apm::kFscFromN) {  // then the ranked arrays
+            if (op == APM_OP_CDET && n_max >= apm::cdet_fsc_from_n()) {  // then the ranked arrays
                 const size_t f = apm::fsc_workspace_bytes(n_max, batch, &err);
                 if (err) return cuda_fail(err);
                 if (f > *bytes) *bytes = f;

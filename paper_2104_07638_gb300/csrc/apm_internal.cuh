@@ -70,8 +70,17 @@ struct CdetArgs {
 };
 
 // Orders whose connected sums apm_cdet_connected and its uneven-batch form take
-// through the fast subset convolution (faster than the recursion from here on).
+// through the fast subset convolution by default (faster than the recursion
+// from here on, as measured); apm_tune_options_set moves the hand-off within
+// kFscMinFrom .. 17 (17: never).
 constexpr int kFscFromN = 16;
+constexpr int kFscMinFrom = 13;
+int cdet_fsc_from_n();
+// tuned knobs of the uneven-batch launches (0: the default)
+int cdet_varlen_ctas_per_sm();
+int keldysh_varlen_warps();
+void keldysh_varlen_warps_set(int w);
+void cdet_tune_options_set(int fsc_from_n, int cdet_ctas_per_sm);
 
 // Launches the fused minors / connected-sum kernel. Returns a cudaError_t.
 int launch_fpm_cdet(const CdetArgs &a, cudaStream_t s);
@@ -139,10 +148,10 @@ int launch_nand(const double *M, int n, int64_t batch, double *out, bool type_su
 int fsc_grid(int n, int64_t batch, int *err);
 size_t fsc_workspace_bytes(int n, int64_t batch, int *err);
 int launch_fsc(const double *a, int n, int64_t batch, double *c, void *workspace, cudaStream_t s);
-// in place on the rows c + c_off[order[i]] (2^n doubles: weights in, connected
-// sums out) for i < *count (a device counter, at most max_items)
-int launch_fsc_items(double *c, const int64_t *c_off, const int *order, const unsigned *count, int64_t max_items,
-                     int n, void *workspace, cudaStream_t s);
+// in place on the rows c + c_off[order[*first + i]] (2^n doubles: weights in,
+// connected sums out) for i < *count (device values, count at most max_items)
+int launch_fsc_items(double *c, const int64_t *c_off, const int *order, const unsigned *first,
+                     const unsigned *count, int64_t max_items, int n, void *workspace, cudaStream_t s);
 
 // uneven batches
 unsigned long long cdet_gsel_packed(int n);
@@ -150,7 +159,11 @@ void cdet_tune_set(const unsigned long long *table);
 size_t cdet_varlen_workspace(int n_max, int64_t batch, bool two_mats, int *err);
 int launch_cdet_varlen(const CdetArgs &a, const int64_t *a_off, const int *n_arr, const int64_t *c_off,
                        int n_max, void *workspace, cudaStream_t s);
-int launch_order(const int *n_arr, int64_t batch, int n_max, int *order, unsigned *ctr, cudaStream_t s);
+// Counting sort by decreasing order into `order`; ctr[0] = 0 (work counter),
+// ctr[1] = the items of orders >= fsc_from_n, and for each order m the first
+// index and the count of its items at ctr[2 + 2m], ctr[3 + 2m].
+int launch_order(const int *n_arr, int64_t batch, int n_max, int *order, unsigned *ctr, cudaStream_t s,
+                 int fsc_from_n = kFscFromN);
 int launch_keldysh_varlen(const double *Mt, const int64_t *m_off, const int *n_arr, int64_t batch, int n_max,
                           int sgn, double *sum, double *partial, uint32_t *status, void *stack,
                           const int *order, unsigned *ctr, cudaStream_t s);

@@ -571,9 +571,10 @@ __global__ void __launch_bounds__(kCdetThreads, 3) fpm_cdet_varlen_kernel(const 
 }
 
 // Longest-first order of an uneven batch: counting sort by decreasing order n
-// (one CTA), and reset of the work counter of the consumer kernel.
+// (one CTA), and reset of the work counter of the consumer kernel; per order m
+// the first index and the count of its items (ctr[2 + 2m], ctr[3 + 2m]).
 __global__ void __launch_bounds__(1024) varlen_order_kernel(const int *__restrict__ n_arr, int64_t batch,
-                                                            int n_max, int *order, unsigned *ctr) {
+                                                            int n_max, int *order, unsigned *ctr, int fsc_from_n) {
     __shared__ int hist[18];
     __shared__ int start[18];
     if (threadIdx.x < 18) hist[threadIdx.x] = 0;
@@ -594,8 +595,12 @@ __global__ void __launch_bounds__(1024) varlen_order_kernel(const int *__restric
         // items of the orders that take the fast subset convolution: the first
         // ones of the longest-first order
         int nf = 0;
-        for (int n = kFscFromN; n <= 16; ++n) nf += hist[n];
+        for (int n = fsc_from_n; n <= 16; ++n) nf += hist[n];
         ctr[1] = static_cast<unsigned>(nf);
+        for (int n = 0; n <= 16; ++n) {
+            ctr[2 + 2 * n] = static_cast<unsigned>(start[n]);
+            ctr[3 + 2 * n] = static_cast<unsigned>(hist[n]);
+        }
     }
     __syncthreads();
     for (int64_t b = threadIdx.x; b < batch; b += blockDim.x) {
@@ -657,6 +662,18 @@ void cdet_group_table(int n, int threads, uint8_t *gsel) {
 
 // Lane-group tables installed by apm_cdet_tune_set (0 = use the cost model).
 static unsigned long long g_tuned[17] = {};
+// Knobs installed by apm_tune_options_set: the order from which the connected
+// sums take the fast subset convolution, and the persistent CTAs per SM of the
+// uneven batch (0: as many as fit).
+static int g_fsc_from_n = kFscFromN;
+static int g_varlen_ctas = 0;
+
+int cdet_fsc_from_n() { return g_fsc_from_n; }
+int cdet_varlen_ctas_per_sm() { return g_varlen_ctas; }
+void cdet_tune_options_set(int fsc_from_n, int cdet_ctas_per_sm) {
+    g_fsc_from_n = fsc_from_n;
+    g_varlen_ctas = cdet_ctas_per_sm;
+}
 
 unsigned long long cdet_gsel_packed(int n) {
     if (n >= 0 && n <= 16 && g_tuned[n]) return g_tuned[n];
@@ -740,8 +757,8 @@ int launch_fpm_cdet(const CdetArgs &a, cudaStream_t s) {
     const int grid = cdet_grid(a.n, a.batch, a.two_mats != 0, smem_arrays, &err);
     if (err) return err;
     const size_t smem = cdet_smem_bytes(a.n, a.two_mats != 0, smem_arrays);
-    const bool fsc = a.mode == kModeCdet && a.n >= kFscFromN;
-    P.a.fsc_from_n = fsc ? kFscFromN : 0;
+    const bool fsc = a.mode == kModeCdet && a.n >= g_fsc_from_n;
+    P.a.fsc_from_n = fsc ? g_fsc_from_n : 0;
     if (smem_arrays)
         fpm_cdet_kernel<true><<<grid, kCdetThreads, smem, s>>>(P);
     else
@@ -775,6 +792,7 @@ int cdet_varlen_grid(bool two_mats, int *err) {
         return 0;
     }
     *err = 0;
+    if (g_varlen_ctas > 0 && g_varlen_ctas < per_sm) per_sm = g_varlen_ctas;
     return sms * per_sm;
 }
 
@@ -785,7 +803,7 @@ size_t cdet_varlen_workspace(int n_max, int64_t batch, bool two_mats, int *err) 
         const int grid = cdet_varlen_grid(two_mats, err);
         if (*err) return 0;
         size_t slots = static_cast<size_t>(grid) * slot_doubles(n_max) * sizeof(double);
-        if (n_max >= kFscFromN) {  // the same region then holds the ranked arrays
+        if (n_max >= g_fsc_from_n) {  // the same region then holds the ranked arrays
             const size_t f = fsc_workspace_bytes(n_max, batch, err);
             if (*err) return 0;
             if (f > slots) slots = f;
@@ -797,8 +815,9 @@ size_t cdet_varlen_workspace(int n_max, int64_t batch, bool two_mats, int *err) 
     return bytes;
 }
 
-int launch_order(const int *n_arr, int64_t batch, int n_max, int *order, unsigned *ctr, cudaStream_t s) {
-    varlen_order_kernel<<<1, 1024, 0, s>>>(n_arr, batch, n_max, order, ctr);
+int launch_order(const int *n_arr, int64_t batch, int n_max, int *order, unsigned *ctr, cudaStream_t s,
+                 int fsc_from_n) {
+    varlen_order_kernel<<<1, 1024, 0, s>>>(n_arr, batch, n_max, order, ctr, fsc_from_n);
     return static_cast<int>(cudaGetLastError());
 }
 
@@ -813,7 +832,8 @@ int launch_cdet_varlen(const CdetArgs &a, const int64_t *a_off, const int *n_arr
     unsigned *ctr = reinterpret_cast<unsigned *>(ws);
     int *order = reinterpret_cast<int *>(ws + 256);
     double *slots = reinterpret_cast<double *>(ws + 256 + align256(static_cast<size_t>(a.batch) * sizeof(int)));
-    err = launch_order(n_arr, a.batch, n_max, order, ctr, s);
+    const int fsc_from = g_fsc_from_n;
+    err = launch_order(n_arr, a.batch, n_max, order, ctr, s, fsc_from);
     if (err) return err;
     VarlenParams V;
     V.a = a;
@@ -826,16 +846,18 @@ int launch_cdet_varlen(const CdetArgs &a, const int64_t *a_off, const int *n_arr
     V.smem_max_n = kVarlenSmemMaxN;
     V.n_max = n_max;
     for (int n = 0; n <= 16; ++n) V.gsel[n] = cdet_gsel_packed(n);
-    static_assert(kFscFromN == 16, "the item launch below takes the one order 16");
-    const bool fsc = a.mode == kModeCdet && n_max >= kFscFromN;
-    V.a.fsc_from_n = fsc ? kFscFromN : 0;
+    const bool fsc = a.mode == kModeCdet && n_max >= fsc_from;
+    V.a.fsc_from_n = fsc ? fsc_from : 0;
     const int64_t g = a.batch < grid ? a.batch : grid;
     fpm_cdet_varlen_kernel<<<static_cast<int>(g), kCdetThreads, cdet_smem_bytes(kVarlenSmemMaxN, two, true), s>>>(V);
     err = static_cast<int>(cudaGetLastError());
     if (err || !fsc) return err;
-    // the longest-first prefix of n >= kFscFromN items (counted by the order
-    // kernel), in place on their output rows
-    return launch_fsc_items(a.c_out, c_off, order, ctr + 1, a.batch, kFscFromN, slots, s);
+    // the items of the orders >= fsc_from (the longest-first prefix), one launch
+    // per order from its first index and count as the order kernel left them,
+    // in place on their output rows
+    for (int m = n_max; m >= fsc_from && !err; --m)
+        err = launch_fsc_items(a.c_out, c_off, order, ctr + 2 + 2 * m, ctr + 3 + 2 * m, a.batch, m, slots, s);
+    return err;
 }
 
 }  // namespace apm

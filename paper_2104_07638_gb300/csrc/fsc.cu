@@ -171,11 +171,11 @@ __device__ __forceinline__ void fsc_log(double *T, int nx, int n, const uint16_t
 }
 
 // Rows: a + b 2^n -> c + b 2^n for b < batch, or, with `order`, in place on the
-// rows c + c_off[order[i]] for i < *count (a may equal c: every row is read in
-// pass A before pass C writes it).
+// rows c + c_off[order[*first + i]] for i < *count (a may equal c: every row is
+// read in pass A before pass C writes it).
 __global__ void __launch_bounds__(kFscThreads, 3) fsc_kernel(const double *a, int n, int64_t batch, double *c,
                                                               double *ws, const int *order, const int64_t *c_off,
-                                                              const unsigned *count) {
+                                                              const unsigned *first, const unsigned *count) {
     extern __shared__ __align__(16) double T[];
     __shared__ uint16_t s_order[kFscTile];  // tile entries by (popcount, value)
     __shared__ double s_inv[kFscMaxN + 1];  // 1/k
@@ -204,8 +204,9 @@ __global__ void __launch_bounds__(kFscThreads, 3) fsc_kernel(const double *a, in
     }
     __syncthreads();
     const int64_t items = order ? static_cast<int64_t>(*count) : batch;
-    auto row_in = [&](int64_t i) { return order ? c + c_off[order[i]] : a + i * N; };
-    auto row_out = [&](int64_t i) { return order ? c + c_off[order[i]] : c + i * N; };
+    const int64_t i0 = order ? static_cast<int64_t>(*first) : 0;
+    auto row_in = [&](int64_t i) { return order ? c + c_off[order[i0 + i]] : a + i * N; };
+    auto row_out = [&](int64_t i) { return order ? c + c_off[order[i0 + i]] : c + i * N; };
     if (n <= kFscTileBits) {
         for (int64_t b = blockIdx.x; b < items; b += gridDim.x) {
             const double *ab = row_in(b);
@@ -319,17 +320,17 @@ int launch_fsc(const double *a, int n, int64_t batch, double *c, void *workspace
     const int grid = fsc_grid(n, batch, &err);
     if (err) return err;
     fsc_kernel<<<grid, kFscThreads, fsc_smem(n), s>>>(a, n, batch, c, static_cast<double *>(workspace), nullptr,
-                                                      nullptr, nullptr);
+                                                      nullptr, nullptr, nullptr);
     return static_cast<int>(cudaGetLastError());
 }
 
-int launch_fsc_items(double *c, const int64_t *c_off, const int *order, const unsigned *count, int64_t max_items,
-                     int n, void *workspace, cudaStream_t s) {
+int launch_fsc_items(double *c, const int64_t *c_off, const int *order, const unsigned *first,
+                     const unsigned *count, int64_t max_items, int n, void *workspace, cudaStream_t s) {
     int err = 0;
     const int grid = fsc_grid(n, max_items, &err);
     if (err) return err;
     fsc_kernel<<<grid, kFscThreads, fsc_smem(n), s>>>(c, n, max_items, c, static_cast<double *>(workspace), order,
-                                                      c_off, count);
+                                                      c_off, first, count);
     return static_cast<int>(cudaGetLastError());
 }
 

@@ -398,7 +398,9 @@ __global__ void __launch_bounds__(kKelWarps * 32, kKelMinBlocks) keldysh_kernel(
 }
 
 // Uneven batch: warps take matrices longest-first from `order` through a
-// global counter. partial rows have 17 complex entries per matrix.
+// global counter. partial rows have 17 complex entries per matrix. The CTA has
+// blockDim.x / 32 warps (at most kKelWarps: a tuned launch may take fewer, and
+// then more CTAs fit on an SM).
 __global__ void __launch_bounds__(kKelWarps * 32, kKelMinBlocks) keldysh_varlen_kernel(
     const double2 *__restrict__ Mt, const int64_t *__restrict__ m_off, const int *__restrict__ n_arr,
     int64_t batch, int n_max, int sgn_flag, double *sum, double *partial, uint32_t *status,
@@ -406,7 +408,7 @@ __global__ void __launch_bounds__(kKelWarps * 32, kKelMinBlocks) keldysh_varlen_
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     KelWarpSmem &w = reinterpret_cast<KelWarpSmem *>(smem_raw)[wid];
-    const int64_t gw = static_cast<int64_t>(blockIdx.x) * kKelWarps + wid;
+    const int64_t gw = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + wid;
     double2 *stack = stack_base ? stack_base + gw * stack_per_warp : nullptr;
     while (true) {
         int item = 0;
@@ -429,14 +431,33 @@ __global__ void __launch_bounds__(kKelWarps * 32, kKelMinBlocks) keldysh_varlen_
     }
 }
 
+// Warps per CTA of the uneven-batch launch (apm_tune_options_set; 0: kKelWarps).
+static int g_kel_varlen_warps = 0;
+int keldysh_varlen_warps() { return g_kel_varlen_warps; }
+void keldysh_varlen_warps_set(int w) { g_kel_varlen_warps = w; }
+
 int launch_keldysh_varlen(const double *Mt, const int64_t *m_off, const int *n_arr, int64_t batch, int n_max,
                           int sgn, double *sum, double *partial, uint32_t *status, void *stack,
                           const int *order, unsigned *ctr, cudaStream_t s) {
     int err = 0;
-    const int grid = keldysh_grid(batch, &err);
+    // the workspace holds a stack for every warp of the default launch
+    // (keldysh_grid(batch) CTAs of kKelWarps warps, as apm_workspace_size sizes it)
+    const int full = keldysh_grid(batch, &err);
     if (err) return err;
-    const size_t smem = kKelWarps * sizeof(KelWarpSmem);
-    keldysh_varlen_kernel<<<grid, kKelWarps * 32, smem, s>>>(
+    const int warps = g_kel_varlen_warps > 0 ? g_kel_varlen_warps : kKelWarps;
+    const size_t smem = static_cast<size_t>(warps) * sizeof(KelWarpSmem);
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, keldysh_varlen_kernel, warps * 32, smem);
+    if (e != cudaSuccess || per_sm < 1) return e != cudaSuccess ? static_cast<int>(e) : 1;
+    int64_t grid = static_cast<int64_t>(sms) * per_sm;
+    const int64_t slots = static_cast<int64_t>(full) * kKelWarps;  // stacks in the workspace
+    if (grid * warps > slots) grid = slots / warps;
+    const int64_t need = (batch + warps - 1) / warps;
+    if (grid > need) grid = need;
+    keldysh_varlen_kernel<<<static_cast<int>(grid < 1 ? 1 : grid), warps * 32, smem, s>>>(
         reinterpret_cast<const double2 *>(Mt), m_off, n_arr, batch, n_max, sgn, sum, partial, status,
         static_cast<double2 *>(stack), kel_stack_entries(n_max), order, ctr);
     return static_cast<int>(cudaGetLastError());

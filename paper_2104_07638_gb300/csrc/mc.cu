@@ -246,6 +246,31 @@ apm_status_t apm_mlp_train_step(const apm_mlp *net, const uint16_t *X, const flo
                : APM_OK;
 }
 
+apm_status_t apm_mlp_gradient(const apm_mlp *net, const uint16_t *X, const float *target, int batch_padded,
+                              int batch_valid, float *loss_acc, void *workspace, size_t workspace_bytes,
+                              apm_stream_t stream) {
+    if (!net || !net->param || !net->param_bf16 || !net->grad) return APM_ERR_ARG;
+    if (batch_padded <= 0 || batch_padded % 64 || batch_valid < 1 || batch_valid > batch_padded) return APM_ERR_ARG;
+    if (!X || !target || !loss_acc) return APM_ERR_ARG;
+    if (!workspace || workspace_bytes < mlp_workspace_bytes(batch_padded)) return APM_ERR_WORKSPACE;
+    MlpParams P;
+    mlp_bind(net, P);
+    MlpWork w;
+    mlp_work(workspace, batch_padded, w);
+    return mlp_gradient(P, reinterpret_cast<const __nv_bfloat16 *>(X), target, batch_padded, batch_valid, w,
+                        loss_acc, reinterpret_cast<cudaStream_t>(stream))
+               ? APM_ERR_CUDA
+               : APM_OK;
+}
+
+apm_status_t apm_mlp_adam_step(const apm_mlp *net, float lr, int step, apm_stream_t stream) {
+    if (!net || !net->param || !net->param_bf16 || !net->grad || !net->adam_m || !net->adam_v || step < 1)
+        return APM_ERR_ARG;
+    MlpParams P;
+    mlp_bind(net, P);
+    return mlp_adam(P, lr, step, reinterpret_cast<cudaStream_t>(stream)) ? APM_ERR_CUDA : APM_OK;
+}
+
 apm_status_t apm_mlp_status(void *workspace, size_t workspace_bytes, uint32_t *flags, apm_stream_t stream) {
     if (!workspace || workspace_bytes < mlp_workspace_bytes(0)) return APM_ERR_WORKSPACE;
     uint32_t v = 0;

@@ -44,24 +44,34 @@ __global__ void head_forward_kernel(const __nv_bfloat16 *__restrict__ H, const _
 
 // dy = 2 (y - target) / B_valid for rows < B_valid (0 for padding rows); loss partial sums
 __global__ void mse_grad_kernel(const float *__restrict__ y, const float *__restrict__ target, float *dy,
-                                int Bp, int B_valid, float *loss_acc) {
+                                int Bp, int B_valid, float *loss_part) {
+    // dy = 2 (y - t) / B_valid on the valid rows; the block's share of the loss
+    // into loss_part[block] (added in a fixed order later: deterministic)
+    __shared__ float red[256];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= Bp) return;
-    float d = 0.f;
+    float d = 0.f, l = 0.f;
     if (i < B_valid) {
         const float e = y[i] - target[i];
         d = 2.f * e / static_cast<float>(B_valid);
-        atomicAdd(loss_acc, e * e / static_cast<float>(B_valid));
+        l = e * e / static_cast<float>(B_valid);
     }
-    dy[i] = d;
+    if (i < Bp) dy[i] = d;
+    red[threadIdx.x] = l;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) loss_part[blockIdx.x] = red[0];
 }
 
 // head backward: dZ[b][i] = (H[b][i] > 0) ? dy[b] * w[i] : 0 (fp32 and bf16);
-// dw[i] += sum_b dy[b] H[b][i]; db += sum_b dy[b]; dbz[i] += sum_b dZ[b][i]
-// (atomic partial sums per block of rows)
+// per block of rows the partial sums of dw[i] = sum_b dy[b] H[b][i],
+// dbz[i] = sum_b dZ[b][i] and db = sum_b dy[b] (added over the blocks in a
+// fixed order by col_sum_kernel: no atomics, so training is deterministic)
 __global__ void head_backward_kernel(const __nv_bfloat16 *__restrict__ H, const __nv_bfloat16 *__restrict__ w,
-                                     const float *__restrict__ dy, float *dZ32, __nv_bfloat16 *dZb, float *dw,
-                                     float *db, float *dbz, int Bp, int D, int rows_per_block) {
+                                     const float *__restrict__ dy, float *dZ32, __nv_bfloat16 *dZb, float *pw,
+                                     float *pb, float *pz, int Bp, int D, int rows_per_block) {
     const int i = threadIdx.x;  // column, blockDim.x == D
     const int r0 = blockIdx.x * rows_per_block;
     float accw = 0.f, accb = 0.f, accz = 0.f;
@@ -76,14 +86,15 @@ __global__ void head_backward_kernel(const __nv_bfloat16 *__restrict__ H, const 
         accb += g;
         accz += z;
     }
-    atomicAdd(&dw[i], accw);
-    atomicAdd(&dbz[i], accz);
-    if (i == 0) atomicAdd(db, accb);
+    pw[static_cast<size_t>(blockIdx.x) * D + i] = accw;
+    pz[static_cast<size_t>(blockIdx.x) * D + i] = accz;
+    if (i == 0) pb[blockIdx.x] = accb;
 }
 
-// dZ = dH * (H > 0) (fp32 in, fp32 + bf16 out) and column sums into db
+// dZ = dH * (H > 0) (fp32 in, fp32 + bf16 out); per block of rows the partial
+// column sums (the bias gradient) into pdb[block][i]
 __global__ void relu_backward_kernel(const float *__restrict__ dH, const __nv_bfloat16 *__restrict__ H,
-                                     float *dZ32, __nv_bfloat16 *dZb, float *db, int Bp, int D,
+                                     float *dZ32, __nv_bfloat16 *dZb, float *pdb, int Bp, int D,
                                      int rows_per_block) {
     const int i = threadIdx.x;
     const int r0 = blockIdx.x * rows_per_block;
@@ -95,7 +106,16 @@ __global__ void relu_backward_kernel(const float *__restrict__ dH, const __nv_bf
         dZb[o] = __float2bfloat16_rn(z);
         acc += z;
     }
-    atomicAdd(&db[i], acc);
+    pdb[static_cast<size_t>(blockIdx.x) * D + i] = acc;
+}
+
+// out[i] (+)= sum over the blocks k = 0 .. nblk-1, in that order, of part[k][i]
+__global__ void col_sum_kernel(const float *__restrict__ part, float *out, int nblk, int D, int accumulate) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= D) return;
+    float acc = 0.f;
+    for (int k = 0; k < nblk; ++k) acc += part[static_cast<size_t>(k) * D + i];
+    out[i] = accumulate ? out[i] + acc : acc;
 }
 
 // Adam on the flat fp32 parameter vector; refreshes the bf16 copy
@@ -124,11 +144,16 @@ __global__ void f32_to_bf16_kernel(const float *in, __nv_bfloat16 *out, int coun
 
 static size_t al(size_t x) { return (x + 255) & ~size_t(255); }
 
-// layout: status word (offset 0), split-K partials, activations and gradients
+constexpr int kMlpRowsPerBlock = 64;  // rows per block of the backward column sums
+
+// layout: status word (offset 0), split-K partials, activations and gradients,
+// per-block partial column sums of the backward pass
 size_t mlp_workspace_bytes(int Bp) {
     const size_t act = static_cast<size_t>(Bp) * kMlpH;
+    const size_t nblk = static_cast<size_t>(Bp + kMlpRowsPerBlock - 1) / kMlpRowsPerBlock + 1;
     return al(sizeof(uint32_t)) + al(tc_gemm_split_floats() * 4) + 3 * al(act * 2) + 2 * al(static_cast<size_t>(Bp) * 4) + 2 * al(act * 4) + al(act * 2) +
-           2 * al(act * 2) + al(static_cast<size_t>(kMlpH) * kMlpH * 2);
+           2 * al(act * 2) + al(static_cast<size_t>(kMlpH) * kMlpH * 2) + 2 * al(nblk * kMlpH * 4) +
+           2 * al(static_cast<size_t>(Bp / 256 + 1 > nblk ? Bp / 256 + 1 : nblk) * 4);
 }
 
 void mlp_work(void *ws, int Bp, MlpWork &w) {
@@ -152,6 +177,12 @@ void mlp_work(void *ws, int Bp, MlpWork &w) {
     w.t1 = reinterpret_cast<__nv_bfloat16 *>(take(act * 2));
     w.t2 = reinterpret_cast<__nv_bfloat16 *>(take(act * 2));
     w.wt = reinterpret_cast<__nv_bfloat16 *>(take(static_cast<size_t>(kMlpH) * kMlpH * 2));
+    const size_t nblk = static_cast<size_t>(Bp + kMlpRowsPerBlock - 1) / kMlpRowsPerBlock + 1;
+    const size_t np = static_cast<size_t>(Bp / 256 + 1 > nblk ? Bp / 256 + 1 : nblk);
+    w.pcol = reinterpret_cast<float *>(take(nblk * kMlpH * 4));
+    w.pcol2 = reinterpret_cast<float *>(take(nblk * kMlpH * 4));
+    w.pvec = reinterpret_cast<float *>(take(np * 4));
+    w.pvec2 = reinterpret_cast<float *>(take(np * 4));
 }
 
 void mlp_bind(const apm_mlp *net, MlpParams &P) {
@@ -190,19 +221,27 @@ int mlp_forward(const MlpParams &P, const __nv_bfloat16 *X, int Bp, float *y, Ml
     return static_cast<int>(cudaGetLastError());
 }
 
-int mlp_train_step(MlpParams &P, const __nv_bfloat16 *X, const float *target, int Bp, int B_valid, MlpWork &w,
-                   float lr, int step, float *loss_acc, cudaStream_t s) {
+// The gradient of the mean squared error over the first B_valid rows into
+// P.grad (forward pass, then backpropagation layer by layer).
+int mlp_gradient(MlpParams &P, const __nv_bfloat16 *X, const float *target, int Bp, int B_valid, MlpWork &w,
+                 float *loss_acc, cudaStream_t s) {
     int e;
     if ((e = mlp_forward(P, X, Bp, w.y, w, s))) return e;
     cudaMemsetAsync(P.grad, 0, sizeof(float) * kMlpParams, s);
-    mse_grad_kernel<<<(Bp + 255) / 256, 256, 0, s>>>(w.y, target, w.dy, Bp, B_valid, loss_acc);
-    const int rpb = 64;
+    const int nl = (Bp + 255) / 256;
+    mse_grad_kernel<<<nl, 256, 0, s>>>(w.y, target, w.dy, Bp, B_valid, w.pvec2);
+    col_sum_kernel<<<1, 32, 0, s>>>(w.pvec2, loss_acc, nl, 1, 1);
+    const int rpb = kMlpRowsPerBlock;
+    const int nblk = (Bp + rpb - 1) / rpb;
     float *g = P.grad;
     float *gw1 = g + kOffW1, *gb1 = g + kOffB1, *gw2 = g + kOffW2, *gb2 = g + kOffB2;
     float *gw3 = g + kOffW3, *gb3 = g + kOffB3, *gw4 = g + kOffW4, *gb4 = g + kOffB4;
     // head: dZ3 = dH3 * (H3 > 0), dw4, db4, db3 = column sums of dZ3
-    head_backward_kernel<<<(Bp + rpb - 1) / rpb, kMlpH, 0, s>>>(w.h3, P.w4b, w.dy, w.dz32, w.dzb, gw4, gb4, gb3,
-                                                                Bp, kMlpH, rpb);
+    head_backward_kernel<<<nblk, kMlpH, 0, s>>>(w.h3, P.w4b, w.dy, w.dz32, w.dzb, w.pcol, w.pvec, w.pcol2, Bp,
+                                                kMlpH, rpb);
+    col_sum_kernel<<<1, kMlpH, 0, s>>>(w.pcol, gw4, nblk, kMlpH, 0);
+    col_sum_kernel<<<1, kMlpH, 0, s>>>(w.pcol2, gb3, nblk, kMlpH, 0);
+    col_sum_kernel<<<1, 32, 0, s>>>(w.pvec, gb4, nblk, 1, 0);
     // layer 3: dW3 = dZ3^T H2 ; dH2 = dZ3 W3
     if ((e = transpose(w.dzb, w.t1, Bp, kMlpH, s))) return e;  // dZ3^T [256 x Bp]
     if ((e = transpose(w.h2, w.t2, Bp, kMlpH, s))) return e;   // H2^T  [256 x Bp]
@@ -210,23 +249,36 @@ int mlp_train_step(MlpParams &P, const __nv_bfloat16 *X, const float *target, in
     if ((e = transpose(P.w3b, w.wt, kMlpH, kMlpH, s))) return e;  // W3 stored [out x in] -> [in x out]
     if ((e = gemm_tn(w.dzb, w.wt, nullptr, w.dh32, nullptr, Bp, kMlpH, kMlpH, 0, w, s))) return e;
     // layer 2
-    relu_backward_kernel<<<(Bp + rpb - 1) / rpb, kMlpH, 0, s>>>(w.dh32, w.h2, w.dz32, w.dzb, gb2, Bp, kMlpH, rpb);
+    relu_backward_kernel<<<nblk, kMlpH, 0, s>>>(w.dh32, w.h2, w.dz32, w.dzb, w.pcol, Bp, kMlpH, rpb);
+    col_sum_kernel<<<1, kMlpH, 0, s>>>(w.pcol, gb2, nblk, kMlpH, 0);
     if ((e = transpose(w.dzb, w.t1, Bp, kMlpH, s))) return e;  // dZ2^T
     if ((e = transpose(w.h1, w.t2, Bp, kMlpH, s))) return e;   // H1^T
     if ((e = gemm_tn(w.t1, w.t2, nullptr, gw2, nullptr, kMlpH, kMlpH, Bp, 0, w, s))) return e;
     if ((e = transpose(P.w2b, w.wt, kMlpH, kMlpH, s))) return e;
     if ((e = gemm_tn(w.dzb, w.wt, nullptr, w.dh32, nullptr, Bp, kMlpH, kMlpH, 0, w, s))) return e;
     // layer 1
-    relu_backward_kernel<<<(Bp + rpb - 1) / rpb, kMlpH, 0, s>>>(w.dh32, w.h1, w.dz32, w.dzb, gb1, Bp, kMlpH, rpb);
+    relu_backward_kernel<<<nblk, kMlpH, 0, s>>>(w.dh32, w.h1, w.dz32, w.dzb, w.pcol, Bp, kMlpH, rpb);
+    col_sum_kernel<<<1, kMlpH, 0, s>>>(w.pcol, gb1, nblk, kMlpH, 0);
     if ((e = transpose(w.dzb, w.t1, Bp, kMlpH, s))) return e;  // dZ1^T [256 x Bp]
     if ((e = transpose(X, w.t2, Bp, kMlpIn, s))) return e;     // X^T   [64 x Bp]
     if ((e = gemm_tn(w.t1, w.t2, nullptr, gw1, nullptr, kMlpH, kMlpIn, Bp, 0, w, s))) return e;
-    // Adam
+    return static_cast<int>(cudaGetLastError());
+}
+
+// One Adam step from P.grad (step >= 1 for the bias correction); refreshes the
+// BF16 copy of the weights.
+int mlp_adam(MlpParams &P, float lr, int step, cudaStream_t s) {
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
     const float c1 = 1.f - powf(b1, static_cast<float>(step)), c2 = 1.f - powf(b2, static_cast<float>(step));
     adam_kernel<<<(kMlpParams + 255) / 256, 256, 0, s>>>(P.param, P.grad, P.m, P.v, P.pb, kMlpParams, lr, b1, b2,
                                                          eps, c1, c2);
     return static_cast<int>(cudaGetLastError());
+}
+
+int mlp_train_step(MlpParams &P, const __nv_bfloat16 *X, const float *target, int Bp, int B_valid, MlpWork &w,
+                   float lr, int step, float *loss_acc, cudaStream_t s) {
+    const int e = mlp_gradient(P, X, target, Bp, B_valid, w, loss_acc, s);
+    return e ? e : mlp_adam(P, lr, step, s);
 }
 
 int mlp_refresh_bf16(MlpParams &P, cudaStream_t s) {

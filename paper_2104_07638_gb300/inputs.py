@@ -152,6 +152,15 @@ def hubbard_batch(batch: int = 65536, n: int = 12, seed: int = 2) -> np.ndarray:
     return hubbard_matrices_from_vertices(x, y, m)
 
 
+def hubbard_batch_slice(total: int, n: int, seed: int, lo: int, hi: int) -> np.ndarray:
+    """Matrices lo .. hi-1 of the seeded batch hubbard_batch(total, n, seed): the
+    vertices of the whole batch are drawn (a few numbers per matrix), the
+    matrices only for the slice, so that ranks holding contiguous slices hold
+    exactly the one batch between them."""
+    x, y, m = hubbard_vertices(total, n, seed)
+    return hubbard_matrices_from_vertices(x[lo:hi], y[lo:hi], m[lo:hi])
+
+
 def hubbard_varlen(orders: np.ndarray, seed: int = 3):
     """Packed Hubbard matrices of mixed order: returns (flat float64 array,
     int64 element offsets of each matrix)."""

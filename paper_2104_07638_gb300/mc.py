@@ -24,7 +24,7 @@ import time
 import numpy as np
 import torch
 
-from . import apm
+from . import apm, dist
 
 MLP_IN, MLP_PARAMS = 64, 148488
 
@@ -46,6 +46,8 @@ def _sig(L):
         "apm_mlp_sync_bf16": [ctypes.POINTER(ApmMlp), P],
         "apm_mlp_forward": [ctypes.POINTER(ApmMlp), P, i32, P, P, sz, P],
         "apm_mlp_train_step": [ctypes.POINTER(ApmMlp), P, P, i32, i32, ctypes.c_float, i32, P, P, sz, P],
+        "apm_mlp_gradient": [ctypes.POINTER(ApmMlp), P, P, i32, i32, P, P, sz, P],
+        "apm_mlp_adam_step": [ctypes.POINTER(ApmMlp), ctypes.c_float, i32, P],
         "apm_mlp_status": [P, sz, ctypes.POINTER(ctypes.c_uint32), P],
         "apm_mlp_gemm_tn": [P, P, P, P, P, i32, i32, i32, i32, P, sz, P],
     }.items():
@@ -117,25 +119,50 @@ class Surrogate:
         y.mul_(self.y_std).add_(self.y_mean)
 
     def train(self, F_all: torch.Tensor, target: torch.Tensor, epochs=3, batch=4096, lr=1e-3, seed=0):
-        """Adam on normalised targets; F_all [N, 64] bf16 (int16 storage), target [N] float32."""
+        """Adam on normalised targets; F_all [N, 64] bf16 (int16 storage), target [N] float32.
+
+        Under an initialised process group with several processes, each holding
+        its own rows, the training is data-parallel: the target normalisation
+        and the number of batches per epoch are agreed over the processes, and
+        before every Adam step the gradient is averaged over them
+        (dist.average_gradient_), so that every process applies the same step."""
+        _, ws = dist.world()
         N = target.numel()
-        self.y_mean = float(target.mean())
-        self.y_std = float(target.std().clamp_min(1e-6))
+        mom = dist.allreduce_sum_(torch.tensor([float(N), float(target.double().sum()),
+                                                float((target.double() ** 2).sum())], dtype=torch.float64))
+        cnt = float(mom[0])
+        self.y_mean = float(mom[1] / cnt)
+        self.y_std = max(math.sqrt(max(float(mom[2] / cnt) - self.y_mean ** 2, 0.0) * cnt / max(cnt - 1.0, 1.0)),
+                         1e-6)
         t_norm = ((target - self.y_mean) / self.y_std).contiguous()
         batch = pad64(batch)
+        nb = N // batch
+        if ws > 1:   # every process takes the same number of steps
+            nbt = torch.tensor([nb], dtype=torch.int64)
+            import torch.distributed as tdist
+            tdist.all_reduce(nbt, op=tdist.ReduceOp.MIN)
+            nb = int(nbt)
         g = torch.Generator(device="cpu").manual_seed(seed)
         losses = []
         for _ in range(epochs):
             perm = torch.randperm(N, generator=g).to(F_all.device)
-            for s0 in range(0, N - batch + 1, batch):
+            for s0 in range(0, nb * batch, batch):
                 sel = perm[s0:s0 + batch]
                 Fb = F_all[sel].contiguous()
                 tb = t_norm[sel].contiguous()
                 self.step += 1
                 self.loss_acc.zero_()
-                apm._check(lib().apm_mlp_train_step(ctypes.byref(self.net), _p(Fb), _p(tb), batch, batch,
-                                                    ctypes.c_float(lr), self.step, _p(self.loss_acc), _p(self.ws),
-                                                    self.ws.numel(), _s(Fb)), "apm_mlp_train_step")
+                if ws == 1:
+                    apm._check(lib().apm_mlp_train_step(ctypes.byref(self.net), _p(Fb), _p(tb), batch, batch,
+                                                        ctypes.c_float(lr), self.step, _p(self.loss_acc),
+                                                        _p(self.ws), self.ws.numel(), _s(Fb)), "apm_mlp_train_step")
+                else:
+                    apm._check(lib().apm_mlp_gradient(ctypes.byref(self.net), _p(Fb), _p(tb), batch, batch,
+                                                      _p(self.loss_acc), _p(self.ws), self.ws.numel(), _s(Fb)),
+                               "apm_mlp_gradient")
+                    dist.average_gradient_(self.grad, batch)
+                    apm._check(lib().apm_mlp_adam_step(ctypes.byref(self.net), ctypes.c_float(lr), self.step,
+                                                       _s(Fb)), "apm_mlp_adam_step")
                 losses.append(self.loss_acc)
                 self.loss_acc = torch.zeros(1, dtype=torch.float32, device=F_all.device)
         self.check()
@@ -224,8 +251,11 @@ class Walkers:
             record.append(self.observables())
 
     def observables(self):
-        """(sign, log|c|) of every walker, kept on the device."""
-        return torch.stack([self.sign, torch.log(self.weight.clamp_min(1e-300))])
+        """(sign, log|c|, log(|c| / surrogate)) of every walker, kept on the
+        device; the last row is meaningful for the learned chain only (the
+        plain chain keeps no surrogate value)."""
+        lw = torch.log(self.weight.clamp_min(1e-300))
+        return torch.stack([self.sign, lw, lw - self.s_cur.double()])
 
     def collect(self, steps):
         """Plain steps that also return training pairs (features, log|c|) of
@@ -272,7 +302,8 @@ def integrated_autocorr(series: np.ndarray, c: float = 5.0) -> float:
 
 
 def ess(record, which=0) -> float:
-    """Effective sample size of observable `which` (0 sign, 1 log|c|) over all walkers."""
+    """Effective sample size of observable `which` (0 sign, 1 log|c|, 2 log of
+    |c| over the surrogate) over all walkers; NaN if it does not fluctuate."""
     arr = torch.stack([r[which] for r in record]).cpu().numpy()      # (T, W)
     tau = integrated_autocorr(arr)
     if not math.isfinite(tau):
