@@ -37,10 +37,10 @@ SM_MAX_MHZ = 2070.0
 FP64_FLOP_PER_CLK_SM = 4.0   # 1.25 TFLOP/s nominal FP64 / (152 SMs x 2.07 GHz), 2 DFMA/clk/SM
 METRIC = "minor-sets/sec at n=12 FP64 (% of roofline)"
 # DRAM bytes (read + write) per matrix of the fused kernel from one ncu capture
-# of 4096 matrices (211.3 MB), valid only for the kernel source it was taken on
-# (sha256 prefix below).
-TRAFFIC_PER_SET = 210.80e6 / 4096
-TRAFFIC_SRC_SHA = "3c71fac587f4a704"
+# of the benchmark's launch itself (65536 matrices: 79.8 MB read, 4233.3 MB
+# written), valid only for the kernel source it was taken on (sha256 prefix below).
+TRAFFIC_PER_SET = (79764224 + 4233314816) / 65536
+TRAFFIC_SRC_SHA = "fb291277c1e0fe45"
 UNIT = "minor-sets/s"
 
 
@@ -76,6 +76,16 @@ def job_throughput(per_rank_units: int, world: int, steps: int, seconds: float) 
     return world * per_rank_units * steps / seconds
 
 
+def bench_config(n: int, batch: int, world: int) -> dict:
+    """The workload, identical in the GPU and the reference (CPU oracle) arms."""
+    return {"workload": f"hubbard_g0_n{n}_batch{batch}_minors+cdet", "n": n, "batch": batch,
+            "per_rank_batch": batch, "ranks": world,
+            "inputs": "rank r holds matrices r*batch .. (r+1)*batch-1 of one seeded batch (seed 2)",
+            "outputs": "minors[2^n] and c[2^n] per matrix, FP64",
+            "l2": "GPU arm: a 256 MB buffer rewritten between timed steps (outside the events); "
+                  "per step 75.5 MB of inputs and 4.3 GB of outputs"}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -87,10 +97,14 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-rows", action="store_true",
                     help="skip the per-row measurements of the other hot-path steps")
-    ap.add_argument("--mc-steps", type=int, default=100)
+    ap.add_argument("--mc-steps", type=int, default=1000,
+                    help="steps per chain of the learned-proposal row at orders 10..12")
+    ap.add_argument("--mc-steps-high", type=int, default=400,
+                    help="steps per chain of the learned-proposal row at orders 13, 14")
     ap.add_argument("--case", default=None,
-                    choices=["cdet_n12", "cdet_n16", "keldysh_n12", "ppm_n14", "cdet_uneven", "xnor_n12",
-                             "nand_n10", "keldysh2_n12", "mlp_gemm", "fsc_n16", "minors_n12", "minors_n20"],
+                    choices=["cdet_n12", "cdet_n12_full", "cdet_n16", "keldysh_n12", "ppm_n14", "cdet_uneven",
+                             "xnor_n12", "nand_n10", "keldysh2_n12", "mlp_gemm", "fsc_n16", "minors_n12",
+                             "minors_n20", "fp64_probe"],
                     help="run 3 launches of one kernel on a small case (for profiling) and exit")
     return ap.parse_args()
 
@@ -202,10 +216,11 @@ def sc_flops(n: int) -> int:
 FSC_FROM_N = 16  # orders whose connected sums the library takes through the fast subset convolution
 
 
-def cdet_path_flops(n: int) -> int:
+def cdet_path_flops(n: int, fsc_from: int = None) -> int:
     """Algorithmic flops of one minor set as the library computes it: the
-    recursion's count below FSC_FROM_N, the fast subset convolution's from there."""
-    if n < FSC_FROM_N:
+    recursion's count below the hand-off order (FSC_FROM_N by default), the fast
+    subset convolution's from there."""
+    if n < (FSC_FROM_N if fsc_from is None else fsc_from):
         return flops_per_set(n)
     return flops_per_set(n) - sc_flops(n) + fsc_flops(n)
 
@@ -253,21 +268,35 @@ def measure_rows(args, dev, peak):
     from paper_2104_07638_gb300 import apm, inputs, mc
     from paper_2104_07638_gb300.batch import CdetVarlenGraph, KeldyshVarlenGraph
     rows = {}
-    # a7: uneven batch of 131072 walkers, n uniform in 4..16, minors + connected sums, graph replay
+    from paper_2104_07638_gb300 import batch as pbatch
+    # a7: uneven batch of 131072 walkers, n uniform in 4..16, minors + connected sums, graph replay;
+    # first with the default mappings, then with the ones the autotuner finds on this GPU
     orders = inputs.varlen_orders(131072, 4, 16, seed=3)
     flat, off = inputs.hubbard_varlen(orders, seed=3)
     A = torch.as_tensor(flat).to(dev)
     a_off = torch.as_tensor(off).to(dev)
     n_t = torch.as_tensor(orders).to(dev)
+    apm.tune_set(None)
+    apm.tune_options_set(0, 0, 0)
+    g = CdetVarlenGraph(A, a_off, n_t)
+    ms_default = _event_ms(g.replay)
+    del g
+    tuned, t_tune = mc.timed(lambda: pbatch.autotune(use_cache=False))
     g = CdetVarlenGraph(A, a_off, n_t)
     ms = _event_ms(g.replay)
-    fl = sum(cdet_path_flops(int(k)) for k in orders)
+    fsc_from = tuned["fsc_from_n"]
+    fl = sum(cdet_path_flops(int(k), fsc_from) for k in orders)
+    tuned_summary = {"fsc_from_n": fsc_from, "cdet_ctas_per_sm": tuned["cdet_ctas_per_sm"],
+                     "keldysh_warps": tuned["keldysh_warps"],
+                     "lane_groups": {k: f"{v:#x}" for k, v in tuned["lane_groups"].items()},
+                     "tuner_wall_s": t_tune}
     rows["a7_cdet_uneven_131072_n4to16"] = {
-        "value": orders.size / (ms * 1e-3), "unit": "minor-sets/s", "ms": ms,
+        "value": orders.size / (ms * 1e-3), "unit": "minor-sets/s", "ms": ms, "ms_default_mappings": ms_default,
         "tflops": fl / (ms * 1e-3) / 1e12, "frac_fp64_peak": fl / (ms * 1e-3) / 1e12 / peak,
+        "tuned": tuned_summary,
         "launch": "CUDA graph: counting sort by order + one persistent longest-first kernel "
-                  "+ the fast subset convolution of the order-16 rows",
-        "flops": "recursion count below n = 16, fast-subset-convolution count at n = 16"}
+                  "+ the fast subset convolution of the rows of orders >= fsc_from_n",
+        "flops": "recursion count below fsc_from_n, fast-subset-convolution count from it on"}
     del g, A
     # a5 on the same uneven orders: Keldysh sums of 1D-chain real-time G0
     kflat, koff = inputs.keldysh_varlen(orders, seed=3)
@@ -278,7 +307,8 @@ def measure_rows(args, dev, peak):
     fl = sum(keldysh_flops(int(k)) for k in orders)
     rows["a5_keldysh_uneven_131072_n4to16"] = {
         "value": orders.size / (ms * 1e-3), "unit": "sums/s", "ms": ms,
-        "tflops": fl / (ms * 1e-3) / 1e12, "frac_fp64_peak": fl / (ms * 1e-3) / 1e12 / peak}
+        "tflops": fl / (ms * 1e-3) / 1e12, "frac_fp64_peak": fl / (ms * 1e-3) / 1e12 / peak,
+        "warps_per_cta": tuned["keldysh_warps"] or 12, "tuned_by": "the autotuner of the a7 row"}
     del kg, Mt
     # a6: permanent minors, 4096 masked-uniform matrices of order 14
     P = torch.as_tensor(inputs.perm_batch(14, 4096, seed=4)).to(dev)
@@ -412,13 +442,19 @@ def measure_rows(args, dev, peak):
                  "train_step_8192_us": t_train / max(len(losses), 1) * 1e6,
                  "kernel": "tcgen05.mma kind::f16, TMA loads, TMEM accumulator (one 128 x 128 tile per CTA)"}
     per_n = {}
-    tot = {"plain_ess": 0.0, "plain_s": 0.0, "learned_ess": 0.0, "learned_s": 0.0}
+    tot = {k: 0.0 for k in ("plain_s", "learned_s", "plain_ess_sign", "learned_ess_sign", "plain_ess_logc",
+                            "learned_ess_logc", "learned_ess_ratio")}
+    steps = {}
     for n, wk in walkers.items():
+        T = args.mc_steps if n <= 12 else args.mc_steps_high
+        steps[n] = T
         X0, w0, s0 = wk.X.clone(), wk.weight.clone(), wk.sign.clone()
         rec = []
         e0 = wk.exact_evals
         _, tp = mc.timed(lambda: [wk.step_plain(rec) for _ in range(T)])
-        ep, ess_p = wk.exact_evals - e0, mc.ess(rec, 1)
+        ep = wk.exact_evals - e0
+        ess_ps, ess_pl = mc.ess(rec, 0), mc.ess(rec, 1)
+        del rec
         wk.X.copy_(X0); wk.weight.copy_(w0); wk.sign.copy_(s0)
         rec = []
         e0 = wk.exact_evals
@@ -428,25 +464,62 @@ def measure_rows(args, dev, peak):
             for _ in range(T):
                 wk.step_da(net, rec)
         _, tl = mc.timed(run_learned)
-        el, ess_l = wk.exact_evals - e0, mc.ess(rec, 1)
-        per_n[str(n)] = {"plain_ess_per_s": ess_p / tp, "learned_ess_per_s": ess_l / tl,
-                         "plain_exact_evals_per_ess": ep / ess_p, "learned_exact_evals_per_ess": el / ess_l}
-        tot["plain_ess"] += ess_p
+        el = wk.exact_evals - e0
+        ess_ls, ess_ll, ess_lr = mc.ess(rec, 0), mc.ess(rec, 1), mc.ess(rec, 2)
+        sign_mean = float(torch.stack([r[0] for r in rec]).mean())
+        del rec
+        fin = lambda x: x if np.isfinite(x) else None
+        per_n[str(n)] = {"steps": T, "plain_s": tp, "learned_s": tl, "mean_sign": sign_mean,
+                         "plain_ess_per_s_sign": fin(ess_ps / tp), "learned_ess_per_s_sign": fin(ess_ls / tl),
+                         "plain_ess_per_s_logc": ess_pl / tp, "learned_ess_per_s_logc": ess_ll / tl,
+                         "learned_ess_per_s_log_c_over_surrogate": fin(ess_lr / tl),
+                         "plain_exact_evals_per_ess_logc": ep / ess_pl,
+                         "learned_exact_evals_per_ess_logc": el / ess_ll}
         tot["plain_s"] += tp
-        tot["learned_ess"] += ess_l
         tot["learned_s"] += tl
-    t_net = t_train  # the training pairs come from plain steps that also sample; only training is extra
+        tot["plain_ess_logc"] += ess_pl
+        tot["learned_ess_logc"] += ess_ll
+        if np.isfinite(ess_ps) and np.isfinite(ess_ls):
+            tot["plain_ess_sign"] += ess_ps
+            tot["learned_ess_sign"] += ess_ls
+    fixed = t_collect + t_train   # the learned arm also pays for its training pairs and the training
+    gain = lambda key, extra: ((tot["learned_ess_" + key] / (tot["learned_s"] + extra)) /
+                               (tot["plain_ess_" + key] / tot["plain_s"])) if tot["plain_ess_" + key] else None
     rows["a8_learned_proposal_16384_walkers_n10to14"] = {
-        "metric": "effective samples/s of log|c_n| (Sokal window), all orders 10..14",
-        "plain_ess_per_s": tot["plain_ess"] / tot["plain_s"],
-        "learned_ess_per_s": tot["learned_ess"] / tot["learned_s"],
-        "learned_ess_per_s_incl_training": tot["learned_ess"] / (tot["learned_s"] + t_net),
-        "gain": (tot["learned_ess"] / tot["learned_s"]) / (tot["plain_ess"] / tot["plain_s"]),
-        "gain_incl_training": (tot["learned_ess"] / (tot["learned_s"] + t_net)) /
-                              (tot["plain_ess"] / tot["plain_s"]),
-        "steps_per_chain": T, "train_s": t_train, "collect_s": t_collect,
+        "metric": "effective samples/s (Sokal's adaptive window, mean autocorrelation over 16384 walkers) "
+                  "of sgn c_n, i.e. at equal standard error of <sgn c_n>, summed over orders 10..14; "
+                  "log|c_n| alongside",
+        "plain_ess_per_s_sign": tot["plain_ess_sign"] / tot["plain_s"],
+        "learned_ess_per_s_sign": tot["learned_ess_sign"] / tot["learned_s"],
+        "gain_sign": gain("sign", 0.0),
+        "gain_sign_incl_collection_and_training": gain("sign", fixed),
+        "gain_logc": gain("logc", 0.0),
+        "gain_logc_incl_collection_and_training": gain("logc", fixed),
+        "value": tot["learned_ess_sign"] / (tot["learned_s"] + fixed), "unit": "effective samples/s",
+        "steps_per_chain": {str(k): v for k, v in steps.items()}, "train_s": t_train, "collect_s": t_collect,
         "final_train_loss": float(np.mean(losses[-5:])), "per_order": per_n, "surrogate": surrogate}
     return rows
+
+
+def rows_summary(rows: dict) -> dict:
+    """Three numbers per row: [value, ms, fraction of the FP64 peak] for the
+    kernel rows; [fast-subset-convolution time over the recursion's at n = 15,
+    at n = 16, None] for that comparison; [learned effective samples/s of
+    sgn c_n with collection and training counted, gain over plain at equal
+    standard error without and with them] for the learned proposal."""
+    def r(x, d=4):
+        return None if x is None else float(f"{x:.{d}g}")
+    out = {"fields": "kernel rows: value, ms, frac_fp64_peak; fsc: ratio n15, n16; a8: value, gain, gain_incl"}
+    for k, v in rows.items():
+        if not isinstance(v, dict):
+            continue
+        if k.startswith("a8"):
+            out[k] = [r(v.get("value"), 6), r(v.get("gain_sign")), r(v.get("gain_sign_incl_collection_and_training"))]
+        elif k.startswith("cdet_fsc"):
+            out[k] = [r(v.get(str(m), {}).get("fsc_over_recursion")) for m in (15, 16)] + [None]
+        else:
+            out[k] = [r(v.get("value"), 6), r(v.get("ms"), 5), r(v.get("frac_fp64_peak"))]
+    return out
 
 
 def cpu_rate(run, A_np, seconds: float, threads: int):
@@ -499,17 +572,21 @@ def run_reference(args, rank, world):
         r, threads, count, dt = cpu_oracle_rate(A[(i * 97) % 1024:], per_step)
         if i >= args.warmup:
             rates.append((r, count, dt))
-    value = sum(c for _, c, _ in rates) / sum(d for _, _, d in rates)
+    done = sum(c for _, c, _ in rates)
+    secs = sum(d for _, _, d in rates)
+    value = done / secs
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1000.0 * args.batch / value, "higher_is_better": True, "scaling": "weak",
+        # the time of the work each step actually did: a sample of the batch
+        "ms_per_step": 1000.0 * secs / len(rates), "matrices_per_step": done / len(rates),
+        "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"hubbard_g0_n{N_ORDER}_batch{args.batch}_minors+cdet",
-                   "n": N_ORDER, "batch": args.batch},
+        "config": bench_config(N_ORDER, args.batch, world),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": f"{rates[0][1]} matrices per step of the same workload "
-                                   "(per-minor partial-pivot LU + plain recursion, OpenMP)"},
+                         "sample": f"{done / len(rates):.0f} of the {args.batch} matrices per step, "
+                                   f"{secs / len(rates):.2f} s per step (per-minor partial-pivot LU + "
+                                   "plain recursion, OpenMP)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -525,6 +602,15 @@ def profile_case(name: str):
     if name == "cdet_n12":
         A = torch.as_tensor(inputs.hubbard_batch(4096, 12, seed=2)).to(dev)
         run = lambda: apm.cdet_connected(A, return_minors=True)
+    elif name == "cdet_n12_full":
+        # the benchmark's launch: 65536 matrices, 4.3 GB of outputs (33 x L2), for DRAM counters only
+        A = torch.as_tensor(inputs.hubbard_batch(65536, 12, seed=2)).to(dev)
+        c = torch.empty((65536, 4096), dtype=torch.float64, device=dev)
+        mo = torch.empty_like(c)
+        run = lambda: apm.cdet_connected(A, out_c=c, out_minors=mo)
+    elif name == "fp64_probe":
+        # the FP64 throughput probe of the bench line (456 CTAs of 512 threads, 2048 iterations)
+        run = lambda: apm.fp64_probe(SMS * 3, 512, 2048, dev)
     elif name == "cdet_n16":
         A = torch.as_tensor(inputs.hubbard_batch(304, 16, seed=2)).to(dev)
         run = lambda: apm.cdet_connected(A, return_minors=True)
@@ -610,7 +696,7 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     n, B = N_ORDER, args.batch
-    A_np = inputs.hubbard_batch(B, n, seed=2 + rank)
+    A_np = inputs.hubbard_batch_slice(world * B, n, 2, rank * B, (rank + 1) * B)
     A = torch.as_tensor(A_np).to(dev)
     N = 1 << n
     c = torch.empty((B, N), dtype=torch.float64, device=dev)
@@ -621,16 +707,21 @@ def main():
     def step():
         apm.cdet_connected(A, out_c=c, out_minors=mo)
 
-    # FP64 throughput probe (roofline context)
-    blocks, threads, iters = SMS * 4, 512, 2048
+    # FP64 throughput probe (roofline context): about a second of independent
+    # FMA chains, with the SM clock sampled while it runs; one full wave (the
+    # probe's 38 registers admit three CTAs of 512 threads per SM)
+    blocks, threads, iters, reps = SMS * 3, 512, 2048, 64
     apm.fp64_probe(blocks, threads, 64, dev)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    apm.fp64_probe(blocks, threads, iters, dev)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    probe_tflops = 32.0 * blocks * threads * iters / (e0.elapsed_time(e1) * 1e-3) / 1e12
+    with ClockSampler(local) as pcs:
+        e0.record(stream)
+        for _ in range(reps):
+            apm.fp64_probe(blocks, threads, iters, dev)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    probe_tflops = 32.0 * blocks * threads * iters * reps / (e0.elapsed_time(e1) * 1e-3) / 1e12
+    probe_clocks = pcs.summary()
 
     for _ in range(args.warmup):
         step()
@@ -682,6 +773,11 @@ def main():
     # spot check of the end-to-end result against the device-timed one
     assert torch.equal(c_host[:4].to(dev), c[:4]) if rank == 0 else True
 
+    # the one exchange of the data-parallel path: per-order sums of the
+    # whole-set connected sums, reduced on the device, added over the ranks
+    from paper_2104_07638_gb300 import dist as pdist
+    est = pdist.estimator(pdist.combine_order_sums(apm.order_sums(c, n=n)))[n]
+
     import hashlib
     src = os.path.join(ROOT, "paper_2104_07638_gb300", "csrc", "fpm_cdet.cu")
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
@@ -690,20 +786,26 @@ def main():
     peak = FP64_FLOP_PER_CLK_SM * SMS * SM_MAX_MHZ * 1e6 / 1e12
     achieved = F * B / (ms_per_step * 1e-3) / 1e12
     clocks = cs.summary()
+    rows = measure_rows(args, dev, peak) if rank == 0 and not args.no_rows else None
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"hubbard_g0_n{n}_batch{B}_minors+cdet", "n": n, "batch": B,
-                   "per_rank_batch": B, "outputs": "minors[2^n] and c[2^n] per matrix, FP64",
-                   "l2": "256 MB buffer rewritten between timed steps (outside the events)",
-                   "timing": "CUDA events around each step on the launching stream"},
+    }
+    if rows:
+        # every row in three numbers, early in the line (it survives a truncated tail)
+        result["rows_summary"] = rows_summary(rows)
+    result.update({
+        "config": bench_config(n, B, world),
+        "timing": "CUDA events around each step on the launching stream",
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "traffic_note": "DRAM bytes per launch scaled from a 4096-matrix ncu capture",
+                     "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of this "
+                                     "launch (65536 matrices), per launch",
                      "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz "
                                     "(nominal 1.25 TFLOP/s FP64 at max clock)",
                      "flops_per_set": F, "fp64_probe_tflops": probe_tflops,
+                     "fp64_probe_sm_mhz": probe_clocks.get("sm_mhz"),
                      "hbm_gbs": bytes_per_set(n) * B / (ms_per_step * 1e-3) / 1e9},
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": int(A_host.numel() * 8),
@@ -711,9 +813,12 @@ def main():
         "gpu_launches": args.steps,
         "clocks": clocks,
         "wall_s_timed_region": t_wall,
-    }
-    if rank == 0 and not args.no_rows:
-        result["rows"] = measure_rows(args, dev, peak)
+        "estimator": {"order": n, "ranks": world, "count": est["count"], "mean_c": est["mean"],
+                      "stderr": est["stderr"], "mean_abs_c": est["mean_abs"], "sign": est["sign"],
+                      "exchange": "apm_order_sums per rank, summed over the ranks on the host"},
+    })
+    if rows:
+        result["rows"] = rows
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r, threads, count, dt = cpu_oracle_rate(A_np, args.cpu_seconds)
         r1, _, count1, dt1 = cpu_rate(oracle_run, A_np, args.cpu_seconds / 4, 1)
