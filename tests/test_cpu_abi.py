@@ -187,3 +187,54 @@ def test_host_call_workspace_layout(lib):
         slot = (mats * r256(chunk * n * n * 8) + r256(chunk * N * 8) + r256(chunk * mats * N * 8)
                 + r256(chunk * 4))
         assert out.value == ns * slot, (n, chunk, ns, two)
+
+
+def test_tune_options_host_side(lib):
+    """apm_tune_options_set/get keep host state only: range checks, defaults
+    (0 selects the hand-off at 16, all resident CTAs, 12 Keldysh warps), and a
+    rejected call changes nothing."""
+    i32, P = ctypes.c_int, ctypes.c_void_p
+    lib.apm_tune_options_set.argtypes = [i32, i32, i32]
+    lib.apm_tune_options_set.restype = ctypes.c_int
+    lib.apm_tune_options_get.argtypes = [P, P, P]
+    lib.apm_tune_options_get.restype = ctypes.c_int
+
+    def get():
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        assert lib.apm_tune_options_get(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)) == 0
+        return a.value, b.value, c.value
+
+    try:
+        assert lib.apm_tune_options_set(0, 0, 0) == 0 and get() == (16, 0, 0)
+        assert lib.apm_tune_options_set(14, 2, 6) == 0 and get() == (14, 2, 6)
+        for bad in ((12, 0, 0), (18, 0, 0), (16, 4, 0), (16, -1, 0), (16, 0, 2), (16, 0, 13)):
+            assert lib.apm_tune_options_set(*bad) == 1
+            assert get() == (14, 2, 6)
+        assert lib.apm_tune_options_set(17, 3, 12) == 0 and get() == (17, 3, 12)
+    finally:
+        lib.apm_tune_options_set(0, 0, 0)
+
+
+def test_exchange_and_split_training_argument_errors(lib):
+    """apm_order_sums and the split training step reject bad arguments on the
+    host, before any launch."""
+    P, i32, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+    f = lib.apm_order_sums
+    f.argtypes = [P, i32, P, P, i64, i32, P, P]
+    f.restype = ctypes.c_int
+    fake = ctypes.c_void_p(1 << 20)
+    assert f(fake, 8, None, None, 4, 0, fake, None) == 1        # n_max out of range
+    assert f(fake, 8, None, None, 4, 17, fake, None) == 1
+    assert f(fake, 9, None, None, 4, 8, fake, None) == 1        # fixed order above n_max
+    assert f(fake, 0, fake, None, 4, 8, fake, None) == 1        # n_arr without c_off
+    assert f(fake, 8, None, None, -1, 8, fake, None) == 1       # negative batch
+    assert f(fake, 8, None, None, 4, 8, None, None) == 1        # no output
+    assert f(None, 8, None, None, 4, 8, fake, None) == 1        # rows missing
+    g = lib.apm_mlp_adam_step
+    g.argtypes = [P, ctypes.c_float, i32, P]
+    g.restype = ctypes.c_int
+    assert g(None, ctypes.c_float(1e-3), 1, None) == 1
+    h = lib.apm_mlp_gradient
+    h.argtypes = [P, P, P, i32, i32, P, P, ctypes.c_size_t, P]
+    h.restype = ctypes.c_int
+    assert h(None, fake, fake, 64, 64, fake, fake, 1 << 20, None) == 1
