@@ -708,8 +708,9 @@ def main():
         apm.cdet_connected(A, out_c=c, out_minors=mo)
 
     # FP64 throughput probe (roofline context): about a second of independent
-    # FMA chains, with the SM clock sampled while it runs; one full wave (the
-    # probe's 38 registers admit three CTAs of 512 threads per SM)
+    # FMA chains, with the SM clock sampled while it runs (one full wave: the
+    # probe's 38 registers admit three CTAs of 512 threads per SM; its rate does
+    # not depend on the launch shape)
     blocks, threads, iters, reps = SMS * 3, 512, 2048, 64
     apm.fp64_probe(blocks, threads, 64, dev)
     torch.cuda.synchronize()
