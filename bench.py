@@ -37,10 +37,10 @@ SM_MAX_MHZ = 2070.0
 FP64_FLOP_PER_CLK_SM = 4.0   # 1.25 TFLOP/s nominal FP64 / (152 SMs x 2.07 GHz), 2 DFMA/clk/SM
 METRIC = "minor-sets/sec at n=12 FP64 (% of roofline)"
 # DRAM bytes (read + write) per matrix of the fused kernel from one ncu capture
-# of the benchmark's launch itself (65536 matrices: 79.8 MB read, 4233.3 MB
+# of the benchmark's launch itself (65536 matrices: 80.8 MB read, 4233.4 MB
 # written), valid only for the kernel source it was taken on (sha256 prefix below).
-TRAFFIC_PER_SET = (79764224 + 4233314816) / 65536
-TRAFFIC_SRC_SHA = "fb291277c1e0fe45"
+TRAFFIC_PER_SET = (80803328 + 4233424384) / 65536
+TRAFFIC_SRC_SHA = "5be6076313768eea"
 UNIT = "minor-sets/s"
 
 

@@ -16,11 +16,15 @@
 //   Its (1,1) entry p gives det A[m | {l}] = det A[m] * p (Eq. minor). The left
 //   child (element l excluded) is the same matrix without its first row and
 //   column; the right child (l included) is its Schur complement with respect
-//   to p. Levels 0..L-1 (L = n-4) are expanded breadth first across the CTA,
-//   one child entry per thread step; the 2^L nodes of level L (4x4 each) are
-//   finished by one thread each with closed-form 1x1..4x4 determinants, which
-//   needs no pivot at all. Level buffers alternate between MC and the not yet
-//   written upper part of MA, so the tree needs no memory beyond MA and MC.
+//   to p. Levels 0..L-1 (L = n-4) are expanded breadth first across the CTA
+//   (per level: one thread per node for its minor and pivot reciprocal, then
+//   the pivot rows scaled and the child entries formed, one entry per thread
+//   step); the 2^L nodes of level L (4x4 each) are finished by one thread each:
+//   one more Schur step on the node's first element (a pivot like the others,
+//   corrected when tiny) and the 8 minors of each 3x3 child in closed form (56
+//   FP64 operations per node against 73 for a 4x4 closed form). Level buffers
+//   alternate between MC and the not yet written upper part of MA, so the tree
+//   needs no memory beyond MA and MC.
 //   Pivot correction: a pivot with |p| <= thr is shifted by C; the node's minor
 //   is stored with p + C and the right subtree is built from the shifted
 //   matrix. The shift equals adding C to A_ll for every mask of that subtree, so
@@ -226,6 +230,64 @@ __device__ __forceinline__ void bottom4(const double *__restrict__ w, double pre
     MA[m | (15 << L)] = pre * d0123;
 }
 
+// The 7 principal minors other than the empty one of a 3 x 3 node C (row-major
+// stride 4 from c) with node minor d, written to MA[base | X << sh] for
+// X = 1..7: row 0 scaled by d first, the 2 x 2 minors directly, the whole by
+// expansion along row 0 (no division).
+__device__ __forceinline__ void cf3_store(const double *c, int st, double d, double *MA, int base, int sh) {
+    const double c00 = c[0], c01 = c[1], c02 = c[2];
+    const double c10 = c[st], c11 = c[st + 1], c12 = c[st + 2];
+    const double c20 = c[2 * st], c21 = c[2 * st + 1], c22 = c[2 * st + 2];
+    const double a0 = d * c00, a1 = d * c01, a2 = d * c02;
+    const double m12 = fma(c11, c22, -c12 * c21);
+    const double m02 = fma(c10, c22, -c12 * c20);
+    const double m01 = fma(c10, c21, -c11 * c20);
+    MA[base | (1 << sh)] = a0;
+    MA[base | (2 << sh)] = d * c11;
+    MA[base | (3 << sh)] = fma(a0, c11, -a1 * c10);
+    MA[base | (4 << sh)] = d * c22;
+    MA[base | (5 << sh)] = fma(a0, c22, -a2 * c20);
+    MA[base | (6 << sh)] = d * m12;
+    MA[base | (7 << sh)] = fma(a0, m12, fma(-a1, m02, a2 * m01));
+}
+
+// The 15 principal minors of a 4x4 node w (elements L..L+3, node minor MA[m])
+// by one Schur step on its first element, a pivot of the tree, and the closed
+// forms of the two 3x3 children. A tiny pivot p is shifted by C as on the
+// other levels, but its correction is finished here: the node's right subtree
+// is the 7 minors of its kept child, all in this thread, and this is the
+// deepest level with pivots, so det[m] = det~[m] - C det[m without element L]
+// is applied at once (before the logged corrections of the shallower levels),
+// and the node's own minor is written with the unshifted pivot. No log entry.
+__device__ __forceinline__ void bottom43(const double *__restrict__ w, double *MA, int m, int L, double thr,
+                                         double shift, CdetSmemHdr &h) {
+    const double p = w[0], d = MA[m];
+    const bool corr = fabs(p) <= thr;
+    const double C = corr ? (p >= 0.0 ? shift : -shift) : 0.0;
+    const double piv = p + C;
+    const double v = 1.0 / piv;
+    const int mk = m | (1 << L);
+    MA[mk] = d * p;
+    const double g1 = w[4] * v, g2 = w[8] * v, g3 = w[12] * v;
+    double S[9];
+    S[0] = fma(-g1, w[1], w[5]);
+    S[1] = fma(-g1, w[2], w[6]);
+    S[2] = fma(-g1, w[3], w[7]);
+    S[3] = fma(-g2, w[1], w[9]);
+    S[4] = fma(-g2, w[2], w[10]);
+    S[5] = fma(-g2, w[3], w[11]);
+    S[6] = fma(-g3, w[1], w[13]);
+    S[7] = fma(-g3, w[2], w[14]);
+    S[8] = fma(-g3, w[3], w[15]);
+    cf3_store(w + 5, 4, d, MA, m, L + 1);      // element L dropped
+    cf3_store(S, 3, d * piv, MA, mk, L + 1);   // element L kept (shifted minor when corrected)
+    if (corr) {
+#pragma unroll
+        for (int X = 1; X < 8; ++X) MA[mk | (X << (L + 1))] = fma(-C, MA[m | (X << (L + 1))], MA[mk | (X << (L + 1))]);
+        atomicOr(&h.flags, APM_ST_PIVOT_CORRECTED);
+    }
+}
+
 // All principal minors of the n x n matrix Ag into MA[0 .. 2^n), MC as scratch.
 __device__ __forceinline__ void fpm_tree(const double *__restrict__ Ag, int n, double *MA, double *MC, double thr,
                          double shift, CdetSmemHdr &h) {
@@ -257,8 +319,13 @@ __device__ __forceinline__ void fpm_tree(const double *__restrict__ Ag, int n, d
             double *Wm = Wl + m * ss;
             double v = Wm[0];
             node_pivot(m, l, v, MA, thr, shift, h);
-            for (int q = 1; q < s; ++q) Wm[q] *= v;
             Wm[0] = v;
+        }
+        __syncthreads();
+        // the pivot rows scaled by 1/p, one entry per thread step
+        for (int e = tid; e < P * s1; e += T) {
+            const int m = e / s1, q = e - m * s1 + 1;
+            Wl[m * ss + q] *= Wl[m * ss];
         }
         __syncthreads();
         const int E = 2 * P * ss1;
@@ -277,8 +344,12 @@ __device__ __forceinline__ void fpm_tree(const double *__restrict__ Ag, int n, d
     }
     const double *WL = APM_BUF(L);
 #undef APM_BUF
-    const int s = n < 4 ? n : 4;
-    for (int m = tid; m < (1 << L); m += T) bottom4(WL + m * 16, MA[m], MA, m, L, s);
+    if (n >= 4) {
+        for (int m = tid; m < (1 << L); m += T) bottom43(WL + m * 16, MA, m, L, thr, shift, h);
+    } else {
+        const int s = n;
+        for (int m = tid; m < (1 << L); m += T) bottom4(WL + m * 16, MA[m], MA, m, L, s);
+    }
     __syncthreads();
     // back-propagation of pivot corrections, deepest level first (the log is in
     // non-decreasing level order: each level's pivots are logged in its own

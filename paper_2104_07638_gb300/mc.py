@@ -275,8 +275,11 @@ class Walkers:
             self.steps += 1
         F = torch.cat(feats)
         t = torch.cat(targets)
-        # clip the far lower tail (near-cancelling configurations) for the regression
-        lo = torch.quantile(t[:min(t.numel(), 1 << 20)], 0.01)
+        # clip the far lower tail (near-cancelling configurations) for the
+        # regression; a non-finite target (a matrix the kernel flagged, e.g. a
+        # correction-log overflow) gets the same clip value
+        lo = torch.nanquantile(t[:min(t.numel(), 1 << 20)], 0.01)
+        t = torch.where(torch.isfinite(t), t, lo)
         return F, torch.maximum(t, lo)
 
 
