@@ -364,7 +364,12 @@ __device__ __forceinline__ void nd_tail_levels(double *cur, double *nxt, double 
         __syncwarp();
         const int tcnt = kCorr ? (w.tcnt < kNdTlogCap ? w.tcnt : kNdTlogCap) : 0;
         const double *T = nd_type_sum<kCorr>(S, nxt, cur, cc, tcnt, lane);
-        if (!kCorr || fcnt <= 1) {
+        if constexpr (!kCorr) {
+            // atomic additions performed in L2 (no FP64 instruction, no load
+            // latency on the SM); one warp owns the row and adds its leaves in
+            // order, so the sums are the same on every run
+            for (int i = lane; i < (1 << S); i += 32) atomicAdd(gout + mask0 + i, T[i]);
+        } else if (fcnt <= 1) {
             for (int i = lane; i < (1 << S); i += 32) gout[mask0 + i] += T[i];
         } else {
             for (int j = 0; j < fcnt; ++j) {

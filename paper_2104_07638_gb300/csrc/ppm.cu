@@ -36,9 +36,12 @@
 //    half-warp mostly hit distinct banks. A stream writes the sum of each run
 //    of terms of one S_L to a result slot; the runs of a cut set are added
 //    pairwise in rounds of one addition per lane (a fixed tree), and the warp
-//    adds the 2^l sums into perm[S_H u S_L] in the output
-//    row (no two warps touch one S within a step and steps are separated by
-//    barriers: no atomics, deterministic).
+//    adds the 2^l sums into perm[S_H u S_L] in the output row by atomic
+//    additions performed in L2 (fire and forget: no FP64 instruction and no
+//    load latency on the SM). No two warps touch one S within a step and steps
+//    are separated by CTA barriers, after which the earlier steps' additions
+//    are visible, so every entry receives its terms in the same order on
+//    every run: deterministic.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -567,12 +570,7 @@ __global__ void __launch_bounds__(kPpmWarps * 32, 3) ppm_kernel(const double *__
                         }
                         __syncwarp();
                     }
-                    for (int S = lane; S < NL; S += 32) {
-                        const double tot = res[first[S]];
-                        // the output row streams through L2 only, so that L1 keeps the schedule
-                        double *o = perm + ((SH << l) | S);
-                        __stcg(o, __ldcg(o) + tot);
-                    }
+                    for (int S = lane; S < NL; S += 32) atomicAdd(perm + ((SH << l) | S), res[first[S]]);
                     __syncwarp();
                 }
             }
