@@ -104,7 +104,7 @@ def parse():
     ap.add_argument("--case", default=None,
                     choices=["cdet_n12", "cdet_n12_full", "cdet_n16", "keldysh_n12", "ppm_n14", "cdet_uneven",
                              "xnor_n12", "nand_n10", "keldysh2_n12", "mlp_gemm", "fsc_n16", "minors_n12",
-                             "minors_n20", "fp64_probe"],
+                             "minors_n20", "minors_n24", "fp64_probe"],
                     help="run 3 launches of one kernel on a small case (for profiling) and exit")
     return ap.parse_args()
 
@@ -631,6 +631,10 @@ def profile_case(name: str):
     elif name == "minors_n20":
         # orders past 16: 64 matrices of order 20 (the upper levels, then 1024 leaves each)
         A = torch.as_tensor(np.random.default_rng(20).standard_normal((64, 20, 20)) + 2.0 * np.eye(20)).to(dev)
+        run = lambda: apm.all_minors(A)
+    elif name == "minors_n24":
+        # the benchmark row: 16 matrices of order 24 (2.1 GB of minors; 4096 leaves of order 12 each)
+        A = torch.as_tensor(np.random.default_rng(24).standard_normal((16, 24, 24)) + 2.0 * np.eye(24)).to(dev)
         run = lambda: apm.all_minors(A)
     elif name == "nand_n10":
         M = torch.as_tensor(inputs.two_type_batch(16384, 10, seed=7)).to(dev)

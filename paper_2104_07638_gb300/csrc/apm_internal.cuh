@@ -61,7 +61,10 @@ struct CdetArgs {
     double piv_thr;
     double piv_shift;
     int fsc_from_n;  // orders >= this (0: none) leave the weights a[] in c for the fast subset convolution
-    const uint32_t *redo;  // fixed-order launch: if set, only the matrices b with redo[b] != 0
+    // fixed-order launch: if set, only the matrices redo_list[0 .. *redo_count - 1]
+    // (in any order: each is computed on its own)
+    const uint32_t *redo_list;
+    const unsigned *redo_count;
     // fixed-order launch: if set, matrix b scales its pivot threshold and shift
     // by anorm_in[b >> anorm_shift] instead of its own ||A||max (the leaves of
     // a larger matrix take that matrix's norm)

@@ -159,16 +159,22 @@ __global__ void big_level_kernel(const double *__restrict__ src, double *__restr
 }
 
 // The leaves redone by the fused kernel (redo[L] != 0, usually none): their
-// 4096 minors times det(A[T]). One warp per leaf.
+// 4096 minors times det(A[T]). A warp reads 32 flags at once (one per lane)
+// and scales the flagged leaves among them with all its lanes.
 __global__ void big_scale_redo_kernel(double *out, int64_t leaves, const uint32_t *__restrict__ redo,
                                       const double *__restrict__ dleaf) {
     const int lane = threadIdx.x & 31;
     const int64_t nw = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
-    for (int64_t L = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; L < leaves; L += nw) {
-        if (redo[L] == 0u) continue;
-        const double f = dleaf[L];
-        double *row = out + (L << kBigLeafN);
-        for (int e = lane; e < (1 << kBigLeafN); e += 32) row[e] *= f;
+    for (int64_t L0 = ((static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5) << 5; L0 < leaves;
+         L0 += nw << 5) {
+        unsigned m = __ballot_sync(0xffffffffu, L0 + lane < leaves && redo[L0 + lane] != 0u);
+        while (m) {
+            const int64_t L = L0 + (__ffs(m) - 1);
+            m &= m - 1;
+            const double f = dleaf[L];
+            double *row = out + (L << kBigLeafN);
+            for (int e = lane; e < (1 << kBigLeafN); e += 32) row[e] *= f;
+        }
     }
 }
 
@@ -269,7 +275,11 @@ int launch_fpm_big(const double *A, int n, int64_t batch, double *minors, double
     err = launch_fpm_warp(src, kBigLeafN, batch << H, minors, thr, shf, lstat, leafws, s, det[H & 1], &redo, an,
                           H);
     if (err) return err;
-    big_scale_redo_kernel<<<1216, 256, 0, s>>>(minors, batch << H, redo, det[H & 1]);
+    {
+        const int64_t fb = ((batch << H) + 255) >> 8;  // blocks of 256 flags
+        big_scale_redo_kernel<<<static_cast<int>(fb < 1216 ? fb : 1216), 256, 0, s>>>(minors, batch << H, redo,
+                                                                                       det[H & 1]);
+    }
     big_backprop_kernel<<<static_cast<unsigned>(batch), 512, 0, s>>>(minors, n, H, ccount, clog, Cm, flags);
     big_status_kernel<<<static_cast<unsigned>(batch), 512, 0, s>>>(minors, n, H, flags, lstat, status);
     return static_cast<int>(cudaGetLastError());

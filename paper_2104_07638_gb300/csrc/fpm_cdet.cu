@@ -591,13 +591,19 @@ __global__ void __launch_bounds__(kCdetThreads, 3) fpm_cdet_kernel(const CdetKer
     double *MC = base + N;
     double *MU = MC + NC;
     const int64_t mat = static_cast<int64_t>(n) * n;
-    for (int64_t b = blockIdx.x; b < p.batch; b += gridDim.x) {
-        if (p.redo && p.redo[b] == 0u) continue;  // done by the warp-per-matrix minors kernel
+    auto item = [&](int64_t b) {
         cdet_item(p, n, p.A_up ? p.A_up + b * mat : nullptr, p.A_dn ? p.A_dn + b * mat : nullptr,
                   p.a_in ? p.a_in + b * N : nullptr,
                   p.minors_out ? p.minors_out + b * (p.two_mats ? 2 * N : N) : nullptr,
                   p.c_out ? p.c_out + b * N : nullptr, p.status ? p.status + b : nullptr, MA, MC, MU,
                   kSmemArrays, P.gsel, P.gsel_b, sbase, h, p.anorm_in ? p.anorm_in + (b >> p.anorm_shift) : nullptr);
+    };
+    if (p.redo_list) {
+        // only the matrices the warp-per-matrix minors kernel flagged (usually none)
+        const int64_t cnt = *p.redo_count < p.batch ? static_cast<int64_t>(*p.redo_count) : p.batch;
+        for (int64_t i = blockIdx.x; i < cnt; i += gridDim.x) item(p.redo_list[i]);
+    } else {
+        for (int64_t b = blockIdx.x; b < p.batch; b += gridDim.x) item(b);
     }
     if (threadIdx.x == 0) bulk_wait_all();
 }

@@ -288,7 +288,8 @@ __device__ __forceinline__ int fw_matrix(const double *A, int n, double *out, do
     return __any_sync(0xffffffffu, bad | small);
 }
 
-// Every matrix; redo[b] = 1 where the fused kernel must compute it again. pre
+// Every matrix; redo[b] = 1 where the fused kernel must compute it again, and
+// then b is appended to redo_list (*redo_count entries, zeroed before). pre
 // (or NULL for 1): a factor per matrix on all its minors; anorm (or NULL): the
 // scale of the threshold, anorm[b >> anorm_shift], in place of the matrix's own
 // ||A||max (the leaves of a larger matrix take its norm). T = min(n, 12), one
@@ -299,6 +300,7 @@ template <int T>
 __global__ void __launch_bounds__(kFwWarps * 32, 2) fpm_warp_kernel(const double *__restrict__ A, int n,
                                                                   int64_t batch, double *minors, double thr,
                                                                   const double *__restrict__ pre, uint32_t *redo,
+                                                                  uint32_t *redo_list, unsigned *redo_count,
                                                                   uint32_t *status, double *stack_base,
                                                                   size_t stack_per_warp,
                                                                   const double *__restrict__ anorm,
@@ -315,13 +317,14 @@ __global__ void __launch_bounds__(kFwWarps * 32, 2) fpm_warp_kernel(const double
                                    anorm ? anorm + (b >> anorm_shift) : nullptr, stack, w, lane);
         if (lane == 0) {
             redo[b] = static_cast<uint32_t>(r);
+            if (r) redo_list[atomicAdd(redo_count, 1u)] = static_cast<uint32_t>(b);
             if (status && !r) status[b] = 0u;
         }
     }
 }
 
 using FwKernel = void (*)(const double *, int, int64_t, double *, double, const double *, uint32_t *, uint32_t *,
-                         double *, size_t, const double *, int);
+                         unsigned *, uint32_t *, double *, size_t, const double *, int);
 static FwKernel fw_kernel_for(int n) {
     switch (n < kFwTail ? n : kFwTail) {
         case 9: return fpm_warp_kernel<9>;
@@ -353,9 +356,10 @@ static int fpm_warp_grid(int n, int64_t batch, int *err) {
 }
 
 // Workspace: per resident warp the depth-first stack, one redo flag per
-// matrix, and for n > 12 the fused kernel's global scratch (its redo launch).
+// matrix, the redo list (a counter, then up to one entry per matrix), and for
+// n > 12 the fused kernel's global scratch (its redo launch).
 struct FwPlan {
-    size_t stack, redo, fused, total;
+    size_t stack, redo, list, fused, total;
 };
 static int fw_plan(int n, int64_t batch, FwPlan *p, int *grid) {
     int err = 0;
@@ -364,13 +368,14 @@ static int fw_plan(int n, int64_t batch, FwPlan *p, int *grid) {
     auto al = [](size_t x) { return (x + 255) & ~static_cast<size_t>(255); };
     p->stack = al(static_cast<size_t>(*grid) * kFwWarps * fw_stack_entries(n) * sizeof(double));
     p->redo = al(static_cast<size_t>(batch) * sizeof(uint32_t));
+    p->list = 256 + al(static_cast<size_t>(batch) * sizeof(uint32_t));
     p->fused = 0;
     if (n > cdet_smem_max_n(false)) {
         const int g = cdet_grid(n, batch, false, false, &err);
         if (err) return err;
         p->fused = al(static_cast<size_t>(g) * cdet_slot_doubles(n) * sizeof(double));
     }
-    p->total = p->stack + p->redo + p->fused;
+    p->total = p->stack + p->redo + p->list + p->fused;
     return 0;
 }
 
@@ -395,10 +400,14 @@ int launch_fpm_warp(const double *A, int n, int64_t batch, double *minors, doubl
     char *ws = static_cast<char *>(workspace);
     double *stack = per ? reinterpret_cast<double *>(ws) : nullptr;
     uint32_t *redo = reinterpret_cast<uint32_t *>(ws + plan.stack);
-    double *fused = plan.fused ? reinterpret_cast<double *>(ws + plan.stack + plan.redo) : nullptr;
+    unsigned *count = reinterpret_cast<unsigned *>(ws + plan.stack + plan.redo);
+    uint32_t *list = reinterpret_cast<uint32_t *>(ws + plan.stack + plan.redo + 256);
+    double *fused = plan.fused ? reinterpret_cast<double *>(ws + plan.stack + plan.redo + plan.list) : nullptr;
     if (redo_out) *redo_out = redo;
-    fw_kernel_for(n)<<<grid, kFwWarps * 32, smem, s>>>(A, n, batch, minors, thr, pre, redo, status, stack, per,
-                                                        anorm_in, anorm_shift);
+    err = static_cast<int>(cudaMemsetAsync(count, 0, sizeof(unsigned), s));
+    if (err) return err;
+    fw_kernel_for(n)<<<grid, kFwWarps * 32, smem, s>>>(A, n, batch, minors, thr, pre, redo, list, count, status,
+                                                        stack, per, anorm_in, anorm_shift);
     err = static_cast<int>(cudaGetLastError());
     if (err) return err;
     // the flagged matrices again, by the fused kernel with the pivot correction
@@ -412,7 +421,8 @@ int launch_fpm_warp(const double *A, int n, int64_t batch, double *minors, doubl
     a.mode = kModeMinors;
     a.piv_thr = thr;
     a.piv_shift = shf;
-    a.redo = redo;
+    a.redo_list = list;
+    a.redo_count = count;
     a.gscratch = fused;
     a.anorm_in = anorm_in;
     a.anorm_shift = anorm_shift;

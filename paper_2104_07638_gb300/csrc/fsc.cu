@@ -29,9 +29,12 @@
 //           |X_H| + 9 (the only ones read out) and c[X] = L_{|X|}(X).
 // Butterflies run one element at a time, and a warp skips a step when all its
 // pairs are known no-ops (zero sources in a zeta, targets that are never read
-// out in a Mobius): about a third of the transforms at n = 16 (the butterfly
-// loops are kept rolled, which keeps the kernel within the registers of three
-// CTAs per SM). The transforms act on M_k = k L_k (linear), and the
+// out in a Mobius); the pairs are visited in popcount order of their 8 other
+// elements in passes A and C, and of their high part in pass B, so that the
+// no-ops fall into whole warps: 39 % of the transforms' pair visits are
+// skipped at n = 16 (28 % in mask order). The butterfly loops are kept rolled,
+// which keeps the kernel within the registers of three CTAs per SM. The
+// transforms act on M_k = k L_k (linear), and the
 // read-out divides by |S|. The logarithm keeps Z and M of one mask in
 // registers and skips the terms Z_m = 0 (m > |X|) when every lane of the warp
 // has |X| <= 9: in pass B the masks of a tile are visited in order of
@@ -65,15 +68,18 @@ __device__ __forceinline__ int binom_small(int m, int k) {
 // be a no-op: zeta, the source still sums over no mask with c elements (after
 // the elements below d, it sums over the masks between its part above d and
 // itself); Mobius, no mask with c elements is reached from the target by
-// adding elements above d (its value is never read out).
-__device__ __forceinline__ void fsc_butterfly_low(double *T, int bits, int nr, int c0, bool mobius) {
+// adding elements above d (its value is never read out). With a full tile the
+// pairs of a step are visited in popcount order of their other 8 elements
+// (ord8), which puts the no-ops of both kinds mostly into whole warps.
+__device__ __forceinline__ void fsc_butterfly_low(double *T, int bits, int nr, int c0, bool mobius,
+                                                  const uint8_t *ord8) {
     const int half = 1 << (bits - 1);
     const bool prune = bits == kFscTileBits;
 #pragma unroll 1
     for (int d = 0; d < bits; ++d) {
 #pragma unroll 1
         for (int q = threadIdx.x; q < half * nr; q += kFscThreads) {
-            const int r = q >> (bits - 1), p = q & (half - 1);
+            const int r = q >> (bits - 1), p = prune ? ord8[q & (half - 1)] : q & (half - 1);
             const int lo = ((p >> d) << (d + 1)) | (p & ((1 << d) - 1)), hi = lo | (1 << d);
             if (prune) {
                 const int c = c0 + r;
@@ -180,6 +186,7 @@ __global__ void __launch_bounds__(kFscThreads, 3) fsc_kernel(const double *a, in
     __shared__ uint16_t s_order[kFscTile];  // tile entries by (popcount, value)
     __shared__ double s_inv[kFscMaxN + 1];  // 1/k
     __shared__ uint8_t s_ordh[1 << (kFscMaxN - kFscTileBits - 1)];  // masks of h - 1 bits by popcount
+    __shared__ uint8_t s_ord8[kFscTile / 2];                        // masks of 8 bits by popcount
     const int tid = threadIdx.x;
     const int N = 1 << n;
     if (tid <= kFscMaxN) s_inv[tid] = tid ? 1.0 / tid : 0.0;
@@ -192,6 +199,14 @@ __global__ void __launch_bounds__(kFscThreads, 3) fsc_kernel(const double *a, in
         int i = 0;
         for (int r = t; r; r &= r - 1) pos += binom_small(__ffs(r) - 1, ++i);
         s_order[pos] = static_cast<uint16_t>(t);
+    }
+    for (int t = tid; t < kFscTile / 2; t += kFscThreads) {
+        const int p = __popc(t);
+        int pos = 0;
+        for (int c = 0; c < p; ++c) pos += binom_small(kFscTileBits - 1, c);
+        int i = 0;
+        for (int r = t; r; r &= r - 1) pos += binom_small(__ffs(r) - 1, ++i);
+        s_ord8[pos] = static_cast<uint8_t>(t);
     }
     const int hb = n > kFscTileBits ? n - kFscTileBits - 1 : 0;  // bits of the high part minus one
     for (int t = tid; t < (1 << hb); t += kFscThreads) {
@@ -215,10 +230,10 @@ __global__ void __launch_bounds__(kFscThreads, 3) fsc_kernel(const double *a, in
                 T[r * kFscTile + x] = __popc(x) == r + 1 ? ab[x] : 0.0;
             }
             __syncthreads();
-            fsc_butterfly_low(T, n, n, 1, false);
+            fsc_butterfly_low(T, n, n, 1, false, s_ord8);
             fsc_log(T, N, n, nullptr, 0);
             __syncthreads();
-            fsc_butterfly_low(T, n, n, 1, true);
+            fsc_butterfly_low(T, n, n, 1, true, s_ord8);
             double *cb = row_out(b);
             for (int x = tid; x < N; x += kFscThreads)
                 cb[x] = x ? T[(__popc(x) - 1) * kFscTile + x] * s_inv[__popc(x)] : 0.0;
@@ -240,7 +255,7 @@ __global__ void __launch_bounds__(kFscThreads, 3) fsc_kernel(const double *a, in
                 T[q] = __popc(x) + p == k0 + r ? ab[base + x] : 0.0;
             }
             __syncthreads();
-            fsc_butterfly_low(T, kFscTileBits, nr, k0 - p, false);
+            fsc_butterfly_low(T, kFscTileBits, nr, k0 - p, false, s_ord8);
             for (int q = tid; q < n * kFscTile; q += kFscThreads) {
                 const int k = (q >> kFscTileBits) + 1, x = q & (kFscTile - 1);
                 R[static_cast<size_t>(k - 1) * N + base + x] =
@@ -278,7 +293,7 @@ __global__ void __launch_bounds__(kFscThreads, 3) fsc_kernel(const double *a, in
                 T[q] = R[static_cast<size_t>(k0 + r - 1) * N + base + x];
             }
             __syncthreads();
-            fsc_butterfly_low(T, kFscTileBits, nr, k0 - p, true);
+            fsc_butterfly_low(T, kFscTileBits, nr, k0 - p, true, s_ord8);
             for (int x = tid; x < kFscTile; x += kFscThreads)
                 cb[base + x] = (XH | x) ? T[(__popc(x) + p - k0) * kFscTile + x] * s_inv[__popc(x) + p] : 0.0;
             __syncthreads();
