@@ -9,19 +9,20 @@
 namespace apm {
 
 // 1/d. Where d and 1/d are normal numbers (biased exponent of |d| in 3..2044):
-// the hardware approximation (rcp.approx.ftz.f64, relative error far below
-// 2^-14) refined by two Newton-Raphson steps x <- x + x(1 - d x), each of which
-// squares the relative error, so the result is within a few units in the last
-// place. Elsewhere (zero, subnormal, huge, inf, NaN): the IEEE division.
+// the hardware approximation x (rcp.approx.ftz.f64; its relative error
+// e = 1 - d x measured at most 2^-19.9 over all 2^22 leading mantissa bits at
+// several exponents) refined by one step of the cubic iteration
+// x <- x (1 + e + e^2), the truncated geometric series of 1/(1 - e), which
+// leaves the relative error e^3 < 2^-59 plus the rounding of the last FMA
+// (three FMAs instead of the four of two Newton-Raphson steps).
+// Elsewhere (zero, subnormal, huge, inf, NaN): the IEEE division.
 __device__ __forceinline__ double rcp_nr(double d) {
     const unsigned ex = (static_cast<unsigned>(__double2hiint(d)) >> 20) & 0x7ffu;
     if (ex - 3u < 2042u) {
         double x;
         asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(x) : "d"(d));
-        double e = fma(-d, x, 1.0);
-        x = fma(x, e, x);
-        e = fma(-d, x, 1.0);
-        return fma(x, e, x);
+        const double e = fma(-d, x, 1.0);
+        return fma(x, fma(e, e, e), x);
     }
     return 1.0 / d;
 }

@@ -78,10 +78,13 @@ __host__ __device__ constexpr size_t fw_stack_entries(int n) {
 }
 
 // 1/p for a pivot (flags a zero or non-finite one) and whether |p| <= thrA
+// (thrA >= 0), tested on the high words in integer arithmetic (off the FP64
+// pipe): it also flags pivots up to 2^-20 (relative) above thrA, which only
+// sends such a matrix to the fused kernel, whose own test is exact.
 __device__ __forceinline__ double fw_inv(double p, double thrA, int &bad, int &small) {
     const long long bits = __double_as_longlong(p);
     if ((bits << 1) == 0 || ((bits >> 52) & 0x7ff) == 0x7ff) bad = 1;
-    small |= fabs(p) <= thrA;
+    small |= (static_cast<unsigned>(__double2hiint(p)) & 0x7fffffffu) <= static_cast<unsigned>(__double2hiint(thrA));
     return rcp_nr(p);
 }
 
