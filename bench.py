@@ -37,10 +37,11 @@ SM_MAX_MHZ = 2070.0
 FP64_FLOP_PER_CLK_SM = 4.0   # 1.25 TFLOP/s nominal FP64 / (152 SMs x 2.07 GHz), 2 DFMA/clk/SM
 METRIC = "minor-sets/sec at n=12 FP64 (% of roofline)"
 # DRAM bytes (read + write) per matrix of the fused kernel from one ncu capture
-# of the benchmark's launch itself (65536 matrices: 80.8 MB read, 4233.4 MB
-# written), valid only for the kernel source it was taken on (sha256 prefix below).
-TRAFFIC_PER_SET = (80803328 + 4233424384) / 65536
-TRAFFIC_SRC_SHA = "5be6076313768eea"
+# of the benchmark's launch itself (65536 matrices: 82.7 MB read, 4234.0 MB
+# written), valid only for the kernel source it was taken on: the sha256 prefix
+# below is of fpm_cdet.cu followed by apm_internal.cuh.
+TRAFFIC_PER_SET = (82729472 + 4233979904) / 65536
+TRAFFIC_SRC_SHA = "ea32556d5cbac2da"
 UNIT = "minor-sets/s"
 
 
@@ -784,8 +785,9 @@ def main():
     est = pdist.estimator(pdist.combine_order_sums(apm.order_sums(c, n=n)))[n]
 
     import hashlib
-    src = os.path.join(ROOT, "paper_2104_07638_gb300", "csrc", "fpm_cdet.cu")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    csrc = os.path.join(ROOT, "paper_2104_07638_gb300", "csrc")
+    sha = hashlib.sha256(b"".join(open(os.path.join(csrc, f), "rb").read()
+                                  for f in ("fpm_cdet.cu", "apm_internal.cuh"))).hexdigest()[:16]
     traffic = TRAFFIC_PER_SET * B if sha == TRAFFIC_SRC_SHA else None
     F = flops_per_set(n)
     peak = FP64_FLOP_PER_CLK_SM * SMS * SM_MAX_MHZ * 1e6 / 1e12
