@@ -376,7 +376,7 @@ def measure_rows(args, dev, peak):
         "value": 16 / (ms * 1e-3), "unit": "minor-sets/s", "ms": ms,
         "tflops": fl / (ms * 1e-3) / 1e12, "frac_fp64_peak": fl / (ms * 1e-3) / 1e12 / peak,
         "minors_written_gbs": out_bytes / (ms * 1e-3) / 1e9,
-        "launch": "12 upper-level launches, the minors kernels on the 65536 leaves, scale, back-propagation, status"}
+        "launch": "12 upper-level launches, the minors kernels on the 65536 leaves (the redone ones from the same root minors), back-propagation, status"}
     del A
     torch.cuda.empty_cache()
     # next (Section V.A): the connected sums by the fast subset convolution against

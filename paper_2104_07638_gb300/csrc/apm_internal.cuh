@@ -66,6 +66,10 @@ struct CdetArgs {
     // (in any order: each is computed on its own)
     const uint32_t *redo_list;
     const unsigned *redo_count;
+    // fixed-order minors launch (kModeMinors, one matrix): if set, matrix b's
+    // tree starts from the root minor pre[b] instead of 1, so that all its
+    // minors come out times pre[b]
+    const double *pre;
     // fixed-order launch: if set, matrix b scales its pivot threshold and shift
     // by anorm_in[b >> anorm_shift] instead of its own ||A||max (the leaves of
     // a larger matrix take that matrix's norm)
@@ -93,13 +97,13 @@ int launch_fpm_cdet(const CdetArgs &a, cudaStream_t s);
 // matrices with a small pivot are redone by the fused kernel (fpm_warp.cu).
 constexpr int kWarpMinorsFromN = 9;
 size_t fpm_warp_workspace_bytes(int n, int64_t batch, int *err);
-// pre (or NULL): a factor per matrix on all its minors, not applied to the
-// matrices redone by the fused kernel, whose flags come back in *redo_out.
-// anorm_in (or NULL): per matrix b the scale anorm_in[b >> anorm_shift] of the
-// pivot threshold and shift instead of the matrix's own ||A||max.
+// pre (or NULL): a factor per matrix on all its minors (the root minor of its
+// tree, in the redone matrices too). anorm_in (or NULL): per matrix b the scale
+// anorm_in[b >> anorm_shift] of the pivot threshold and shift instead of the
+// matrix's own ||A||max.
 int launch_fpm_warp(const double *A, int n, int64_t batch, double *minors, double thr, double shf,
                     uint32_t *status, void *workspace, cudaStream_t s, const double *pre = nullptr,
-                    uint32_t **redo_out = nullptr, const double *anorm_in = nullptr, int anorm_shift = 0);
+                    const double *anorm_in = nullptr, int anorm_shift = 0);
 
 // All principal minors for orders 17..24: the upper levels of the tree breadth
 // first, the 12 x 12 leaves by the fused kernel (fpm_big.cu).

@@ -18,7 +18,7 @@
 // warp-per-matrix minors kernel, with det(A[T]) as its root minor, writes the
 // 2^12 minors of M_T already scaled straight into the output row at T * 4096;
 // the leaves that meet a small pivot are redone by the fused kernel with its
-// own pivot correction, and only their rows are scaled afterwards.
+// own pivot correction, from the same root minor.
 //
 // A pivot of the upper levels with |p| <= thr ||A||max is shifted by
 // C = sign(p) shift ||A||max and recorded with its unshifted value; once the
@@ -158,26 +158,6 @@ __global__ void big_level_kernel(const double *__restrict__ src, double *__restr
     }
 }
 
-// The leaves redone by the fused kernel (redo[L] != 0, usually none): their
-// 4096 minors times det(A[T]). A warp reads 32 flags at once (one per lane)
-// and scales the flagged leaves among them with all its lanes.
-__global__ void big_scale_redo_kernel(double *out, int64_t leaves, const uint32_t *__restrict__ redo,
-                                      const double *__restrict__ dleaf) {
-    const int lane = threadIdx.x & 31;
-    const int64_t nw = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
-    for (int64_t L0 = ((static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5) << 5; L0 < leaves;
-         L0 += nw << 5) {
-        unsigned m = __ballot_sync(0xffffffffu, L0 + lane < leaves && redo[L0 + lane] != 0u);
-        while (m) {
-            const int64_t L = L0 + (__ffs(m) - 1);
-            m &= m - 1;
-            const double f = dleaf[L];
-            double *row = out + (L << kBigLeafN);
-            for (int e = lane; e < (1 << kBigLeafN); e += 32) row[e] *= f;
-        }
-    }
-}
-
 // One CTA per matrix: the upper-level corrections, deepest level first:
 // for the kept child of node (l, i), every T in its range and every U,
 // out[T, U] -= C out[T - span, U], span = 2^(H-1-l), C = sign(p) Cm; the
@@ -271,15 +251,8 @@ int launch_fpm_big(const double *A, int n, int64_t batch, double *minors, double
     err = static_cast<int>(cudaGetLastError());
     if (err) return err;
     // the leaves: 12 x 12 matrices in the order of T, their minors into the rows
-    uint32_t *redo = nullptr;
-    err = launch_fpm_warp(src, kBigLeafN, batch << H, minors, thr, shf, lstat, leafws, s, det[H & 1], &redo, an,
-                          H);
+    err = launch_fpm_warp(src, kBigLeafN, batch << H, minors, thr, shf, lstat, leafws, s, det[H & 1], an, H);
     if (err) return err;
-    {
-        const int64_t fb = ((batch << H) + 255) >> 8;  // blocks of 256 flags
-        big_scale_redo_kernel<<<static_cast<int>(fb < 1216 ? fb : 1216), 256, 0, s>>>(minors, batch << H, redo,
-                                                                                       det[H & 1]);
-    }
     big_backprop_kernel<<<static_cast<unsigned>(batch), 512, 0, s>>>(minors, n, H, ccount, clog, Cm, flags);
     big_status_kernel<<<static_cast<unsigned>(batch), 512, 0, s>>>(minors, n, H, flags, lstat, status);
     return static_cast<int>(cudaGetLastError());

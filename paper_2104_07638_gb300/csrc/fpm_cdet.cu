@@ -288,9 +288,10 @@ __device__ __forceinline__ void bottom43(const double *__restrict__ w, double *M
     }
 }
 
-// All principal minors of the n x n matrix Ag into MA[0 .. 2^n), MC as scratch.
+// All principal minors of the n x n matrix Ag, times root (the minor of the
+// empty set), into MA[0 .. 2^n), MC as scratch.
 __device__ __forceinline__ void fpm_tree(const double *__restrict__ Ag, int n, double *MA, double *MC, double thr,
-                         double shift, CdetSmemHdr &h) {
+                         double shift, CdetSmemHdr &h, double root = 1.0) {
     const int tid = threadIdx.x, T = blockDim.x;
     const int L = n > 4 ? n - 4 : 0;
     double *const bufA = MA + (1 << L);
@@ -305,7 +306,7 @@ __device__ __forceinline__ void fpm_tree(const double *__restrict__ Ag, int n, d
             W0[t] = (r < n && q < n) ? __ldg(Ag + r * n + q) : (r == q ? 1.0 : 0.0);
         }
     }
-    if (tid == 0) MA[0] = 1.0;
+    if (tid == 0) MA[0] = root;
     __syncthreads();
     for (int l = 0; l < L; ++l) {
         const int s = n - l, s1 = s - 1, ss = s * s, ss1 = s1 * s1, P = 1 << l;
@@ -513,7 +514,7 @@ __device__ __forceinline__ void cdet_item(const CdetArgs &p, int n, const double
                                           const double *ain, double *mo, double *co, uint32_t *st,
                                           double *MA, double *MC, double *MU, bool in_smem,
                                           unsigned long long gsel, unsigned long long gsel_b, double *blk,
-                                          CdetSmemHdr &h, const double *anorm_over) {
+                                          CdetSmemHdr &h, const double *anorm_over, double root) {
     const int tid = threadIdx.x;
     const int N = 1 << n;
     if (tid == 0) bulk_wait_read();  // the previous item's bulk stores have read their source
@@ -534,7 +535,7 @@ __device__ __forceinline__ void cdet_item(const CdetArgs &p, int n, const double
             __syncthreads();
         }
         matrix_norm(Au, n, h, anorm_over);
-        fpm_tree(Au, n, MA, MC, p.piv_thr * h.anorm, p.piv_shift * h.anorm, h);
+        fpm_tree(Au, n, MA, MC, p.piv_thr * h.anorm, p.piv_shift * h.anorm, h, root);
         if (mo) {
             if (in_smem) {
                 if (tid == 0) {
@@ -596,7 +597,8 @@ __global__ void __launch_bounds__(kCdetThreads, 3) fpm_cdet_kernel(const CdetKer
                   p.a_in ? p.a_in + b * N : nullptr,
                   p.minors_out ? p.minors_out + b * (p.two_mats ? 2 * N : N) : nullptr,
                   p.c_out ? p.c_out + b * N : nullptr, p.status ? p.status + b : nullptr, MA, MC, MU,
-                  kSmemArrays, P.gsel, P.gsel_b, sbase, h, p.anorm_in ? p.anorm_in + (b >> p.anorm_shift) : nullptr);
+                  kSmemArrays, P.gsel, P.gsel_b, sbase, h, p.anorm_in ? p.anorm_in + (b >> p.anorm_shift) : nullptr,
+                  p.pre ? p.pre[b] : 1.0);
     };
     if (p.redo_list) {
         // only the matrices the warp-per-matrix minors kernel flagged (usually none)
@@ -642,7 +644,7 @@ __global__ void __launch_bounds__(kCdetThreads, 3) fpm_cdet_varlen_kernel(const 
                   p.a_in ? p.a_in + co : nullptr,
                   p.minors_out ? p.minors_out + (p.two_mats ? 2 * co : co) : nullptr,
                   p.c_out ? p.c_out + co : nullptr, p.status ? p.status + b : nullptr, MA, MC, MU, in_smem,
-                  gsel_s[n], gsel_s[kBlkB], sbase, h, nullptr);
+                  gsel_s[n], gsel_s[kBlkB], sbase, h, nullptr, 1.0);
     }
     if (threadIdx.x == 0) bulk_wait_all();
 }

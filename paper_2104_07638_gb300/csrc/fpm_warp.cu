@@ -77,14 +77,16 @@ __host__ __device__ constexpr size_t fw_stack_entries(int n) {
     return t;
 }
 
-// 1/p for a pivot (flags a zero or non-finite one) and whether |p| <= thrA
+// 1/p for a pivot; fl gets 1 for a zero or non-finite one and where |p| <= thrA
 // (thrA >= 0), tested on the high words in integer arithmetic (off the FP64
 // pipe): it also flags pivots up to 2^-20 (relative) above thrA, which only
-// sends such a matrix to the fused kernel, whose own test is exact.
-__device__ __forceinline__ double fw_inv(double p, double thrA, int &bad, int &small) {
+// sends such a matrix to the fused kernel, whose own test is exact. One flag
+// for both (the caller only needs to know whether to redo the matrix) keeps
+// the order-7 lane subtree within 255 registers without a spill.
+__device__ __forceinline__ double fw_inv(double p, double thrA, int &fl) {
     const long long bits = __double_as_longlong(p);
-    if ((bits << 1) == 0 || ((bits >> 52) & 0x7ff) == 0x7ff) bad = 1;
-    small |= (static_cast<unsigned>(__double2hiint(p)) & 0x7fffffffu) <= static_cast<unsigned>(__double2hiint(thrA));
+    fl |= ((bits << 1) == 0) | (((bits >> 52) & 0x7ff) == 0x7ff) |
+          ((static_cast<unsigned>(__double2hiint(p)) & 0x7fffffffu) <= static_cast<unsigned>(__double2hiint(thrA)));
     return rcp_nr(p);
 }
 
@@ -92,13 +94,13 @@ __device__ __forceinline__ double fw_inv(double p, double thrA, int &bad, int &s
 // cur give 2^(J+1) children of size k-1 in nxt.
 template <int T, int J>
 __device__ __forceinline__ void fw_tail_level(const double *cur, double *nxt, FwWarpSmem &w, int lane, double thrA,
-                                              int &bad, int &small) {
+                                              int &fl) {
     constexpr int k = T - J, k1 = k - 1, kk = k * k, kk1 = k1 * k1, nodes = 1 << J;
     const double *ndc = w.nd[J & 1];
     double *ndn = w.nd[(J + 1) & 1];
     if (lane < nodes) {
         const double p = cur[lane * kk + k1 * k + k1];
-        w.inv[lane] = fw_inv(p, thrA, bad, small);
+        w.inv[lane] = fw_inv(p, thrA, fl);
         ndn[2 * lane] = ndc[lane];
         ndn[2 * lane + 1] = ndc[lane] * p;
     }
@@ -141,14 +143,13 @@ __device__ __forceinline__ void fw_cf3(const double (&C)[3][3], double d, double
 // out[0 .. 2^K): the last element's pivot gives the kept child (the Schur
 // complement) at out + 2^(K-1), the leading block the dropped one at out.
 template <int K>
-__device__ __forceinline__ void fw_lane_tree(const double (&M)[K][K], double d, double *out, double thrA, int &bad,
-                                             int &small) {
+__device__ __forceinline__ void fw_lane_tree(const double (&M)[K][K], double d, double *out, double thrA, int &fl) {
     if constexpr (K == 3) {
         fw_cf3(M, d, out);
     } else {
         constexpr int K1 = K - 1;
         const double p = M[K1][K1];
-        const double iv = fw_inv(p, thrA, bad, small);
+        const double iv = fw_inv(p, thrA, fl);
         double S[K1][K1];
 #pragma unroll
         for (int r = 0; r < K1; ++r) {
@@ -156,13 +157,13 @@ __device__ __forceinline__ void fw_lane_tree(const double (&M)[K][K], double d, 
 #pragma unroll
             for (int q = 0; q < K1; ++q) S[r][q] = fma(-f, M[K1][q], M[r][q]);
         }
-        fw_lane_tree<K1>(S, d * p, out + (1 << K1), thrA, bad, small);
+        fw_lane_tree<K1>(S, d * p, out + (1 << K1), thrA, fl);
         double Lb[K1][K1];
 #pragma unroll
         for (int r = 0; r < K1; ++r)
 #pragma unroll
             for (int q = 0; q < K1; ++q) Lb[r][q] = M[r][q];
-        fw_lane_tree<K1>(Lb, d, out, thrA, bad, small);
+        fw_lane_tree<K1>(Lb, d, out, thrA, fl);
     }
 }
 
@@ -170,11 +171,10 @@ __device__ __forceinline__ void fw_lane_tree(const double (&M)[K][K], double d, 
 // its kept child is formed in registers; its dropped child, the leading block,
 // is read again from shared memory, so that the two need not be live at once.
 template <int K>
-__device__ __forceinline__ void fw_lane_root(const double *P, double d, double *out, double thrA, int &bad,
-                                             int &small) {
+__device__ __forceinline__ void fw_lane_root(const double *P, double d, double *out, double thrA, int &fl) {
     constexpr int K1 = K - 1;
     const double p = P[K1 * K + K1];
-    const double iv = fw_inv(p, thrA, bad, small);
+    const double iv = fw_inv(p, thrA, fl);
     {
         double S[K1][K1];
 #pragma unroll
@@ -183,32 +183,32 @@ __device__ __forceinline__ void fw_lane_root(const double *P, double d, double *
 #pragma unroll
             for (int q = 0; q < K1; ++q) S[r][q] = fma(-f, P[K1 * K + q], P[r * K + q]);
         }
-        fw_lane_tree<K1>(S, d * p, out + (1 << K1), thrA, bad, small);
+        fw_lane_tree<K1>(S, d * p, out + (1 << K1), thrA, fl);
     }
     double Lb[K1][K1];
 #pragma unroll
     for (int r = 0; r < K1; ++r)
 #pragma unroll
         for (int q = 0; q < K1; ++q) Lb[r][q] = P[r * K + q];
-    fw_lane_tree<K1>(Lb, d, out, thrA, bad, small);
+    fw_lane_tree<K1>(Lb, d, out, thrA, fl);
 }
 
 template <int T, int J>
 __device__ __forceinline__ void fw_tail_levels(double *cur, double *nxt, double *out, FwWarpSmem &w, int lane,
-                                               double thrA, int &bad, int &small) {
+                                               double thrA, int &fl) {
     if constexpr (J < kFwBfs) {
-        fw_tail_level<T, J>(cur, nxt, w, lane, thrA, bad, small);
-        fw_tail_levels<T, J + 1>(nxt, cur, out, w, lane, thrA, bad, small);
+        fw_tail_level<T, J>(cur, nxt, w, lane, thrA, fl);
+        fw_tail_levels<T, J + 1>(nxt, cur, out, w, lane, thrA, fl);
     } else {
         constexpr int L = T - kFwBfs;
-        fw_lane_root<L>(cur + lane * L * L, w.nd[J & 1][lane], out + (lane << L), thrA, bad, small);
+        fw_lane_root<L>(cur + lane * L * L, w.nd[J & 1][lane], out + (lane << L), thrA, fl);
     }
 }
 
 // The tail of T elements whose root matrix is in w.bufE (node minor w.nd[0][0]).
 template <int T>
-__device__ __forceinline__ void fw_tail(double *out, FwWarpSmem &w, int lane, double thrA, int &bad, int &small) {
-    fw_tail_levels<T, 0>(w.bufE, w.bufO, out, w, lane, thrA, bad, small);
+__device__ __forceinline__ void fw_tail(double *out, FwWarpSmem &w, int lane, double thrA, int &fl) {
+    fw_tail_levels<T, 0>(w.bufE, w.bufO, out, w, lane, thrA, fl);
 }
 
 // One matrix of order n (9..16), whole warp: its 2^n minors, each times pre,
@@ -219,16 +219,22 @@ template <int T>
 __device__ __forceinline__ int fw_matrix(const double *A, int n, double *out, double thr, double pre,
                                          const double *anorm, double *stack, FwWarpSmem &w, int lane) {
     const int D = n - T;
-    int bad = 0, small = 0, nonfin = 0;
-    double amax = 0.0;
+    int fl = 0, nonfin = 0;
+    // ||A||max and the finiteness test on the bit patterns of |x| (integer
+    // order is the order of non-negative doubles), off the FP64 pipe
+    unsigned long long am = 0;
     for (int e = lane; e < n * n; e += 32) {
-        const double x = A[e];
-        if (!isfinite(x)) nonfin = 1;
-        amax = fmax(amax, fabs(x));
+        const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(A[e])) & 0x7fffffffffffffffull;
+        nonfin |= b >= 0x7ff0000000000000ull;
+        am = b > am ? b : am;
     }
     nonfin = __any_sync(0xffffffffu, nonfin);
     if (nonfin) return 1;
-    for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long y = __shfl_xor_sync(0xffffffffu, am, o);
+        am = y > am ? y : am;
+    }
+    double amax = __longlong_as_double(static_cast<long long>(am));
     if (anorm) amax = *anorm;
     const double thrA = thr * (amax > 0.0 ? amax : 1.0);
     if (lane == 0) {
@@ -252,7 +258,7 @@ __device__ __forceinline__ int fw_matrix(const double *A, int n, double *out, do
             }
             if (keep) {
                 const double piv = P[k1 * st + k1];
-                const double iv = fw_inv(piv, thrA, bad, small);
+                const double iv = fw_inv(piv, thrA, fl);
                 for (int r = lane; r < k1; r += 32) w.f[r] = P[r * st + k1] * iv;
                 __syncwarp();
                 for (int e = lane; e < k1 * k1; e += 32) {
@@ -285,14 +291,14 @@ __device__ __forceinline__ int fw_matrix(const double *A, int n, double *out, do
         }
         if (lane == 0) w.nd[0][0] = w.pdet[D];
         __syncwarp();
-        fw_tail<T>(out + (t << T), w, lane, thrA, bad, small);
+        fw_tail<T>(out + (t << T), w, lane, thrA, fl);
         __syncwarp();
     }
-    return __any_sync(0xffffffffu, bad | small);
+    return __any_sync(0xffffffffu, fl);
 }
 
-// Every matrix; redo[b] = 1 where the fused kernel must compute it again, and
-// then b is appended to redo_list (*redo_count entries, zeroed before). pre
+// Every matrix; b is appended to redo_list (*redo_count entries, zeroed
+// before) where the fused kernel must compute it again. pre
 // (or NULL for 1): a factor per matrix on all its minors; anorm (or NULL): the
 // scale of the threshold, anorm[b >> anorm_shift], in place of the matrix's own
 // ||A||max (the leaves of a larger matrix take its norm). T = min(n, 12), one
@@ -302,7 +308,7 @@ __device__ __forceinline__ int fw_matrix(const double *A, int n, double *out, do
 template <int T>
 __global__ void __launch_bounds__(kFwWarps * 32, 2) fpm_warp_kernel(const double *__restrict__ A, int n,
                                                                   int64_t batch, double *minors, double thr,
-                                                                  const double *__restrict__ pre, uint32_t *redo,
+                                                                  const double *__restrict__ pre,
                                                                   uint32_t *redo_list, unsigned *redo_count,
                                                                   uint32_t *status, double *stack_base,
                                                                   size_t stack_per_warp,
@@ -319,15 +325,14 @@ __global__ void __launch_bounds__(kFwWarps * 32, 2) fpm_warp_kernel(const double
         const int r = fw_matrix<T>(A + b * nn, n, minors + b * N, thr, pre ? pre[b] : 1.0,
                                    anorm ? anorm + (b >> anorm_shift) : nullptr, stack, w, lane);
         if (lane == 0) {
-            redo[b] = static_cast<uint32_t>(r);
             if (r) redo_list[atomicAdd(redo_count, 1u)] = static_cast<uint32_t>(b);
             if (status && !r) status[b] = 0u;
         }
     }
 }
 
-using FwKernel = void (*)(const double *, int, int64_t, double *, double, const double *, uint32_t *, uint32_t *,
-                         unsigned *, uint32_t *, double *, size_t, const double *, int);
+using FwKernel = void (*)(const double *, int, int64_t, double *, double, const double *, uint32_t *, unsigned *,
+                         uint32_t *, double *, size_t, const double *, int);
 static FwKernel fw_kernel_for(int n) {
     switch (n < kFwTail ? n : kFwTail) {
         case 9: return fpm_warp_kernel<9>;
@@ -358,11 +363,11 @@ static int fpm_warp_grid(int n, int64_t batch, int *err) {
     return static_cast<int>(g < 1 ? 1 : g);
 }
 
-// Workspace: per resident warp the depth-first stack, one redo flag per
-// matrix, the redo list (a counter, then up to one entry per matrix), and for
-// n > 12 the fused kernel's global scratch (its redo launch).
+// Workspace: per resident warp the depth-first stack, the redo list (a
+// counter, then up to one entry per matrix), and for n > 12 the fused kernel's
+// global scratch (its redo launch).
 struct FwPlan {
-    size_t stack, redo, list, fused, total;
+    size_t stack, list, fused, total;
 };
 static int fw_plan(int n, int64_t batch, FwPlan *p, int *grid) {
     int err = 0;
@@ -370,7 +375,6 @@ static int fw_plan(int n, int64_t batch, FwPlan *p, int *grid) {
     if (err) return err;
     auto al = [](size_t x) { return (x + 255) & ~static_cast<size_t>(255); };
     p->stack = al(static_cast<size_t>(*grid) * kFwWarps * fw_stack_entries(n) * sizeof(double));
-    p->redo = al(static_cast<size_t>(batch) * sizeof(uint32_t));
     p->list = 256 + al(static_cast<size_t>(batch) * sizeof(uint32_t));
     p->fused = 0;
     if (n > cdet_smem_max_n(false)) {
@@ -378,7 +382,7 @@ static int fw_plan(int n, int64_t batch, FwPlan *p, int *grid) {
         if (err) return err;
         p->fused = al(static_cast<size_t>(g) * cdet_slot_doubles(n) * sizeof(double));
     }
-    p->total = p->stack + p->redo + p->list + p->fused;
+    p->total = p->stack + p->list + p->fused;
     return 0;
 }
 
@@ -392,7 +396,7 @@ size_t fpm_warp_workspace_bytes(int n, int64_t batch, int *err) {
 }
 
 int launch_fpm_warp(const double *A, int n, int64_t batch, double *minors, double thr, double shf,
-                    uint32_t *status, void *workspace, cudaStream_t s, const double *pre, uint32_t **redo_out,
+                    uint32_t *status, void *workspace, cudaStream_t s, const double *pre,
                     const double *anorm_in, int anorm_shift) {
     FwPlan plan;
     int grid = 0;
@@ -402,19 +406,17 @@ int launch_fpm_warp(const double *A, int n, int64_t batch, double *minors, doubl
     const size_t per = fw_stack_entries(n);
     char *ws = static_cast<char *>(workspace);
     double *stack = per ? reinterpret_cast<double *>(ws) : nullptr;
-    uint32_t *redo = reinterpret_cast<uint32_t *>(ws + plan.stack);
-    unsigned *count = reinterpret_cast<unsigned *>(ws + plan.stack + plan.redo);
-    uint32_t *list = reinterpret_cast<uint32_t *>(ws + plan.stack + plan.redo + 256);
-    double *fused = plan.fused ? reinterpret_cast<double *>(ws + plan.stack + plan.redo + plan.list) : nullptr;
-    if (redo_out) *redo_out = redo;
+    unsigned *count = reinterpret_cast<unsigned *>(ws + plan.stack);
+    uint32_t *list = reinterpret_cast<uint32_t *>(ws + plan.stack + 256);
+    double *fused = plan.fused ? reinterpret_cast<double *>(ws + plan.stack + plan.list) : nullptr;
     err = static_cast<int>(cudaMemsetAsync(count, 0, sizeof(unsigned), s));
     if (err) return err;
-    fw_kernel_for(n)<<<grid, kFwWarps * 32, smem, s>>>(A, n, batch, minors, thr, pre, redo, list, count, status,
-                                                        stack, per, anorm_in, anorm_shift);
+    fw_kernel_for(n)<<<grid, kFwWarps * 32, smem, s>>>(A, n, batch, minors, thr, pre, list, count, status, stack,
+                                                        per, anorm_in, anorm_shift);
     err = static_cast<int>(cudaGetLastError());
     if (err) return err;
     // the flagged matrices again, by the fused kernel with the pivot correction
-    // (without the factor pre: the caller scales those rows)
+    // (pre as the root minor of their trees too)
     CdetArgs a = {};
     a.A_up = A;
     a.minors_out = minors;
@@ -429,6 +431,7 @@ int launch_fpm_warp(const double *A, int n, int64_t batch, double *minors, doubl
     a.gscratch = fused;
     a.anorm_in = anorm_in;
     a.anorm_shift = anorm_shift;
+    a.pre = pre;
     return launch_fpm_cdet(a, s);
 }
 
