@@ -138,24 +138,27 @@ __device__ __forceinline__ void fsc_butterfly_high(double *T, int lg, int n, boo
 }
 
 // M_1..M_n (M_k = k L_k, L = log Z) of tile entry t in place of Z_1..Z_n,
-// for a mask with at most X elements (Z_m = 0 for m > X; X <= n)
+// for a mask with at most X elements (Z_m = 0 for m > X; X <= n). The Z_m
+// are read from the tile as they are needed and the M_k kept in registers,
+// then stored together, which keeps the kernel within the registers of three
+// CTAs per SM without a spill.
 template <int X>
 __device__ __forceinline__ void fsc_log_entry(double *T, int t, int n) {
-    double Z[X + 1], M[kFscMaxN + 1];
-#pragma unroll
-    for (int m = 1; m <= X; ++m) Z[m] = m <= n ? T[(m - 1) * kFscTile + t] : 0.0;  // no mask has more than n
+    double M[kFscMaxN + 1];
 #pragma unroll
     for (int k = 1; k <= kFscMaxN; ++k) {
         if (k <= n) {
             double s = 0.0;
-            if (k <= X) s = static_cast<double>(k) * Z[k];
+            if (k <= X) s = static_cast<double>(k) * T[(k - 1) * kFscTile + t];
 #pragma unroll
             for (int m = 1; m < kFscMaxN; ++m)
-                if (m < k && m <= X) s = fma(-Z[m], M[k - m], s);
+                if (m < k && m <= X) s = fma(-T[(m - 1) * kFscTile + t], M[k - m], s);
             M[k] = s;
-            T[(k - 1) * kFscTile + t] = s;
         }
     }
+#pragma unroll
+    for (int k = 1; k <= kFscMaxN; ++k)
+        if (k <= n) T[(k - 1) * kFscTile + t] = M[k];
 }
 
 // the logarithm for the tile entries order[i] (i < nx; identity when order is

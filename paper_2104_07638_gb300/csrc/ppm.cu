@@ -511,13 +511,13 @@ __global__ void __launch_bounds__(kPpmWarps * 32, 3) ppm_kernel(const double *__
                 const int highmask = freeH & ~lowmask;
                 const int fh = f - m;
                 // path of alpha vectors over the inner (lowest four) remaining
-                // free elements; a0 restarts from the base for each outer block
-                double b0[4], a0[4], a1[4], a2[4], a3[4], a4[4];
+                // free elements; a0 restarts for each outer block (n >= 15 only)
+                // as the product over T_H, R_w and the block's outer elements
+                double a0[4], a1[4], a2[4], a3[4], a4[4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const int TL = lane + 32 * k;
-                    b0[k] = TL < NL ? alpha[TL] : 0.0;
-                    a0[k] = b0[k];
+                    a0[k] = TL < NL ? alpha[TL] : 0.0;
                     a1[k] = a2[k] = a3[k] = a4[k] = 0.0;
                 }
                 for (int j = 0; j < (1 << fh); ++j) {
@@ -526,14 +526,9 @@ __global__ void __launch_bounds__(kPpmWarps * 32, 3) ppm_kernel(const double *__
                         // new outer block: base times the outer elements of j
                         const int outer = pdep_dev(j, highmask) & ~pdep_dev(15, highmask);
 #pragma unroll
-                        for (int k = 0; k < 4; ++k) a0[k] = b0[k];
-                        for (int r = outer; r; r &= r - 1) {
-                            const int el = __ffs(r) - 1;
-#pragma unroll
-                            for (int k = 0; k < 4; ++k) {
-                                const int TL = lane + 32 * k;
-                                if (TL < NL) a0[k] *= sm.U[(l + el) * 128 + TL];
-                            }
+                        for (int k = 0; k < 4; ++k) {
+                            const int TL = lane + 32 * k;
+                            if (TL < NL) a0[k] = set_prod(sm.U, l, TH | Rw | outer, TL);
                         }
                     }
                     if (p > 0) {
