@@ -402,6 +402,9 @@ def measure_rows(args, dev, peak):
     G = torch.as_tensor(inputs.hubbard_g0_table()).to(dev)
     W, T = 16384, args.mc_steps
     walkers, feats, targs = {}, [], []
+    # untimed warm-up of the collection path on throwaway walkers (the first
+    # use of some kernels in a process loads them)
+    mc.Walkers(1024, 10, G, inputs.HUB_WIN, inputs.HUB_MTAU, seed=99).collect(2)
     t_collect = 0.0
     for n in range(10, 15):
         wk = mc.Walkers(W, n, G, inputs.HUB_WIN, inputs.HUB_MTAU, seed=100 + n)

@@ -277,10 +277,14 @@ class Walkers:
         t = torch.cat(targets)
         # clip the far lower tail (near-cancelling configurations) for the
         # regression; a non-finite target (a matrix the kernel flagged, e.g. a
-        # correction-log overflow) gets the same clip value
-        lo = torch.nanquantile(t[:min(t.numel(), 1 << 20)], 0.01)
-        t = torch.where(torch.isfinite(t), t, lo)
-        return F, torch.maximum(t, lo)
+        # correction-log overflow) gets the same clip value. The 1 % quantile
+        # is taken on the host (a few MB): the device sort behind a quantile
+        # costs seconds on its first use in a process
+        th = t[:min(t.numel(), 1 << 20)].cpu().numpy()
+        fin = th[np.isfinite(th)]
+        lo = float(np.quantile(fin, 0.01)) if fin.size else 0.0
+        t = torch.where(torch.isfinite(t), t, torch.full_like(t, lo))
+        return F, t.clamp_min(lo)
 
 
 def integrated_autocorr(series: np.ndarray, c: float = 5.0) -> float:
