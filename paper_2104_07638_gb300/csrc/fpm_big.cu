@@ -41,11 +41,15 @@ namespace apm {
 constexpr int kBigLeafN = 12;
 constexpr int kBigCorrCap = 256;  // upper-level corrections recorded per matrix
 constexpr int kBigThreads = 256;
+constexpr int kBigSubThreads = 512;
 
-// Workspace parts (bytes, each a multiple of 256).
+// Workspace parts (bytes, each a multiple of 256). The upper levels run in two
+// launches: levels 0 .. s1-1 (s1 = H/2) for each matrix, then levels
+// s1 .. H-1 for each node of level s1; nodeM holds the nodes of level s1 and
+// nodeL the leaves (level H).
 struct BigPlan {
-    int H;
-    size_t thr, cm, an, flags, ccount, clog, det, nodeE, nodeO, lstat, leafws, total;
+    int H, s1;
+    size_t thr, cm, an, flags, ccount, clog, det, nodeM, nodeL, lstat, leafws, total;
 };
 
 static size_t big_align(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
@@ -53,13 +57,8 @@ static size_t big_align(size_t x) { return (x + 255) & ~static_cast<size_t>(255)
 static int big_plan(int n, int64_t batch, BigPlan *p) {
     const size_t b = static_cast<size_t>(batch);
     p->H = n - kBigLeafN;
-    size_t e = 0, o = 0;
-    for (int l = 1; l <= p->H; ++l) {
-        const size_t k = static_cast<size_t>(n - l);
-        const size_t sz = b * (static_cast<size_t>(1) << l) * k * k * sizeof(double);
-        if (l & 1) o = o > sz ? o : sz;
-        else e = e > sz ? e : sz;
-    }
+    p->s1 = p->H / 2;
+    const size_t km = static_cast<size_t>(n - p->s1);
     p->thr = big_align(b * sizeof(double));
     p->cm = p->thr;
     p->an = p->thr;
@@ -67,12 +66,12 @@ static int big_plan(int n, int64_t batch, BigPlan *p) {
     p->ccount = big_align(b * sizeof(int));
     p->clog = big_align(b * kBigCorrCap * 2 * sizeof(double));
     p->det = big_align(b * (static_cast<size_t>(1) << p->H) * sizeof(double));
-    p->nodeE = big_align(e);
-    p->nodeO = big_align(o);
+    p->nodeM = big_align(b * (static_cast<size_t>(1) << p->s1) * km * km * sizeof(double));
+    p->nodeL = big_align(b * (static_cast<size_t>(1) << p->H) * kBigLeafN * kBigLeafN * sizeof(double));
     p->lstat = big_align(b * (static_cast<size_t>(1) << p->H) * sizeof(uint32_t));
     int err = 0;
     p->leafws = big_align(fpm_warp_workspace_bytes(kBigLeafN, batch << p->H, &err));
-    p->total = p->thr + p->cm + p->an + p->flags + p->ccount + p->clog + 2 * p->det + p->nodeE + p->nodeO + p->lstat +
+    p->total = p->thr + p->cm + p->an + p->flags + p->ccount + p->clog + 2 * p->det + p->nodeM + p->nodeL + p->lstat +
                p->leafws;
     return err;
 }
@@ -114,47 +113,104 @@ __global__ void big_prep_kernel(const double *__restrict__ A, int n, int64_t bat
     }
 }
 
-// Level l: one warp per node (matrix b, index i), node = src + (b 2^l + i) k^2,
-// k = n - l; children 2i (drop the last element) and 2i+1 (keep it).
-__global__ void big_level_kernel(const double *__restrict__ src, double *__restrict__ dst,
-                                 const double *__restrict__ dsrc, double *__restrict__ ddst, int n, int l,
-                                 int64_t batch, const double *__restrict__ thrA, const double *__restrict__ Cm,
-                                 int *ccount, double *clog, uint32_t *flags) {
-    const int lane = threadIdx.x & 31;
-    const int64_t w = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    if (w >= (batch << l)) return;  // whole warps only: blockDim is a multiple of 32
-    const int64_t b = w >> l;
-    const int k = n - l, k1 = k - 1;
-    const double *M = src + w * k * k;
-    double *D0 = dst + 2 * w * k1 * k1;
-    double *D1 = D0 + static_cast<int64_t>(k1) * k1;
-    const double p = M[k1 * k + k1];
-    const double C = fabs(p) <= thrA[b] ? (p >= 0.0 ? Cm[b] : -Cm[b]) : 0.0;
-    const double pp = p + C;
-    const double ip = 1.0 / pp;
-    for (int e = lane; e < k1 * k1; e += 32) {
-        const int r = e / k1, q = e - r * k1;
-        const double v = M[r * k + q];
-        D0[e] = v;
-        D1[e] = fma(-M[r * k + k1] * ip, M[k1 * k + q], v);
+// Shared-memory layout of a subtree launch over levels ls .. ls+nl-1 (k0 =
+// n - ls): the even and odd relative levels alternate between two buffers
+// (level j holds 2^j nodes of k0 - j squared entries), then the reciprocal
+// pivots of one level and the node minors of the current and the next level.
+struct BigSubLayout {
+    size_t odd, ip, nd, bytes;
+};
+static BigSubLayout big_sub_layout(int n, int ls, int nl) {
+    const int k0 = n - ls;
+    size_t e = 0, o = 0;
+    for (int j = 0; j < nl; ++j) {
+        const size_t sz = (static_cast<size_t>(1) << j) * (k0 - j) * (k0 - j);
+        if (j & 1) o = o > sz ? o : sz;
+        else e = e > sz ? e : sz;
     }
-    if (lane == 0) {
-        const double d = dsrc[w];
-        ddst[2 * w] = d;
-        ddst[2 * w + 1] = d * pp;
-        const long long bits = __double_as_longlong(pp);
-        if ((bits << 1) == 0 || ((bits >> 52) & 0x7ff) == 0x7ff) atomicOr(&flags[b], APM_ST_ZERO_PIVOT);
-        if (C != 0.0) {
-            const int pos = atomicAdd(&ccount[b], 1);
-            if (pos < kBigCorrCap) {
-                const int64_t i = w - (b << l);
-                clog[(b * kBigCorrCap + pos) * 2] = static_cast<double>(l) + 32.0 * static_cast<double>(i);
-                clog[(b * kBigCorrCap + pos) * 2 + 1] = p;
+    BigSubLayout L;
+    L.odd = e;
+    L.ip = e + o;
+    L.nd = L.ip + (static_cast<size_t>(1) << (nl - 1));
+    L.bytes = (L.nd + 2 * (static_cast<size_t>(1) << nl)) * sizeof(double);
+    return L;
+}
+
+// One CTA per node of level ls (global index w0 = b 2^ls + i0; for ls = 0 the
+// matrix itself): its subtree's levels ls .. ls+nl-1 breadth first in shared
+// memory, and the nodes of level ls+nl with their minors written out. Node
+// (l, i) of matrix b has global index b 2^l + i and children 2i (drop the
+// node's last element: its leading block) and 2i+1 (keep it: the leading
+// block less the rank-1 term of the last row and column over the pivot, the
+// pivot shifted by C = sign(p) Cm where |p| <= thrA and recorded with its
+// unshifted value).
+__global__ void __launch_bounds__(kBigSubThreads) big_subtree_kernel(
+    const double *__restrict__ src, const double *__restrict__ dsrc, double *__restrict__ dst,
+    double *__restrict__ ddst, int n, int ls, int nl, size_t off_odd, size_t off_ip, size_t off_nd,
+    const double *__restrict__ thrA, const double *__restrict__ Cm, int *ccount, double *clog, uint32_t *flags) {
+    extern __shared__ __align__(16) double sm[];
+    const int tid = threadIdx.x, T = blockDim.x;
+    const int64_t w0 = blockIdx.x;
+    const int64_t b = w0 >> ls;
+    const int k0 = n - ls;
+    double *const IP = sm + off_ip;
+    double *const ND = sm + off_nd;
+    const double *R = src + w0 * k0 * k0;
+    for (int e = tid; e < k0 * k0; e += T) sm[e] = R[e];
+    if (tid == 0) ND[0] = dsrc[w0];
+    __syncthreads();
+    const double thr = thrA[b], cm = Cm[b];
+    for (int j = 0; j < nl; ++j) {
+        const int k = k0 - j, k1 = k - 1, kk = k * k, kk1 = k1 * k1, P = 1 << j, l = ls + j;
+        const bool last = j == nl - 1;
+        const double *cur = sm + ((j & 1) ? off_odd : 0);
+        double *nxt = sm + ((j & 1) ? 0 : off_odd);
+        const double *ndc = ND + ((j & 1) << nl);
+        double *ndn = ND + (((j + 1) & 1) << nl);
+        for (int t = tid; t < P; t += T) {
+            const int64_t wp = (w0 << j) + t;  // global index at level l
+            const double p = cur[t * kk + k1 * k + k1];
+            const double C = fabs(p) <= thr ? (p >= 0.0 ? cm : -cm) : 0.0;
+            const double pp = p + C;
+            IP[t] = 1.0 / pp;
+            const double d = ndc[t];
+            if (last) {
+                ddst[2 * wp] = d;
+                ddst[2 * wp + 1] = d * pp;
             } else {
-                atomicOr(&flags[b], APM_ST_CORRECTION_OVERFLOW);
+                ndn[2 * t] = d;
+                ndn[2 * t + 1] = d * pp;
             }
-            atomicOr(&flags[b], APM_ST_PIVOT_CORRECTED);
+            const long long bits = __double_as_longlong(pp);
+            if ((bits << 1) == 0 || ((bits >> 52) & 0x7ff) == 0x7ff) atomicOr(&flags[b], APM_ST_ZERO_PIVOT);
+            if (C != 0.0) {
+                const int pos = atomicAdd(&ccount[b], 1);
+                if (pos < kBigCorrCap) {
+                    const int64_t i = wp - (b << l);
+                    clog[(b * kBigCorrCap + pos) * 2] = static_cast<double>(l) + 32.0 * static_cast<double>(i);
+                    clog[(b * kBigCorrCap + pos) * 2 + 1] = p;
+                } else {
+                    atomicOr(&flags[b], APM_ST_CORRECTION_OVERFLOW);
+                }
+                atomicOr(&flags[b], APM_ST_PIVOT_CORRECTED);
+            }
         }
+        __syncthreads();
+        for (int e = tid; e < P * kk1; e += T) {
+            const int t = e / kk1, rem = e - t * kk1, r = rem / k1, q = rem - r * k1;
+            const double *M = cur + t * kk;
+            const double v = M[r * k + q];
+            const double v1 = fma(-M[r * k + k1] * IP[t], M[k1 * k + q], v);
+            if (last) {
+                double *D0 = dst + 2 * ((w0 << j) + t) * kk1;
+                D0[rem] = v;
+                D0[kk1 + rem] = v1;
+            } else {
+                nxt[(2 * t) * kk1 + rem] = v;
+                nxt[(2 * t + 1) * kk1 + rem] = v1;
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -230,8 +286,9 @@ int launch_fpm_big(const double *A, int n, int64_t batch, double *minors, double
     w += p.clog;
     double *det[2] = {reinterpret_cast<double *>(w), reinterpret_cast<double *>(w + p.det)};
     w += 2 * p.det;
-    double *node[2] = {reinterpret_cast<double *>(w), reinterpret_cast<double *>(w + p.nodeE)};
-    w += p.nodeE + p.nodeO;
+    double *nodeM = reinterpret_cast<double *>(w);
+    double *leaves = reinterpret_cast<double *>(w + p.nodeM);
+    w += p.nodeM + p.nodeL;
     uint32_t *lstat = reinterpret_cast<uint32_t *>(w);
     w += p.lstat;
     void *leafws = w;
@@ -239,19 +296,22 @@ int launch_fpm_big(const double *A, int n, int64_t batch, double *minors, double
     const int64_t warps0 = batch;
     big_prep_kernel<<<static_cast<unsigned>((warps0 * 32 + kBigThreads - 1) / kBigThreads), kBigThreads, 0, s>>>(
         A, n, batch, thr, shf, thrA, Cm, an, flags, ccount, det[0]);
-    const double *src = A;
-    for (int l = 0; l < H; ++l) {
-        const int64_t nodes = batch << l;
-        double *dst = node[(l + 1) & 1];
-        big_level_kernel<<<static_cast<unsigned>((nodes * 32 + kBigThreads - 1) / kBigThreads), kBigThreads, 0,
-                           s>>>(src, dst, det[l & 1], det[(l + 1) & 1], n, l, batch, thrA, Cm, ccount, clog,
-                                flags);
-        src = dst;
-    }
+    // levels 0 .. s1-1 for each matrix (det[0]: the roots' minors, 1), then
+    // levels s1 .. H-1 for each node of level s1; the leaves' minors in det[0]
+    const int s1 = p.s1, s2 = H - s1;
+    const BigSubLayout L1 = big_sub_layout(n, 0, s1), L2 = big_sub_layout(n, s1, s2);
+    err = static_cast<int>(cudaFuncSetAttribute(big_subtree_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                static_cast<int>(L1.bytes > L2.bytes ? L1.bytes : L2.bytes)));
+    if (err) return err;
+    big_subtree_kernel<<<static_cast<unsigned>(batch), kBigSubThreads, L1.bytes, s>>>(
+        A, det[0], nodeM, det[1], n, 0, s1, L1.odd, L1.ip, L1.nd, thrA, Cm, ccount, clog, flags);
+    big_subtree_kernel<<<static_cast<unsigned>(batch << s1), kBigSubThreads, L2.bytes, s>>>(
+        nodeM, det[1], leaves, det[0], n, s1, s2, L2.odd, L2.ip, L2.nd, thrA, Cm, ccount, clog, flags);
+    const double *src = leaves;
     err = static_cast<int>(cudaGetLastError());
     if (err) return err;
     // the leaves: 12 x 12 matrices in the order of T, their minors into the rows
-    err = launch_fpm_warp(src, kBigLeafN, batch << H, minors, thr, shf, lstat, leafws, s, det[H & 1], an, H);
+    err = launch_fpm_warp(src, kBigLeafN, batch << H, minors, thr, shf, lstat, leafws, s, det[0], an, H);
     if (err) return err;
     big_backprop_kernel<<<static_cast<unsigned>(batch), 512, 0, s>>>(minors, n, H, ccount, clog, Cm, flags);
     big_status_kernel<<<static_cast<unsigned>(batch), 512, 0, s>>>(minors, n, H, flags, lstat, status);
