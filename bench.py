@@ -11,7 +11,8 @@ Prints ONE JSON line (rank 0):
   value      minor-sets/s over all ranks, device-timed (inputs resident in HBM)
   e2e        the same metric through the public API from pinned host buffers,
              host->device copy of the inputs and device->host copy of minors and
-             c inside the timed region (32 chunks over 4 streams)
+             c inside the timed region (chunks of 2048 matrices over 4 streams,
+             the last two chunks' worth in halving pieces)
   roofline   FP64-ALU bound of the fused kernel (bound "alu")
   cpu_baseline  the CPU oracle (per-minor LU + plain recursion) on a bounded
              sample of the same workload, all host cores
@@ -755,9 +756,10 @@ def main():
     ms_per_step = 1000.0 * dev_s / args.steps
 
     # ---- end to end through the C ABI on host buffers (apm_cdet_connected_host) ----
-    # 32 chunks over 4 streams inside the library: the copies of one chunk
-    # overlap the kernels of the others, and only the last chunk's device->host
-    # copy is left exposed
+    # chunks of 2048 matrices over 4 streams inside the library: the copies of
+    # one chunk overlap the kernels of the others; the library cuts the last
+    # two chunks' worth into halving pieces, so that the device->host copy left
+    # exposed at the end is short
     chunks, nstreams = 32, 4
     cb = B // chunks
     A_host = torch.as_tensor(A_np).pin_memory()

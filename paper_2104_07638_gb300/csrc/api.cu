@@ -203,12 +203,19 @@ apm_status_t apm_cdet_connected_host(const double *A_up, const double *A_dn, int
         if (err != cudaSuccess) break;
         err = cudaStreamWaitEvent(ss[made], ready, 0);  // the caller's earlier work on the workspace
     }
-    const int64_t nchunks = (batch + chunk - 1) / chunk;
-    // chunk k goes to slot k % nstreams: a slot's buffers are reused only by
-    // chunks on its own stream, so stream order keeps them apart
-    for (int64_t k = 0; err == cudaSuccess && res == APM_OK && k < nchunks; ++k) {
+    // Pieces of `chunk` matrices while more than two chunks remain, then
+    // halving pieces down to chunk / 16: the copy-out of the last piece is the
+    // one part of the pipeline nothing overlaps, so it is kept short. Piece k
+    // goes to slot k % nstreams: a slot's buffers are reused only by pieces on
+    // its own stream, so stream order keeps them apart.
+    const int64_t min_piece = chunk / 16 > 0 ? chunk / 16 : 1;
+    int64_t b0 = 0;
+    for (int64_t k = 0; err == cudaSuccess && res == APM_OK && b0 < batch; ++k) {
         const int q = static_cast<int>(k % nstreams);
-        const int64_t b0 = k * chunk, cb = batch - b0 < chunk ? batch - b0 : chunk;
+        const int64_t rem = batch - b0;
+        int64_t cb = rem > 2 * chunk ? chunk : (rem + 1) / 2;
+        if (cb < min_piece || rem <= min_piece) cb = rem;
+        if (cb > chunk) cb = chunk;
         const size_t ub = static_cast<size_t>(b0), ucb = static_cast<size_t>(cb);
         char *base = static_cast<char *>(workspace) + static_cast<size_t>(q) * L.total;
         double *dA = reinterpret_cast<double *>(base);
@@ -230,6 +237,7 @@ apm_status_t apm_cdet_connected_host(const double *A_up, const double *A_dn, int
                                   cudaMemcpyDeviceToHost, ss[q]);
         if (err == cudaSuccess && status)
             err = cudaMemcpyAsync(status + ub, dst, ucb * sizeof(uint32_t), cudaMemcpyDeviceToHost, ss[q]);
+        b0 += cb;
     }
     for (int i = 0; i < made; ++i) {  // wait for everything issued, even after an error
         const cudaError_t e = cudaStreamSynchronize(ss[i]);
