@@ -165,10 +165,12 @@ apm_status_t apm_cdet_connected(const double *A_up, const double *A_dn, int n, i
  * apm_cdet_connected_host -- apm_cdet_connected (Section V.A, Eq. recursion:
  * the same arithmetic, bit for bit) on matrices and outputs in HOST memory. The
  * transfer pipeline has no counterpart in the paper: the batch is cut into
- * chunks of `chunk` matrices that go in turn to `nstreams` slots of the device
- * workspace, each with a stream the call creates; a slot copies its chunk in,
- * runs the kernels of apm_cdet_connected on it and copies the outputs back, so
- * the copies of one chunk overlap the kernels of the others. The kernels
+ * chunks of `chunk` matrices (the last two chunks' worth into halving pieces,
+ * down to chunk/16, so that the copy-out left exposed at the end is short)
+ * that go in turn to `nstreams` slots of the device workspace, each with a
+ * stream the call creates; a slot copies its chunk in, runs the kernels of
+ * apm_cdet_connected on it and copies the outputs back, so the copies of one
+ * chunk overlap the kernels of the others. The kernels
  * only ever touch device memory. The exceptions to the conventions at the top
  * of this header: A_up, A_dn, c, minors_out and status are host pointers (any
  * alignment), and the call is blocking.
