@@ -27,10 +27,12 @@
 //           high elements;
 //   pass C  per X_H: Mobius over the low elements for the ranks |X_H| ..
 //           |X_H| + 9 (the only ones read out) and c[X] = L_{|X|}(X).
-// Butterflies run one element at a time, and a warp skips a step when all its
-// pairs are known no-ops (zero sources in a zeta, targets that are never read
-// out in a Mobius); the pairs are visited in popcount order of their 8 other
-// elements in passes A and C, and of their high part in pass B, so that the
+// Butterflies run two elements at a time (a quad of entries per thread step,
+// the additions of the two single steps in their order), the last element of
+// an odd count alone; a warp skips a step when all its pairs are known no-ops
+// (zero sources in a zeta, targets that are never read out in a Mobius); the
+// pairs or quads are visited in popcount order of their other elements (of
+// the tile bits in passes A and C, of the high part in pass B), so that the
 // no-ops fall into whole warps: 39 % of the transforms' pair visits are
 // skipped at n = 16 (28 % in mask order). The butterfly loops are kept rolled,
 // which keeps the kernel within the registers of three CTAs per SM. The
@@ -72,11 +74,11 @@ __device__ __forceinline__ int binom_small(int m, int k) {
 // pairs of a step are visited in popcount order of their other 8 elements
 // (ord8), which puts the no-ops of both kinds mostly into whole warps.
 __device__ __forceinline__ void fsc_butterfly_low(double *T, int bits, int nr, int c0, bool mobius,
-                                                  const uint8_t *ord8) {
+                                                  const uint8_t *ord8, int d0 = 0) {
     const int half = 1 << (bits - 1);
     const bool prune = bits == kFscTileBits;
 #pragma unroll 1
-    for (int d = 0; d < bits; ++d) {
+    for (int d = d0; d < bits; ++d) {
 #pragma unroll 1
         for (int q = threadIdx.x; q < half * nr; q += kFscThreads) {
             const int r = q >> (bits - 1), p = prune ? ord8[q & (half - 1)] : q & (half - 1);
@@ -100,6 +102,50 @@ __device__ __forceinline__ void fsc_butterfly_low(double *T, int bits, int nr, i
     }
 }
 
+// Two steps at once of a full-tile transform over the low elements (tile bits
+// d and d + 1): one quad (x, x + 2^d, x + 2^(d+1), x + 2^d + 2^(d+1)) per
+// thread step, the quads visited in popcount order of their other 7 bits
+// (ord7); a warp skips a quad step when each of its four pairs is a no-op by
+// the rules of fsc_butterfly_low. The additions are those of the two single
+// steps, in the same order.
+__device__ __forceinline__ bool fsc_low_noop(int lo, int d, int c, bool mobius) {
+    if (!mobius) return __popc(lo) < c || __popc(lo >> d) > c;
+    const int ph = __popc(lo) + 1, free_above = (kFscTileBits - 1 - d) - __popc(lo >> (d + 1));
+    return ph > c || ph + free_above < c;
+}
+__device__ __forceinline__ void fsc_butterfly_low4(double *T, int nr, int c0, int d, bool mobius,
+                                                   const uint8_t *ord7) {
+#pragma unroll 1
+    for (int q = threadIdx.x; q < (kFscTile / 4) * nr; q += kFscThreads) {
+        const int r = q >> (kFscTileBits - 2), p = ord7[q & (kFscTile / 4 - 1)];
+        const int a = ((p >> d) << (d + 2)) | (p & ((1 << d) - 1));  // bits d, d+1 clear
+        const int b = a | (1 << d), cq = a | (1 << (d + 1)), e = b | cq, c = c0 + r;
+        const bool skip = fsc_low_noop(a, d, c, mobius) && fsc_low_noop(cq, d, c, mobius) &&
+                          fsc_low_noop(a, d + 1, c, mobius) && fsc_low_noop(b, d + 1, c, mobius);
+        if (__all_sync(0xffffffffu, skip)) continue;
+        double *row = T + r * kFscTile;
+        const double va = row[a], vb = row[b], vc = row[cq], ve = row[e];
+        if (!mobius) {
+            row[b] = vb + va;
+            row[cq] = vc + va;
+            row[e] = (ve + vc) + (vb + va);
+        } else {
+            row[b] = vb - va;
+            row[cq] = vc - va;
+            row[e] = (ve - vc) - (vb - va);
+        }
+    }
+    __syncthreads();
+}
+
+// A full-tile transform over the 9 low elements: four double steps, then the
+// last element alone.
+__device__ __forceinline__ void fsc_transform_low(double *T, int nr, int c0, bool mobius, const uint8_t *ord8,
+                                                  const uint8_t *ord7) {
+    for (int d = 0; d + 1 < kFscTileBits; d += 2) fsc_butterfly_low4(T, nr, c0, d, mobius, ord7);
+    fsc_butterfly_low(T, kFscTileBits, nr, c0, mobius, ord8, kFscTileBits - 1);
+}
+
 // pass B: zeta or Mobius over the high tile bits [lg, 9) (the h = 9 - lg high
 // elements) of the rank rows 0..n-1 (rank k = row + 1), the pairs of a step
 // visited in popcount order of their high part (ordh: the masks of h - 1 bits
@@ -109,10 +155,11 @@ __device__ __forceinline__ void fsc_butterfly_low(double *T, int bits, int nr, i
 // above d and itself); Mobius, no high part with k - 9 .. k elements (the only
 // ones pass C reads at rank k) is reached from the target by adding elements
 // above d.
-__device__ __forceinline__ void fsc_butterfly_high(double *T, int lg, int n, bool mobius, const uint8_t *ordh) {
+__device__ __forceinline__ void fsc_butterfly_high(double *T, int lg, int n, bool mobius, const uint8_t *ordh,
+                                                   int dh0 = 0) {
     const int h = kFscTileBits - lg;
 #pragma unroll 1
-    for (int dh = 0; dh < h; ++dh) {
+    for (int dh = dh0; dh < h; ++dh) {
         const int d = lg + dh;
 #pragma unroll 1
         for (int q = threadIdx.x; q < (kFscTile / 2) * n; q += kFscThreads) {
@@ -135,6 +182,59 @@ __device__ __forceinline__ void fsc_butterfly_high(double *T, int lg, int n, boo
         }
         __syncthreads();
     }
+}
+
+// Two steps at once of the pass-B transform: the high elements dh and dh+1
+// (tile bits d = lg + dh and d + 1), one quad (x, x + 2^d, x + 2^(d+1),
+// x + 2^d + 2^(d+1)) per thread step, the quads visited in popcount order of
+// their other h - 2 high bits (ordh2). A warp skips a quad step when each of
+// its four pairs (two per element) is a no-op by the rules of
+// fsc_butterfly_high.
+__device__ __forceinline__ bool fsc_pair_noop(int xlo, int dh, int h, int k, bool mobius) {
+    if (!mobius) return __popc(xlo) < k - kFscTileBits || __popc(xlo >> dh) > k;
+    const int free_above = (h - 1 - dh) - __popc(xlo >> (dh + 1));
+    const int pl = __popc(xlo);
+    return pl + 1 > k || pl + 1 + free_above < k - kFscTileBits;
+}
+__device__ __forceinline__ void fsc_butterfly_high4(double *T, int lg, int n, int dh, bool mobius,
+                                                    const uint8_t *ordh2) {
+    const int h = kFscTileBits - lg, d = lg + dh;
+#pragma unroll 1
+    for (int q = threadIdx.x; q < (kFscTile / 4) * n; q += kFscThreads) {
+        const int r = q >> (kFscTileBits - 2), pq = q & (kFscTile / 4 - 1);
+        const int xr = ordh2[pq >> lg];                                              // h - 2 bits
+        const int xlo = ((xr >> dh) << (dh + 2)) | (xr & ((1 << dh) - 1));          // bits dh, dh+1 clear
+        const int k = r + 1;
+        const int bd = 1 << dh, bd1 = 1 << (dh + 1);
+        // the pairs of element dh (sources x and x + 2^(dh+1)) and of element dh+1
+        // (sources x and x + 2^dh, the latter already summed over element dh)
+        const bool skip = fsc_pair_noop(xlo, dh, h, k, mobius) && fsc_pair_noop(xlo | bd1, dh, h, k, mobius) &&
+                          fsc_pair_noop(xlo, dh + 1, h, k, mobius) && fsc_pair_noop(xlo | bd, dh + 1, h, k, mobius);
+        if (__all_sync(0xffffffffu, skip)) continue;
+        double *row = T + r * kFscTile;
+        const int a = (xlo << lg) | (pq & ((1 << lg) - 1)), b = a | (1 << d), c = a | (1 << (d + 1)), e = b | c;
+        const double va = row[a], vb = row[b], vc = row[c], ve = row[e];
+        if (!mobius) {
+            row[b] = vb + va;
+            row[c] = vc + va;
+            row[e] = (ve + vc) + (vb + va);
+        } else {
+            row[b] = vb - va;
+            row[c] = vc - va;
+            row[e] = (ve - vc) - (vb - va);
+        }
+    }
+    __syncthreads();
+}
+
+// The pass-B transform over the h high elements: two elements at a time, and
+// the last one alone when h is odd.
+__device__ __forceinline__ void fsc_transform_high(double *T, int lg, int n, bool mobius, const uint8_t *ordh,
+                                                   const uint8_t *ordh2) {
+    const int h = kFscTileBits - lg;
+    int dh = 0;
+    for (; dh + 1 < h; dh += 2) fsc_butterfly_high4(T, lg, n, dh, mobius, ordh2);
+    if (dh < h) fsc_butterfly_high(T, lg, n, mobius, ordh, dh);
 }
 
 // M_1..M_n (M_k = k L_k, L = log Z) of tile entry t in place of Z_1..Z_n,
@@ -189,7 +289,9 @@ __global__ void __launch_bounds__(kFscThreads, 3) fsc_kernel(const double *a, in
     __shared__ uint16_t s_order[kFscTile];  // tile entries by (popcount, value)
     __shared__ double s_inv[kFscMaxN + 1];  // 1/k
     __shared__ uint8_t s_ordh[1 << (kFscMaxN - kFscTileBits - 1)];  // masks of h - 1 bits by popcount
+    __shared__ uint8_t s_ordh2[1 << (kFscMaxN - kFscTileBits - 2)];  // masks of h - 2 bits by popcount
     __shared__ uint8_t s_ord8[kFscTile / 2];                        // masks of 8 bits by popcount
+    __shared__ uint8_t s_ord7[kFscTile / 4];                        // masks of 7 bits by popcount
     const int tid = threadIdx.x;
     const int N = 1 << n;
     if (tid <= kFscMaxN) s_inv[tid] = tid ? 1.0 / tid : 0.0;
@@ -211,6 +313,14 @@ __global__ void __launch_bounds__(kFscThreads, 3) fsc_kernel(const double *a, in
         for (int r = t; r; r &= r - 1) pos += binom_small(__ffs(r) - 1, ++i);
         s_ord8[pos] = static_cast<uint8_t>(t);
     }
+    for (int t = tid; t < kFscTile / 4; t += kFscThreads) {
+        const int p = __popc(t);
+        int pos = 0;
+        for (int c = 0; c < p; ++c) pos += binom_small(kFscTileBits - 2, c);
+        int i = 0;
+        for (int r = t; r; r &= r - 1) pos += binom_small(__ffs(r) - 1, ++i);
+        s_ord7[pos] = static_cast<uint8_t>(t);
+    }
     const int hb = n > kFscTileBits ? n - kFscTileBits - 1 : 0;  // bits of the high part minus one
     for (int t = tid; t < (1 << hb); t += kFscThreads) {
         const int p = __popc(t);
@@ -219,6 +329,15 @@ __global__ void __launch_bounds__(kFscThreads, 3) fsc_kernel(const double *a, in
         int i = 0;
         for (int r = t; r; r &= r - 1) pos += binom_small(__ffs(r) - 1, ++i);
         s_ordh[pos] = static_cast<uint8_t>(t);
+    }
+    const int hb2 = n > kFscTileBits + 1 ? n - kFscTileBits - 2 : 0;  // bits of the high part minus two
+    for (int t = tid; t < (1 << hb2); t += kFscThreads) {
+        const int p = __popc(t);
+        int pos = 0;
+        for (int c = 0; c < p; ++c) pos += binom_small(hb2, c);
+        int i = 0;
+        for (int r = t; r; r &= r - 1) pos += binom_small(__ffs(r) - 1, ++i);
+        s_ordh2[pos] = static_cast<uint8_t>(t);
     }
     __syncthreads();
     const int64_t items = order ? static_cast<int64_t>(*count) : batch;
@@ -258,7 +377,7 @@ __global__ void __launch_bounds__(kFscThreads, 3) fsc_kernel(const double *a, in
                 T[q] = __popc(x) + p == k0 + r ? ab[base + x] : 0.0;
             }
             __syncthreads();
-            fsc_butterfly_low(T, kFscTileBits, nr, k0 - p, false, s_ord8);
+            fsc_transform_low(T, nr, k0 - p, false, s_ord8, s_ord7);
             for (int q = tid; q < n * kFscTile; q += kFscThreads) {
                 const int k = (q >> kFscTileBits) + 1, x = q & (kFscTile - 1);
                 R[static_cast<size_t>(k - 1) * N + base + x] =
@@ -274,10 +393,10 @@ __global__ void __launch_bounds__(kFscThreads, 3) fsc_kernel(const double *a, in
                 T[q] = R[static_cast<size_t>(r) * N + (static_cast<size_t>(XH) << kFscTileBits) + (g << lg) + j];
             }
             __syncthreads();
-            fsc_butterfly_high(T, lg, n, false, s_ordh);
+            fsc_transform_high(T, lg, n, false, s_ordh, s_ordh2);
             fsc_log(T, kFscTile, n, s_order, __popc(g));
             __syncthreads();
-            fsc_butterfly_high(T, lg, n, true, s_ordh);
+            fsc_transform_high(T, lg, n, true, s_ordh, s_ordh2);
             for (int q = tid; q < n * kFscTile; q += kFscThreads) {
                 const int r = q >> kFscTileBits, t = q & (kFscTile - 1);
                 const int XH = t >> lg, j = t & ((1 << lg) - 1);
@@ -296,7 +415,7 @@ __global__ void __launch_bounds__(kFscThreads, 3) fsc_kernel(const double *a, in
                 T[q] = R[static_cast<size_t>(k0 + r - 1) * N + base + x];
             }
             __syncthreads();
-            fsc_butterfly_low(T, kFscTileBits, nr, k0 - p, true, s_ord8);
+            fsc_transform_low(T, nr, k0 - p, true, s_ord8, s_ord7);
             for (int x = tid; x < kFscTile; x += kFscThreads)
                 cb[base + x] = (XH | x) ? T[(__popc(x) + p - k0) * kFscTile + x] * s_inv[__popc(x) + p] : 0.0;
             __syncthreads();
