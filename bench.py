@@ -403,9 +403,18 @@ def measure_rows(args, dev, peak):
     G = torch.as_tensor(inputs.hubbard_g0_table()).to(dev)
     W, T = 16384, args.mc_steps
     walkers, feats, targs = {}, [], []
-    # untimed warm-up of the collection path on throwaway walkers (the first
-    # use of some kernels in a process loads them)
-    mc.Walkers(1024, 10, G, inputs.HUB_WIN, inputs.HUB_MTAU, seed=99).collect(2)
+    # untimed warm-up of every part of this row (collection, training, plain
+    # and delayed-acceptance steps) on throwaway walkers and a throwaway
+    # network: the first use of some kernels in a process loads or compiles
+    # them, seconds on a fresh box
+    wu = mc.Walkers(1024, 10, G, inputs.HUB_WIN, inputs.HUB_MTAU, seed=99)
+    Fw, tw = wu.collect(2)
+    net_w = mc.Surrogate(seed=99, max_batch=1024)
+    net_w.train(Fw, tw, epochs=1, batch=1024)
+    wu.step_plain(record=[])
+    wu.init_surrogate(net_w)
+    wu.step_da(net_w, record=[])
+    del wu, Fw, tw, net_w
     t_collect = 0.0
     for n in range(10, 15):
         wk = mc.Walkers(W, n, G, inputs.HUB_WIN, inputs.HUB_MTAU, seed=100 + n)
