@@ -203,6 +203,10 @@ def test_trained_network_gains_effective_samples_per_second(mc):
     F, t = wk.collect(60)
     net = mc.Surrogate(seed=32, max_batch=W)
     net.train(F, t, epochs=2, batch=8192, lr=3e-3)
+    # an untimed delayed-acceptance step first (the first use of a kernel in a
+    # process may load it); both timed chains start from the state after it
+    wk.init_surrogate(net)
+    wk.step_da(net, [])
     X0, w0, s0 = wk.X.clone(), wk.weight.clone(), wk.sign.clone()
     rec_p, rec_d = [], []
     _, t_p = mc.timed(lambda: [wk.step_plain(rec_p) for _ in range(300)])
