@@ -106,6 +106,28 @@ def test_pivots_between_1e6_and_1e3_of_the_norm(apm, n):
         assert np.max(np.abs(c.cpu().numpy() - cref)[:, 1:] / csc[:, 1:]) <= TOL
 
 
+def test_order_12_bench_size_sampled(apm):
+    """The launch the benchmark times for the minors alone (65536 Hubbard G0
+    matrices of order 12, the warp-per-matrix kernel and its redo launch):
+    1024 seeded sampled matrices and the first and last against the oracle
+    with the perm(|A[S]|) scale, and properties of every output (finite, the
+    empty set's minor 1, every singleton's minor its diagonal entry exactly:
+    its tree path drops every other element)."""
+    A = I.hubbard_batch(65536, 12, seed=2)
+    m, st = apm.all_minors(dev(A), return_status=True)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(12)
+    idx = np.concatenate([[0, 65535], np.sort(rng.choice(np.arange(1, 65535), 1024, replace=False))])
+    ref = oracle.minors_lu(A[idx])
+    scale = oracle.minors_scale(A[idx])
+    err = float(np.max(np.abs(m[idx].cpu().numpy() - ref) / np.maximum(scale, 1e-300)))
+    assert err <= TOL, err
+    assert int(st.cpu().numpy().max()) & ERROR_BITS == 0
+    assert bool(torch.isfinite(m).all()) and bool((m[:, 0] == 1.0).all())
+    diag = torch.as_tensor(np.ascontiguousarray(np.diagonal(A, axis1=1, axis2=2))).cuda()
+    assert torch.equal(m[:, [1 << i for i in range(12)]], diag)
+
+
 def test_order_24_sampled(apm):
     rng = np.random.default_rng(7300)
     n = 24
