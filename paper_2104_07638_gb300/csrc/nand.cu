@@ -215,7 +215,15 @@ __device__ __forceinline__ void nd_tail_level(const double *cur, double *nxt, Nd
     for (int i = lane; i < 2 * nodes; i += 32) {
         const int k = i >> 1, t = i & 1, pi = m - 2 + t;
         const double p = cur[k * mm + pi * rl + (m - 2)];
-        has |= nd_small(p, cc);
+        if constexpr (kCorr) {
+            has |= nd_small(p, cc);
+        } else {
+            // the first pass on the high words in integer arithmetic: also true
+            // up to 2^-20 above thrA, which only sends the matrix to the second
+            // pass, whose test is exact
+            has |= (static_cast<unsigned>(__double2hiint(p)) & 0x7fffffffu) <=
+                   static_cast<unsigned>(__double2hiint(cc.thrA));
+        }
         w.inv[i] = nd_inv(p, badl);
         ndn[3 * k + 1 + t] = ndc[k] * p;
         if (t == 0) ndn[3 * k] = ndc[k];
@@ -477,14 +485,19 @@ __device__ __forceinline__ int nd_matrix(const double *A, int n, double *out, ui
     cc.corr = 0;
     cc.ovf = 0;
     int bad = 0, nonfin = 0;
-    double amax = 0.0;
+    // ||A||max and the finiteness test on the bit patterns of |x|, off the FP64 pipe
+    unsigned long long am = 0;
     for (int e = lane; e < m0 * m0; e += 32) {
-        const double x = A[e];
-        if (!isfinite(x)) nonfin = 1;
-        amax = fmax(amax, fabs(x));
+        const unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(A[e])) & 0x7fffffffffffffffull;
+        nonfin |= u >= 0x7ff0000000000000ull;
+        am = u > am ? u : am;
     }
     nonfin = __any_sync(0xffffffffu, nonfin);
-    for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long y = __shfl_xor_sync(0xffffffffu, am, o);
+        am = y > am ? y : am;
+    }
+    const double amax = __longlong_as_double(static_cast<long long>(am));
     const double sc = amax > 0.0 ? amax : 1.0;
     cc.thrA = thr * sc;
     cc.Cm = shf * sc;
