@@ -38,6 +38,11 @@
 #include "apm_internal.cuh"
 #include "complex_ops.cuh"
 
+// x is infinite or NaN: the exponent bits all set, tested on the high word in
+// integer arithmetic (no FP64 compare)
+__device__ __forceinline__ bool nonfinite_bits(double x) {
+    return (static_cast<unsigned>(__double2hiint(x)) & 0x7ff00000u) == 0x7ff00000u;
+}
 namespace apm {
 
 // Tail size S (vertices expanded breadth first in shared memory) and warps per
@@ -270,7 +275,7 @@ __device__ __forceinline__ void kel_matrix(const double2 *A, int n, bool sgn, bo
     nonfin = 0;
     for (int e = lane; e < m0 * m0; e += 32) {
         const double2 v = A[e];
-        if (!isfinite(v.x) || !isfinite(v.y)) nonfin = 1;
+        nonfin |= nonfinite_bits(v.x) | nonfinite_bits(v.y);
     }
     nonfin = __any_sync(0xffffffffu, nonfin);
     KelAcc acc;

@@ -22,6 +22,11 @@
 #include "apm_internal.cuh"
 #include "complex_ops.cuh"
 
+// x is infinite or NaN: the exponent bits all set, tested on the high word in
+// integer arithmetic (no FP64 compare)
+__device__ __forceinline__ bool nonfinite_bits(double x) {
+    return (static_cast<unsigned>(__double2hiint(x)) & 0x7ff00000u) == 0x7ff00000u;
+}
 namespace apm {
 
 constexpr int kK2Tail = 6;
@@ -245,7 +250,7 @@ __device__ __forceinline__ void k2_matrix(const double2 *Au, const double2 *Ad, 
     int bad = 0, nonfin = 0;
     for (int e = lane; e < m0 * m0; e += 32) {
         const double2 u = Au[e], d = Ad[e];
-        if (!isfinite(u.x) || !isfinite(u.y) || !isfinite(d.x) || !isfinite(d.y)) nonfin = 1;
+        nonfin |= nonfinite_bits(u.x) | nonfinite_bits(u.y) | nonfinite_bits(d.x) | nonfinite_bits(d.y);
     }
     nonfin = __any_sync(0xffffffffu, nonfin);
     K2Acc acc;

@@ -30,6 +30,11 @@
 
 #include "apm_internal.cuh"
 
+// x is infinite or NaN: the exponent bits all set, tested on the high word in
+// integer arithmetic (no FP64 compare)
+__device__ __forceinline__ bool nonfinite_bits(double x) {
+    return (static_cast<unsigned>(__double2hiint(x)) & 0x7ff00000u) == 0x7ff00000u;
+}
 namespace apm {
 
 // vertices expanded breadth first (S) and warps per CTA
@@ -239,7 +244,7 @@ __device__ __forceinline__ void xn_matrix(const double *A, int n, double *out, u
     const int m0 = 2 * n;
     int bad = 0, nonfin = 0;
     for (int e = lane; e < m0 * m0; e += 32)
-        if (!isfinite(A[e])) nonfin = 1;
+        nonfin |= nonfinite_bits(A[e]);
     nonfin = __any_sync(0xffffffffu, nonfin);
     if (!nonfin) {
         if (D == 0) {
