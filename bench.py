@@ -838,8 +838,6 @@ def main():
                       "stderr": est["stderr"], "mean_abs_c": est["mean_abs"], "sign": est["sign"],
                       "exchange": "apm_order_sums per rank, summed over the ranks on the host"},
     })
-    if rows:
-        result["rows"] = rows
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r, threads, count, dt = cpu_oracle_rate(A_np, args.cpu_seconds)
         r1, _, count1, dt1 = cpu_rate(oracle_run, A_np, args.cpu_seconds / 4, 1)
@@ -854,6 +852,9 @@ def main():
                        "kind": "the paper's depth-first tree with pivot correction + the recursion, C/OpenMP",
                        "sample": f"{fcount} matrices on {threads} cores ({fdt:.1f} s), "
                                  f"{fcount1} on 1 core ({fdt1:.1f} s)"}}
+    if rows:
+        # the full rows last: the contract's keys all come before them
+        result["rows"] = rows
     if rank == 0:
         print(json.dumps(result), flush=True)
     if world > 1:
