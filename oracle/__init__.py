@@ -19,6 +19,15 @@ Functions (numpy in, numpy out; FP64 / complex128):
   keldysh_scale(Mt)         error scale for the Keldysh sum
   minors_scale(A)           perm(|A[S]|): sum of |Leibniz terms| of every minor
   minors_rowsum_bound(A)    prod_{i in S} sum_{j in S} |A_ij| (a cheaper upper bound)
+  xnor_minors(M)            all 2^n XNOR minors of 2n x 2n block matrices, one LU per
+                            kept submatrix (Section III.B)
+  xnor_scale(M)             error scale of the XNOR minors
+  nand(M, minors)           the 3^n NAND minors (Section III.C) or their sums over the
+                            two types of every subset (Section V.C), with their scale
+  keldysh2(Mu, Md, signed)  sum over shared Keldysh assignments of the product of the
+                            two spins' determinants (Section V.D), separate LUs
+  keldysh2_scale(Mu, Md)    error scale of that sum
+The surrogate network's FP64 forward and backward pass is in ``oracle/mlp.py``.
 """
 from __future__ import annotations
 
