@@ -807,7 +807,9 @@ def main():
     peak = FP64_FLOP_PER_CLK_SM * SMS * SM_MAX_MHZ * 1e6 / 1e12
     achieved = F * B / (ms_per_step * 1e-3) / 1e12
     clocks = cs.summary()
-    rows = measure_rows(args, dev, peak) if rank == 0 and not args.no_rows else None
+    # the per-row measurements are single-GPU kernel timings: taken at N = 1
+    # only, so that a multi-GPU launch ends with its timed steps
+    rows = measure_rows(args, dev, peak) if rank == 0 and world == 1 and not args.no_rows else None
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
