@@ -56,6 +56,10 @@ constexpr int kPpmWarps = 8;
 constexpr int kPpmMaxL = 7;
 constexpr int kPpmMaxN = 16;
 constexpr int kPpmVLanes = 64;      // term streams: two per lane
+// row stride of the U and RL tables: one double more than the 128 columns, so
+// that the 16 rows of one column, which a half-warp of the table phase writes
+// or reads at once, fall on different banks
+constexpr int kPpmLd = 129;
 constexpr int kPpmBpSlots = 2240;   // stream-interleaved B table: 64 x 35 terms for l = 7
 constexpr int kPpmResSlots = 236;   // 2^l sums + slots of the runs of cut sets (236 for l = 7)
 constexpr int kPpmSchedInts = 60000;
@@ -368,18 +372,18 @@ __device__ __forceinline__ double neg_bits(double x) {
     return __longlong_as_double(__double_as_longlong(x) ^ static_cast<long long>(0x8000000000000000ull));
 }
 
-// prod over the set bits e of mask of U[(row0 + e) * 128 + col] (1 for an empty
+// prod over the set bits e of mask of U[(row0 + e) * kPpmLd + col] (1 for an empty
 // mask): |mask| - 1 multiplies
 __device__ __forceinline__ double set_prod(const double *U, int row0, int mask, int col) {
     if (mask == 0) return 1.0;
-    double v = U[(row0 + __ffs(mask) - 1) * 128 + col];
-    for (int r = mask & (mask - 1); r; r &= r - 1) v *= U[(row0 + __ffs(r) - 1) * 128 + col];
+    double v = U[(row0 + __ffs(mask) - 1) * kPpmLd + col];
+    for (int r = mask & (mask - 1); r; r &= r - 1) v *= U[(row0 + __ffs(r) - 1) * kPpmLd + col];
     return v;
 }
 
 struct PpmSmem {
-    double U[kPpmMaxN * 128];   // [i][T_L]
-    double RL[kPpmMaxN * 128];  // [i][T_L]
+    double U[kPpmMaxN * kPpmLd];   // [i][T_L], rows kPpmLd apart
+    double RL[kPpmMaxN * kPpmLd];  // [i][T_L], rows kPpmLd apart
     double Bp[kPpmBpSlots];
     double alpha[kPpmWarps][128];  // base_w(T_L), then warp w's current alpha
     double res[kPpmWarps][kPpmResSlots];
@@ -422,7 +426,7 @@ __global__ void __launch_bounds__(kPpmWarps * 32, 3) ppm_kernel(const double *__
             double s = 0.0;
             for (int j = 0; j < l; ++j)
                 if ((TL >> j) & 1) s += __ldg(A + i * n + j);
-            sm.RL[i * 128 + TL] = s;
+            sm.RL[i * kPpmLd + TL] = s;
         }
         __syncthreads();
         for (int TH = 0; TH < (1 << h); ++TH) {
@@ -444,8 +448,8 @@ __global__ void __launch_bounds__(kPpmWarps * 32, 3) ppm_kernel(const double *__
                     for (int k = lane >> 4; k < ntl; k += 2) {
                         const int TL = tllist[k];
                         const bool inT = high ? inTH : ((TL >> i) & 1);
-                        const double rr = rhi + sm.RL[i * 128 + TL];
-                        sm.U[i * 128 + TL] = inT ? rr : neg_bits(rr);
+                        const double rr = rhi + sm.RL[i * kPpmLd + TL];
+                        sm.U[i * kPpmLd + TL] = inT ? rr : neg_bits(rr);
                     }
                 }
             }
@@ -456,15 +460,15 @@ __global__ void __launch_bounds__(kPpmWarps * 32, 3) ppm_kernel(const double *__
                 double *base = &sm.alpha[0][TL];  // base[bb * 128] for the lattice element subsets bb
                 base[0] = pt;
                 if (m >= 1) {
-                    const double u0 = sm.U[(l + e0) * 128 + TL];
+                    const double u0 = sm.U[(l + e0) * kPpmLd + TL];
                     base[128] = pt * u0;
                     if (m >= 2) {
-                        const double u1 = sm.U[(l + e1) * 128 + TL];
+                        const double u1 = sm.U[(l + e1) * kPpmLd + TL];
                         const double b2 = pt * u1;
                         base[2 * 128] = b2;
                         base[3 * 128] = b2 * u0;
                         if (m >= 3) {
-                            const double u2 = sm.U[(l + e2) * 128 + TL];
+                            const double u2 = sm.U[(l + e2) * kPpmLd + TL];
                             const double b4 = pt * u2, b6 = b4 * u1;
                             base[4 * 128] = b4;
                             base[5 * 128] = b4 * u0;
@@ -496,7 +500,7 @@ __global__ void __launch_bounds__(kPpmWarps * 32, 3) ppm_kernel(const double *__
                             const int2 w = cur[k];
                             const int dst = w.x & 0xffff, src = (w.x >> 16) & 0xffff;
                             const int el = w.y & 0xff, TL = w.y >> 8;
-                            sm.Bp[dst] = d == 0 ? set_prod(sm.U, 0, TL, TL) : sm.Bp[src] * sm.U[el * 128 + TL];
+                            sm.Bp[dst] = d == 0 ? set_prod(sm.U, 0, TL, TL) : sm.Bp[src] * sm.U[el * kPpmLd + TL];
                         }
                     }
                     __syncwarp();
@@ -537,7 +541,7 @@ __global__ void __launch_bounds__(kPpmWarps * 32, 3) ppm_kernel(const double *__
                         for (int k = 0; k < 4; ++k) {
                             const int TL = lane + 32 * k;
                             if (TL < NL) {
-                                const double u = sm.U[(l + el) * 128 + TL];
+                                const double u = sm.U[(l + el) * kPpmLd + TL];
                                 switch (p) {
                                     case 1: a1[k] = a0[k] * u; break;
                                     case 2: a2[k] = a1[k] * u; break;
