@@ -27,6 +27,26 @@ __device__ __forceinline__ double rcp_nr(double d) {
     return 1.0 / d;
 }
 
+// Asynchronous global -> shared copies of 8 or 16 bytes (cp.async): a thread
+// issues all of its copies of a staging step back to back, without holding the
+// values in registers, and waits once for all of them, so that one memory
+// latency is exposed per step instead of one per unrolled group of loads.
+// Both addresses must be aligned to the copy size. After cp_async_wait_all the
+// data is visible to the issuing thread; a barrier makes it visible to the
+// others.
+__device__ __forceinline__ void cp_async8(double *dst, const double *src) {
+    const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(double *dst, const double *src) {
+    const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
 // Threads per CTA of the minor / connected-sum kernels.
 constexpr int kCdetThreads = 256;
 // Capacity of the per-matrix pivot-correction log.

@@ -472,26 +472,29 @@ __device__ __forceinline__ void block_conv(const double *cb, const double *ab, d
 // low part, T_L = S_L allowed), the S_L = {} entry only when the lowest element
 // of S_H lies in T_H; then the diagonal block solves its own recursion with
 // init a[S_H u S_L] - acc[S_L] and the pure-low block a[0 u .]. a (global) and
-// c (global output row) are read block-wise into shared memory (blk: 6 x 2^kBlkB).
+// c (global output row) are read block-wise into shared memory (blk: 6 x 2^kBlkB)
+// by asynchronous 16-byte copies (both rows and every block are 16-byte aligned).
 __device__ void cdet_blocked(const double *a, double *c, int n, double *blk, unsigned long long gsel_b) {
     const int tid = threadIdx.x, T = blockDim.x;
     const int b = kBlkB, NB = 1 << kBlkB, h = n - b;
     double *cb = blk, *ab = blk + NB, *acc = blk + 2 * NB, *cs = blk + 3 * NB, *as = blk + 4 * NB,
            *a0 = blk + 5 * NB;
-    for (int t = tid; t < NB; t += T) a0[t] = a[t];
+    for (int t = tid; t < NB / 2; t += T) cp_async16(a0 + 2 * t, a + 2 * t);
     for (int SH = 0; SH < (1 << h); ++SH) {
-        for (int t = tid; t < NB; t += T) {
-            acc[t] = 0.0;
-            as[t] = a[(static_cast<size_t>(SH) << b) + t];
-        }
+        const double *aS = a + (static_cast<size_t>(SH) << b);
+        for (int t = tid; t < NB / 2; t += T) cp_async16(as + 2 * t, aS + 2 * t);
+        for (int t = tid; t < NB; t += T) acc[t] = 0.0;
         const int jH = SH & (-SH);
+        cp_async_wait_all();
         __syncthreads();
         if (SH) {
             for (int TH = (SH - 1) & SH;; TH = (TH - 1) & SH) {
-                for (int t = tid; t < NB; t += T) {
-                    cb[t] = c[(static_cast<size_t>(TH) << b) + t];
-                    ab[t] = a[(static_cast<size_t>(SH ^ TH) << b) + t];
+                const double *cT = c + (static_cast<size_t>(TH) << b), *aR = a + (static_cast<size_t>(SH ^ TH) << b);
+                for (int t = tid; t < NB / 2; t += T) {
+                    cp_async16(cb + 2 * t, cT + 2 * t);
+                    cp_async16(ab + 2 * t, aR + 2 * t);
                 }
+                cp_async_wait_all();
                 __syncthreads();
                 block_conv(cb, ab, acc, b, gsel_b);
                 if (tid == 0 && (TH & jH)) acc[0] = fma(cb[0], ab[0], acc[0]);

@@ -36,9 +36,11 @@
 // no-ops fall into whole warps: 39 % of the transforms' pair visits are
 // skipped at n = 16 (28 % in mask order). The butterfly loops are kept rolled,
 // which keeps the kernel within the registers of three CTAs per SM. The
-// transforms act on M_k = k L_k (linear), and the
-// read-out divides by |S|. The logarithm keeps Z and M of one mask in
-// registers and skips the terms Z_m = 0 (m > |X|) when every lane of the warp
+// transforms act on M_k = k L_k (linear), and the read-out divides by |S|.
+// The input row and the ranked arrays come into the tile by asynchronous
+// copies (cp.async, 16 bytes where the layout allows), all of a thread's
+// copies of a staging step in flight at once. The logarithm keeps Z and M of
+// one mask in registers and skips the terms Z_m = 0 (m > |X|) when every lane of the warp
 // has |X| <= 9: in pass B the masks of a tile are visited in order of
 // popcount (|X| = popcount of the tile index + that of the group), so that
 // the warps are mostly uniform in |X|.
@@ -374,8 +376,12 @@ __global__ void __launch_bounds__(kFscThreads, 3) fsc_kernel(const double *a, in
             const size_t base = static_cast<size_t>(XH) << kFscTileBits;
             for (int q = tid; q < nr * kFscTile; q += kFscThreads) {
                 const int r = q >> kFscTileBits, x = q & (kFscTile - 1);
-                T[q] = __popc(x) + p == k0 + r ? ab[base + x] : 0.0;
+                if (__popc(x) + p == k0 + r)
+                    cp_async8(T + q, ab + base + x);
+                else
+                    T[q] = 0.0;
             }
+            cp_async_wait_all();
             __syncthreads();
             fsc_transform_low(T, nr, k0 - p, false, s_ord8, s_ord7);
             for (int q = tid; q < n * kFscTile; q += kFscThreads) {
@@ -387,11 +393,14 @@ __global__ void __launch_bounds__(kFscThreads, 3) fsc_kernel(const double *a, in
         }
         // pass B: zeta over the high elements, logarithm, Mobius over the high elements
         for (int g = 0; g < NH; ++g) {
-            for (int q = tid; q < n * kFscTile; q += kFscThreads) {
-                const int r = q >> kFscTileBits, t = q & (kFscTile - 1);
+            // pairs of entries (lg >= 1: j and j + 1 are adjacent in R as in T)
+            for (int q2 = tid; q2 < n * kFscTile / 2; q2 += kFscThreads) {
+                const int q = 2 * q2, r = q >> kFscTileBits, t = q & (kFscTile - 1);
                 const int XH = t >> lg, j = t & ((1 << lg) - 1);
-                T[q] = R[static_cast<size_t>(r) * N + (static_cast<size_t>(XH) << kFscTileBits) + (g << lg) + j];
+                cp_async16(T + q, R + static_cast<size_t>(r) * N + (static_cast<size_t>(XH) << kFscTileBits) +
+                                      (g << lg) + j);
             }
+            cp_async_wait_all();
             __syncthreads();
             fsc_transform_high(T, lg, n, false, s_ordh, s_ordh2);
             fsc_log(T, kFscTile, n, s_order, __popc(g));
@@ -410,10 +419,11 @@ __global__ void __launch_bounds__(kFscThreads, 3) fsc_kernel(const double *a, in
             const int p = __popc(XH), k0 = p > 1 ? p : 1, k1 = p + kFscTileBits < n ? p + kFscTileBits : n;
             const int nr = k1 - k0 + 1;
             const size_t base = static_cast<size_t>(XH) << kFscTileBits;
-            for (int q = tid; q < nr * kFscTile; q += kFscThreads) {
-                const int r = q >> kFscTileBits, x = q & (kFscTile - 1);
-                T[q] = R[static_cast<size_t>(k0 + r - 1) * N + base + x];
+            for (int q2 = tid; q2 < nr * kFscTile / 2; q2 += kFscThreads) {
+                const int q = 2 * q2, r = q >> kFscTileBits, x = q & (kFscTile - 1);
+                cp_async16(T + q, R + static_cast<size_t>(k0 + r - 1) * N + base + x);
             }
+            cp_async_wait_all();
             __syncthreads();
             fsc_transform_low(T, nr, k0 - p, true, s_ord8, s_ord7);
             for (int x = tid; x < kFscTile; x += kFscThreads)
