@@ -152,6 +152,13 @@ apm_status_t apm_all_minors(const double *A, int n, int64_t batch, double *minor
  * convolution of apm_cdet_from_weights_fsc (a second launch on `stream`, in
  * place on c), which is faster there; the results agree with the recursion up
  * to rounding.
+ * For n >= 13 with A_dn NULL the minors come first from the one-warp-per-matrix
+ * tree of apm_all_minors (a launch on `stream` before the fused kernel, writing
+ * them to minors_out, or to c when minors_out is NULL); the fused kernel forms
+ * the weights from them and computes the tree itself, with the pivot
+ * correction, only for the matrices that tree flagged (a pivot at or below the
+ * threshold, a non-finite entry). The workspace then also holds one flag byte
+ * per matrix (apm_workspace_size with APM_OP_CDET includes it).
  */
 apm_status_t apm_cdet_connected(const double *A_up, const double *A_dn, int n, int64_t batch,
                                 int flags, double *c, double *minors_out,
@@ -428,7 +435,9 @@ apm_status_t apm_perm_minors(const double *A, int n, int64_t batch, double *perm
  * The lane-group mapping per order is the one installed by apm_cdet_tune_set.
  * Order-16 matrices (the first ones of that order, counted by the sort) leave
  * their weights in c and a third launch finishes them in place by the fast
- * subset convolution, as apm_cdet_connected does at n = 16.
+ * subset convolution, as apm_cdet_connected does at n = 16. Without A_dn, the
+ * matrices of orders 13..16 take their minors, as apm_cdet_connected does, from
+ * one warp-per-matrix launch per order before the persistent kernel.
  * A matrix whose n[b] is outside 1..n_max is skipped with APM_ST_BAD_ORDER.
  * The call allocates nothing and does not synchronise: it can be captured in a
  * CUDA graph once the first (non-captured) call on the device has run.

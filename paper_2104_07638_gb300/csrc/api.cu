@@ -51,8 +51,22 @@ apm_status_t cdet_common(apm::CdetArgs &a, void *workspace, size_t workspace_byt
             if (err) return cuda_fail(err);
             if (f > need) need = f;
         }
-        if (!workspace || workspace_bytes < need || !aligned16(workspace)) return APM_ERR_WORKSPACE;
-        a.gscratch = static_cast<double *>(workspace);
+        // connected sums of one matrix per item: the minors come from the
+        // warp-per-matrix kernel (its flags first, its stacks in the slots' region)
+        const bool route = a.mode == apm::kModeCdet && !two && a.n >= apm::kWarpRouteFromN;
+        size_t flag_bytes = 0;
+        if (route) {
+            const size_t st = apm::fpm_warp_route_stack_bytes(a.n, a.batch, &err);
+            if (err) return cuda_fail(err);
+            if (st > need) need = st;
+            flag_bytes = (static_cast<size_t>(a.batch) + 255) & ~static_cast<size_t>(255);
+        }
+        if (!workspace || workspace_bytes < flag_bytes + need || !aligned16(workspace)) return APM_ERR_WORKSPACE;
+        if (route) {
+            a.wflag = static_cast<uint8_t *>(workspace);
+            a.warp_from_n = apm::kWarpRouteFromN;
+        }
+        a.gscratch = reinterpret_cast<double *>(static_cast<unsigned char *>(workspace) + flag_bytes);
     }
     const int e = apm::launch_fpm_cdet(a, s);
     return e ? cuda_fail(e) : APM_OK;
@@ -539,6 +553,13 @@ apm_status_t apm_workspace_size(int op, int n_max, int64_t batch, int two_mats, 
                 const size_t f = apm::fsc_workspace_bytes(n_max, batch, &err);
                 if (err) return cuda_fail(err);
                 if (f > *bytes) *bytes = f;
+            }
+            if (op == APM_OP_CDET && !two && n_max >= apm::kWarpRouteFromN) {
+                // the warp-per-matrix minors: its stacks in the same region, its flags before it
+                const size_t st = apm::fpm_warp_route_stack_bytes(n_max, batch, &err);
+                if (err) return cuda_fail(err);
+                if (st > *bytes) *bytes = st;
+                *bytes += (static_cast<size_t>(batch) + 255) & ~static_cast<size_t>(255);
             }
             return APM_OK;
         }

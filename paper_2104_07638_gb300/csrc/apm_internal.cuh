@@ -95,6 +95,13 @@ struct CdetArgs {
     // a larger matrix take that matrix's norm)
     const double *anorm_in;
     int anorm_shift;
+    // connected sums of one matrix per item at orders >= warp_from_n (0: none):
+    // the warp-per-matrix minors kernel ran first and left each item's minors
+    // in its minors_out row (its c row when minors_out is NULL); the fused
+    // kernel reads them back and only computes the tree itself where
+    // wflag[b] != 0 (b: the item's batch index)
+    uint8_t *wflag;
+    int warp_from_n;
 };
 
 // Orders whose connected sums apm_cdet_connected and its uneven-batch form take
@@ -124,6 +131,17 @@ size_t fpm_warp_workspace_bytes(int n, int64_t batch, int *err);
 int launch_fpm_warp(const double *A, int n, int64_t batch, double *minors, double thr, double shf,
                     uint32_t *status, void *workspace, cudaStream_t s, const double *pre = nullptr,
                     const double *anorm_in = nullptr, int anorm_shift = 0);
+
+// The minors of the connected-sum paths at orders 13..16, one warp per matrix:
+// fixed order (order == NULL: matrix b at A + b n^2, minors at out + b 2^n) or
+// the items order[*first + i], i < *count, of an uneven batch (A + a_off[b],
+// out + o_off[b]); flag[b] = 1 where the fused kernel must compute the tree
+// itself. The stack is caller scratch of fpm_warp_route_stack_bytes(n_max, batch).
+constexpr int kWarpRouteFromN = 13;
+size_t fpm_warp_route_stack_bytes(int n, int64_t batch, int *err);
+int launch_fpm_warp_route(const double *A, int n, int64_t batch, double *out, double thr, uint8_t *flag,
+                          uint32_t *status, double *stack, const int *order, const int64_t *a_off,
+                          const int64_t *o_off, const unsigned *first, const unsigned *count, cudaStream_t s);
 
 // All principal minors for orders 17..24: the upper levels of the tree breadth
 // first, the 12 x 12 leaves by the fused kernel (fpm_big.cu).

@@ -512,12 +512,16 @@ __device__ void cdet_blocked(const double *a, double *c, int n, double *blk, uns
 }
 
 // One matrix: minors (and optionally the connected sums) into the output rows.
-// MA/MC/MU are on chip (in_smem) or in the CTA's global scratch slot.
+// MA/MC/MU are on chip (in_smem) or in the CTA's global scratch slot. given:
+// the warp-per-matrix minors kernel has already left this matrix's minors in
+// mo (in co when mo is NULL) and its status; only the weights and the
+// connected sums remain.
 __device__ __forceinline__ void cdet_item(const CdetArgs &p, int n, const double *Au, const double *Ad,
                                           const double *ain, double *mo, double *co, uint32_t *st,
                                           double *MA, double *MC, double *MU, bool in_smem,
                                           unsigned long long gsel, unsigned long long gsel_b, double *blk,
-                                          CdetSmemHdr &h, const double *anorm_over, double root) {
+                                          CdetSmemHdr &h, const double *anorm_over, double root,
+                                          bool given = false) {
     const int tid = threadIdx.x;
     const int N = 1 << n;
     if (tid == 0) bulk_wait_read();  // the previous item's bulk stores have read their source
@@ -528,6 +532,14 @@ __device__ __forceinline__ void cdet_item(const CdetArgs &p, int n, const double
     __syncthreads();
     if (p.mode == kModeWeights) {
         for (int t = tid; t < N; t += blockDim.x) MA[t] = __ldg(ain + t);
+        __syncthreads();
+    } else if (given) {
+        // the weights from the given minors (one matrix: det^2, or det)
+        const double *src = mo ? mo : co;
+        for (int t = tid; t < N; t += blockDim.x) {
+            const double m = src[t];
+            MA[t] = p.single_det ? m : m * m;
+        }
         __syncthreads();
     } else {
         if (p.two_mats) {
@@ -601,7 +613,7 @@ __global__ void __launch_bounds__(kCdetThreads, 3) fpm_cdet_kernel(const CdetKer
                   p.minors_out ? p.minors_out + b * (p.two_mats ? 2 * N : N) : nullptr,
                   p.c_out ? p.c_out + b * N : nullptr, p.status ? p.status + b : nullptr, MA, MC, MU,
                   kSmemArrays, P.gsel, P.gsel_b, sbase, h, p.anorm_in ? p.anorm_in + (b >> p.anorm_shift) : nullptr,
-                  p.pre ? p.pre[b] : 1.0);
+                  p.pre ? p.pre[b] : 1.0, p.wflag && n >= p.warp_from_n && !p.wflag[b]);
     };
     if (p.redo_list) {
         // only the matrices the warp-per-matrix minors kernel flagged (usually none)
@@ -647,7 +659,8 @@ __global__ void __launch_bounds__(kCdetThreads, 3) fpm_cdet_varlen_kernel(const 
                   p.a_in ? p.a_in + co : nullptr,
                   p.minors_out ? p.minors_out + (p.two_mats ? 2 * co : co) : nullptr,
                   p.c_out ? p.c_out + co : nullptr, p.status ? p.status + b : nullptr, MA, MC, MU, in_smem,
-                  gsel_s[n], gsel_s[kBlkB], sbase, h, nullptr, 1.0);
+                  gsel_s[n], gsel_s[kBlkB], sbase, h, nullptr, 1.0,
+                  p.wflag && p.warp_from_n && n >= p.warp_from_n && !p.wflag[b]);
     }
     if (threadIdx.x == 0) bulk_wait_all();
 }
@@ -841,6 +854,13 @@ int launch_fpm_cdet(const CdetArgs &a, cudaStream_t s) {
     const size_t smem = cdet_smem_bytes(a.n, a.two_mats != 0, smem_arrays);
     const bool fsc = a.mode == kModeCdet && a.n >= g_fsc_from_n;
     P.a.fsc_from_n = fsc ? g_fsc_from_n : 0;
+    if (a.wflag && a.warp_from_n && a.n >= a.warp_from_n) {
+        // the minors first, one warp per matrix (its stack in the slots' region,
+        // which the fused kernel takes over after it)
+        err = launch_fpm_warp_route(a.A_up, a.n, a.batch, a.minors_out ? a.minors_out : a.c_out, a.piv_thr,
+                                    a.wflag, a.status, a.gscratch, nullptr, nullptr, nullptr, nullptr, nullptr, s);
+        if (err) return err;
+    }
     if (smem_arrays)
         fpm_cdet_kernel<true><<<grid, kCdetThreads, smem, s>>>(P);
     else
@@ -878,7 +898,16 @@ int cdet_varlen_grid(bool two_mats, int *err) {
     return sms * per_sm;
 }
 
-// Workspace of an uneven batch: [counter 256 B][order: batch int32][per-CTA slots]
+// Orders from which the connected-sum paths of one matrix per item take their
+// minors from the warp-per-matrix kernel (0: never).
+static int warp_route_from(int n_max, bool two_mats) {
+    return !two_mats && n_max >= kWarpRouteFromN ? kWarpRouteFromN : 0;
+}
+
+// Workspace of an uneven batch: [counter 256 B][order: batch int32]
+// [flags of the warp-kernel minors: batch bytes, with orders >= 13 of one
+// matrix per item][per-CTA slots; the same region holds the warp kernel's
+// stacks before and the ranked arrays after the persistent kernel]
 size_t cdet_varlen_workspace(int n_max, int64_t batch, bool two_mats, int *err) {
     size_t bytes = 256 + align256(static_cast<size_t>(batch) * sizeof(int));
     if (n_max > kVarlenSmemMaxN) {
@@ -889,6 +918,12 @@ size_t cdet_varlen_workspace(int n_max, int64_t batch, bool two_mats, int *err) 
             const size_t f = fsc_workspace_bytes(n_max, batch, err);
             if (*err) return 0;
             if (f > slots) slots = f;
+        }
+        if (warp_route_from(n_max, two_mats)) {
+            const size_t st = fpm_warp_route_stack_bytes(n_max, batch, err);
+            if (*err) return 0;
+            if (st > slots) slots = st;
+            bytes += align256(static_cast<size_t>(batch));
         }
         bytes += slots;
     } else {
@@ -913,12 +948,24 @@ int launch_cdet_varlen(const CdetArgs &a, const int64_t *a_off, const int *n_arr
     unsigned char *ws = static_cast<unsigned char *>(workspace);
     unsigned *ctr = reinterpret_cast<unsigned *>(ws);
     int *order = reinterpret_cast<int *>(ws + 256);
-    double *slots = reinterpret_cast<double *>(ws + 256 + align256(static_cast<size_t>(a.batch) * sizeof(int)));
+    size_t off = 256 + align256(static_cast<size_t>(a.batch) * sizeof(int));
+    const int wfrom = n_max > kVarlenSmemMaxN && a.mode == kModeCdet ? warp_route_from(n_max, two) : 0;
+    uint8_t *wflag = wfrom ? ws + off : nullptr;
+    if (wfrom) off += align256(static_cast<size_t>(a.batch));
+    double *slots = reinterpret_cast<double *>(ws + off);
     const int fsc_from = g_fsc_from_n;
     err = launch_order(n_arr, a.batch, n_max, order, ctr, s, fsc_from);
     if (err) return err;
+    // the minors of the items of orders >= wfrom, one launch per order from its
+    // first index and count in the sorted list, one warp per matrix
+    for (int m = n_max; wfrom && m >= wfrom && !err; --m)
+        err = launch_fpm_warp_route(a.A_up, m, a.batch, a.minors_out ? a.minors_out : a.c_out, a.piv_thr, wflag,
+                                    a.status, slots, order, a_off, c_off, ctr + 2 + 2 * m, ctr + 3 + 2 * m, s);
+    if (err) return err;
     VarlenParams V;
     V.a = a;
+    V.a.wflag = wflag;
+    V.a.warp_from_n = wfrom;
     V.a.gscratch = n_max > kVarlenSmemMaxN ? slots : nullptr;
     V.a_off = a_off;
     V.n_arr = n_arr;

@@ -331,6 +331,39 @@ __global__ void __launch_bounds__(kFwWarps * 32, 2) fpm_warp_kernel(const double
     }
 }
 
+// The minors of the connected-sum paths at orders 13..16 (fpm_cdet.cu reads
+// them back unless a matrix is flagged): matrix b's minors go to
+// out + b * 2^n, or, with an item list (order != NULL), the items
+// order[*first + i], i < *count, of an uneven batch, matrix A + a_off[b] and
+// minors out + o_off[b]. flag[b] = 1 where the fused kernel must compute the
+// matrix itself (a pivot at or below the threshold, a non-finite entry), else 0
+// with status[b] = 0. Orders above 12 only (tail of 12 elements).
+__global__ void __launch_bounds__(kFwWarps * 32, 2) fpm_warp_route_kernel(
+    const double *__restrict__ A, int n, int64_t batch, double *out, double thr, uint8_t *flag,
+    uint32_t *status, double *stack_base, size_t stack_per_warp, const int *__restrict__ order,
+    const int64_t *__restrict__ a_off, const int64_t *__restrict__ o_off, const unsigned *first,
+    const unsigned *count) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    FwWarpSmem &w = reinterpret_cast<FwWarpSmem *>(smem_raw)[wid];
+    const int64_t gw = static_cast<int64_t>(blockIdx.x) * kFwWarps + wid;
+    const int64_t nw = static_cast<int64_t>(gridDim.x) * kFwWarps;
+    double *stack = stack_base ? stack_base + gw * stack_per_warp : nullptr;
+    const int64_t nn = static_cast<int64_t>(n) * n, N = int64_t(1) << n;
+    const int64_t items = order ? static_cast<int64_t>(*count) : batch;
+    const int64_t i0 = order ? static_cast<int64_t>(*first) : 0;
+    for (int64_t i = gw; i < items; i += nw) {
+        const int64_t b = order ? order[i0 + i] : i;
+        const double *Ab = order ? A + a_off[b] : A + b * nn;
+        double *ob = order ? out + o_off[b] : out + b * N;
+        const int r = fw_matrix<kFwTail>(Ab, n, ob, thr, 1.0, nullptr, stack, w, lane);
+        if (lane == 0) {
+            flag[b] = static_cast<uint8_t>(r);
+            if (status && !r) status[b] = 0u;
+        }
+    }
+}
+
 using FwKernel = void (*)(const double *, int, int64_t, double *, double, const double *, uint32_t *, unsigned *,
                          uint32_t *, double *, size_t, const double *, int);
 static FwKernel fw_kernel_for(int n) {
@@ -433,6 +466,47 @@ int launch_fpm_warp(const double *A, int n, int64_t batch, double *minors, doubl
     a.anorm_shift = anorm_shift;
     a.pre = pre;
     return launch_fpm_cdet(a, s);
+}
+
+static int fw_route_grid(int64_t batch, int *err) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t smem = kFwWarps * sizeof(FwWarpSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(fpm_warp_route_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(smem));
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fpm_warp_route_kernel, kFwWarps * 32, smem);
+    if (e != cudaSuccess || per_sm < 1) {
+        *err = e != cudaSuccess ? static_cast<int>(e) : static_cast<int>(cudaErrorInvalidConfiguration);
+        return 0;
+    }
+    *err = 0;
+    const int64_t need = (batch + kFwWarps - 1) / kFwWarps;
+    int64_t g = static_cast<int64_t>(sms) * per_sm;
+    if (need < g) g = need;
+    return static_cast<int>(g < 1 ? 1 : g);
+}
+
+size_t fpm_warp_route_stack_bytes(int n, int64_t batch, int *err) {
+    *err = 0;
+    if (batch == 0 || n <= kFwTail) return 0;
+    const int grid = fw_route_grid(batch, err);
+    if (*err) return 0;
+    return static_cast<size_t>(grid) * kFwWarps * fw_stack_entries(n) * sizeof(double);
+}
+
+int launch_fpm_warp_route(const double *A, int n, int64_t batch, double *out, double thr, uint8_t *flag,
+                          uint32_t *status, double *stack, const int *order, const int64_t *a_off,
+                          const int64_t *o_off, const unsigned *first, const unsigned *count, cudaStream_t s) {
+    if (n <= kFwTail || n > kFwMaxN) return static_cast<int>(cudaErrorInvalidValue);
+    int err = 0;
+    const int grid = fw_route_grid(batch, &err);
+    if (err) return err;
+    fpm_warp_route_kernel<<<grid, kFwWarps * 32, kFwWarps * sizeof(FwWarpSmem), s>>>(
+        A, n, batch, out, thr, flag, status, stack, fw_stack_entries(n), order, a_off, o_off, first, count);
+    return static_cast<int>(cudaGetLastError());
 }
 
 }  // namespace apm
