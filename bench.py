@@ -106,7 +106,7 @@ def parse():
     ap.add_argument("--case", default=None,
                     choices=["cdet_n12", "cdet_n12_full", "cdet_n16", "keldysh_n12", "ppm_n14", "cdet_uneven",
                              "xnor_n12", "nand_n10", "keldysh2_n12", "mlp_gemm", "fsc_n16", "minors_n12",
-                             "minors_n20", "minors_n24", "fp64_probe"],
+                             "minors_n20", "minors_n24", "fp64_probe", "keldysh_uneven"],
                     help="run 3 launches of one kernel on a small case (for profiling) and exit")
     return ap.parse_args()
 
@@ -650,6 +650,14 @@ def profile_case(name: str):
         # the benchmark row: 16 matrices of order 24 (2.1 GB of minors; 4096 leaves of order 12 each)
         A = torch.as_tensor(np.random.default_rng(24).standard_normal((16, 24, 24)) + 2.0 * np.eye(24)).to(dev)
         run = lambda: apm.all_minors(A)
+    elif name == "keldysh_uneven":
+        # the uneven Keldysh batch of the a5 row on 16384 walkers (orders 4..16)
+        orders = inputs.varlen_orders(16384, 4, 16, seed=3)
+        kflat, koff = inputs.keldysh_varlen(orders, seed=3)
+        Mt = torch.as_tensor(kflat).to(dev)
+        m_off = torch.as_tensor(koff).to(dev)
+        n_t = torch.as_tensor(orders).to(dev)
+        run = lambda: apm.keldysh_sum_varlen(Mt, m_off, n_t)
     elif name == "nand_n10":
         M = torch.as_tensor(inputs.two_type_batch(16384, 10, seed=7)).to(dev)
         run = lambda: apm.two_type_cdet(M)
