@@ -119,6 +119,10 @@ def test_uneven_batch_with_flagged_items_equals_fixed(apm):
     c, mo, st = apm.cdet_connected_varlen(A, ao, nt, return_minors=True, return_status=True)
     c_off = apm.varlen_out_offsets(nt).cpu().numpy()
     c, mo, st = c.cpu().numpy(), mo.cpu().numpy(), st.cpu().numpy()
+    # without the minors requested (they pass through the connected-sum rows)
+    c2, st2 = apm.cdet_connected_varlen(A, ao, nt, return_status=True)
+    assert np.array_equal(c2.cpu().numpy(), c, equal_nan=True)
+    assert np.array_equal(st2.cpu().numpy(), st)
     assert st[2] & apm.ST_PIVOT_CORRECTED and st[3] & apm.ST_PIVOT_CORRECTED, st
     assert st[6] & apm.ST_NONFINITE_INPUT, st
     for n in np.unique(orders):
